@@ -1,0 +1,456 @@
+"""Throughput benchmark of the TVOLAP hot path on GB300.
+
+Workload (default): 64 independent channels, L = 256 (2L = 512, 4L = 1024),
+480000 samples per channel (10 s at 48 kHz, pink-ish noise), eight stored
+48000-tap impulse responses per channel (M = 94 partitions), a new filter at
+every block mixed from two stored responses by a random walk. One step is the
+whole path over that batch: transform the 512 stored responses into the
+partition bank (Eqs. 2, 4, 6), then the offline TVOLAP of all channels
+(forward transforms, Eq. 7 multiply-accumulate, inverse transforms and
+overlap-add). Inputs are resident in device memory when the timed region
+starts; the step's working set (about 1.5 GB) is far larger than the 129 MB
+L2, so no flush is needed between steps.
+
+Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "channel-samples/s"
+UNIT = "channel-samples/s"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP32 FMA peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops x clock.
+SMS, FP32_LANES = 152, 128
+
+
+def fp32_peak_tflops(mhz: float) -> float:
+    return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            p = [s.strip() for s in line.split(",")]
+            if len(p) >= 9:
+                self.rows.append(p)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        mhz = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(mhz) if mhz else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def workload(args):
+    from synth import workloads as W
+    return W.plain_at_scale(n_ch=args.channels, N=args.samples)
+
+
+def mac_terms(nb: int, M: int) -> int:
+    """Number of (block, partition) products of Eq. 7 with t - 2m >= 0."""
+    t = np.arange(nb)
+    return int(np.minimum(M, t // 2 + 1).sum())
+
+
+# --------------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2310_00319_gb300 import Plan, costmodel
+    from paper_2310_00319_gb300.tvolap import n_blocks_for
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    wl = workload(args)
+    L, M, P = wl.L, wl.M, 2 * wl.L
+    n_ch, N = wl.n_in, wl.N
+    nb = n_blocks_for(wl.out_len, L)
+    stream = torch.cuda.current_stream(dev)
+
+    plan = Plan(L, M, n_in=n_ch, n_out=wl.n_out, out_to_in=wl.out_to_in,
+                n_slots=wl.irs.shape[0], device=dev)
+    x = torch.from_numpy(wl.x).to(dev)
+    irs = torch.from_numpy(wl.irs).to(dev)
+    sa = torch.from_numpy(wl.sched_a).to(dev)
+    sb = torch.from_numpy(wl.sched_b).to(dev)
+    sal = torch.from_numpy(wl.sched_alpha).to(dev)
+    X = torch.empty((n_ch, nb, P), dtype=torch.complex64, device=dev)
+    Y = torch.empty((wl.n_out, nb, P), dtype=torch.complex64, device=dev)
+    y = torch.empty((wl.n_out, wl.out_len), dtype=torch.float32, device=dev)
+    lib, h = plan.lib, plan.h
+    from paper_2310_00319_gb300.tvolap import _ptr
+    from paper_2310_00319_gb300 import _lib as L_
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        L_.check(lib.tvolap_load_bank(h, 0, irs.shape[0], _ptr(irs), irs.shape[1], irs.shape[1]),
+                 "load_bank")
+        if ev:
+            ev[1].record(stream)
+        L_.check(lib.tvolap_forward_spectra(h, _ptr(x), N, N, nb, _ptr(X)), "forward")
+        if ev:
+            ev[2].record(stream)
+        L_.check(lib.tvolap_mac(h, _ptr(X), nb, _ptr(sa), _ptr(sb), _ptr(sal), sa.shape[1],
+                                _ptr(Y)), "mac")
+        if ev:
+            ev[3].record(stream)
+        L_.check(lib.tvolap_inverse_ola(h, _ptr(Y), nb, _ptr(y), wl.out_len, wl.out_len),
+                 "inverse")
+        if ev:
+            ev[4].record(stream)
+
+    launches_per_step = 4
+    for _ in range(args.warmup):
+        step()
+    plan.check()
+    torch.cuda.synchronize(dev)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(dev.index) as clk:
+        t0.record(stream)
+        for i in range(args.steps):
+            step(evs[i])
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+    elapsed_ms = t0.elapsed_time(t1)
+    stage_ms = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in evs])
+    plan.check()
+    if ws > 1:
+        tt = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+
+    units_per_step = wl.n_out * wl.out_len * ws
+    ms_per_step = elapsed_ms / args.steps
+    value = units_per_step / (ms_per_step * 1e-3)
+
+    # dominant kernel: the Eq. 7 multiply-accumulate, FP32 ALU bound
+    peaks, peak_kind = _peaks()
+    clocks = clk.summary()
+    mac_ms = float(stage_ms[:, 2].mean())
+    flops = mac_terms(nb, M) * P * wl.n_out * costmodel.mac_flops_per_block_bin_partition(True)
+    achieved = flops / (mac_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "traffic": args.traffic, "kernel": "k_mac_signal",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}
+    # the transform stages are memory bound: algorithmic bytes / time vs measured HBM copy
+    bytes_fwd = 4.0 * n_ch * N + 8.0 * P * n_ch * nb
+    bytes_inv = 8.0 * P * wl.n_out * nb + 4.0 * wl.n_out * wl.out_len
+    bytes_bank = 4.0 * irs.numel() + 8.0 * P * M * irs.shape[0]
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    st = stage_ms.mean(0)
+    stages = {
+        "bank_fft": {"ms": round(float(st[0]), 4),
+                     "gbs": round(bytes_bank / (st[0] * 1e-3) / 1e9, 1)},
+        "forward_fft": {"ms": round(float(st[1]), 4),
+                        "gbs": round(bytes_fwd / (st[1] * 1e-3) / 1e9, 1)},
+        "mac": {"ms": round(float(st[2]), 4), "tflops": round(achieved, 3)},
+        "inverse_ola": {"ms": round(float(st[3]), 4),
+                        "gbs": round(bytes_inv / (st[3] * 1e-3) / 1e9, 1)},
+        "hbm_peak_gbs": hbm,
+    }
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name + f"_N{N}_ir{wl.ir_len}", "channels": wl.n_out,
+                   "L": L, "M": M, "fft_len": 4 * L, "ir_len": wl.ir_len,
+                   "stored_irs_per_channel": 8, "filter": "new mix every block",
+                   "samples_per_channel": wl.out_len, "blocks": nb,
+                   "per_gpu_units": wl.n_out * wl.out_len,
+                   "l2": "working set ~1.5 GB >> 129 MB L2; no flush",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roofline, "stages": stages, "peaks": peak_kind,
+        "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+    }
+    if rank == 0 and not args.skip_extras:
+        out["e2e"] = run_e2e(args, plan, wl, dev, stream)
+        out["vs_per_source"] = run_per_source(args, wl, dev, stream, ms_per_step)
+        out["stream"] = run_stream(args, wl, dev, stream)
+    if rank == 0 and not args.skip_extras and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(args, wl, budget_s=args.cpu_seconds)
+    plan.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def run_e2e(args, plan, wl, dev, stream):
+    """Same metric through the public API with host buffers: pinned host inputs
+    copied in, process, output copied back, all inside the timed region."""
+    import torch
+    xh = torch.from_numpy(wl.x).pin_memory()
+    irh = torch.from_numpy(wl.irs).pin_memory()
+    sah = torch.from_numpy(wl.sched_a).pin_memory()
+    sbh = torch.from_numpy(wl.sched_b).pin_memory()
+    salh = torch.from_numpy(wl.sched_alpha).pin_memory()
+    yh = torch.empty((wl.n_out, wl.out_len), dtype=torch.float32).pin_memory()
+    xd, ird = torch.empty_like(xh, device=dev), torch.empty_like(irh, device=dev)
+    sad, sbd = torch.empty_like(sah, device=dev), torch.empty_like(sbh, device=dev)
+    sald = torch.empty_like(salh, device=dev)
+    yd = torch.empty((wl.n_out, wl.out_len), dtype=torch.float32, device=dev)
+
+    def step():
+        for d, s in ((xd, xh), (ird, irh), (sad, sah), (sbd, sbh), (sald, salh)):
+            d.copy_(s, non_blocking=True)
+        plan.load_bank(0, ird)
+        plan.process_signal(xd, sad, sbd, sald, out_len=wl.out_len, out=yd)
+        yh.copy_(yd, non_blocking=True)
+
+    steps = max(3, args.steps // 2)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(dev)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = t0.elapsed_time(t1) / steps
+    h2d = sum(t.numel() * t.element_size() for t in (xh, irh, sah, sbh, salh))
+    d2h = yh.numel() * yh.element_size()
+    return {"value": round(wl.n_out * wl.out_len / (ms * 1e-3), 1), "unit": UNIT,
+            "ms_per_step": round(ms, 4), "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps}
+
+
+def run_per_source(args, wl, dev, stream, batched_ms):
+    """The plain per-source form: one single-channel process_signal call per
+    channel in a Python loop, same kernels, no batching."""
+    import torch
+    from paper_2310_00319_gb300 import Plan
+    plans = []
+    x = torch.from_numpy(wl.x).to(dev)
+    sa = torch.from_numpy(wl.sched_a).to(dev)
+    sb = torch.from_numpy(wl.sched_b).to(dev)
+    sal = torch.from_numpy(wl.sched_alpha).to(dev)
+    irs = torch.from_numpy(wl.irs).to(dev)
+    n_ir = irs.shape[0] // wl.n_out
+    ys = torch.empty((wl.n_out, wl.out_len), dtype=torch.float32, device=dev)
+    p = Plan(wl.L, wl.M, n_in=1, n_out=1, n_slots=n_ir, device=dev)
+    sa_l = (sa - (torch.arange(wl.n_out, device=dev, dtype=torch.int32) * n_ir)[:, None]).contiguous()
+    sb_l = (sb - (torch.arange(wl.n_out, device=dev, dtype=torch.int32) * n_ir)[:, None]).contiguous()
+
+    def step():
+        for c in range(wl.n_out):
+            p.load_bank(0, irs[c * n_ir:(c + 1) * n_ir])
+            p.process_signal(x[c:c + 1], sa_l[c:c + 1], sb_l[c:c + 1], sal[c:c + 1],
+                             out_len=wl.out_len, out=ys[c:c + 1])
+
+    step()
+    torch.cuda.synchronize(dev)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 3
+    t0.record(stream)
+    for _ in range(n):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = t0.elapsed_time(t1) / n
+    p.check()
+    p.close()
+    return {"per_source_ms_per_step": round(ms, 4), "batched_ms_per_step": round(batched_ms, 4),
+            "ratio": round(ms / batched_ms, 3)}
+
+
+def run_stream(args, wl, dev, stream, ticks=600, warm=50):
+    """Streaming ticks (process_block) on the same channels and filters: per
+    tick device time, p50 / p99, against the L / fs deadline."""
+    import torch
+    from paper_2310_00319_gb300 import Plan, costmodel
+    p = Plan(wl.L, wl.M, n_in=wl.n_in, n_out=wl.n_out, out_to_in=wl.out_to_in,
+             n_slots=wl.irs.shape[0], device=dev)
+    p.load_bank(0, torch.from_numpy(wl.irs).to(dev))
+    L = wl.L
+    x = torch.from_numpy(wl.x[:, :(ticks + warm) * L]).to(dev)
+    sa = torch.from_numpy(np.ascontiguousarray(wl.sched_a.T)).to(dev)
+    sb = torch.from_numpy(np.ascontiguousarray(wl.sched_b.T)).to(dev)
+    sal = torch.from_numpy(np.ascontiguousarray(wl.sched_alpha.T)).to(dev)
+    blocks = [x[:, t * L:(t + 1) * L].contiguous() for t in range(ticks + warm)]
+    out = torch.empty((wl.n_out, L), dtype=torch.float32, device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(ticks)]
+    for t in range(warm):
+        p.process_block(blocks[t], out, sa[t], sb[t], sal[t])
+    torch.cuda.synchronize(dev)
+    for i in range(ticks):
+        t = warm + i
+        evs[i][0].record(stream)
+        p.process_block(blocks[t], out, sa[t], sb[t], sal[t])
+        evs[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    p.check()
+    ms = np.array([a.elapsed_time(b) for a, b in evs])
+    p.close()
+    deadline_ms = L / 48000 * 1e3
+    bpt = costmodel.stream_mac_bytes_per_tick(wl.n_out, 2 * L, wl.M, 2)
+    return {"ticks": ticks, "tick_ms_p50": round(float(np.percentile(ms, 50)), 4),
+            "tick_ms_p99": round(float(np.percentile(ms, 99)), 4),
+            "deadline_ms": round(deadline_ms, 4),
+            "channel_samples_per_s": round(wl.n_out * L / (ms.mean() * 1e-3), 1),
+            "mac_bytes_per_tick": bpt,
+            "logical_gbs_per_tick": round(bpt / (ms.mean() * 1e-3) / 1e9, 1)}
+
+
+# --------------------------------------------------------------------------- oracle
+def _oracle_sample(wl, n_samples, channel=0, start=None):
+    import oracle
+    start = wl.out_len // 2 if start is None else start
+    n_idx = np.arange(start, start + n_samples, dtype=np.int64)
+    oc = np.full(n_samples, channel, dtype=np.int32)
+    t = time.perf_counter()
+    oracle.tvolap_samples(wl.x, wl.irs, wl.L, wl.sched_a, wl.sched_b, wl.sched_alpha, oc, n_idx,
+                          out_to_in=wl.out_to_in)
+    return time.perf_counter() - t
+
+
+def cpu_baseline(args, wl, budget_s=15.0):
+    """The FP64 oracle on the host cores: a contiguous run of output samples of
+    one channel in the steady state, sized to about budget_s seconds."""
+    import oracle
+    probe = 256
+    dt = _oracle_sample(wl, probe)
+    n = int(max(probe, min(wl.out_len // 2, probe * budget_s / max(dt, 1e-6))))
+    dt = _oracle_sample(wl, n)
+    return {"value": round(n / dt, 1), "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "seconds": round(dt, 2),
+            "sample": f"{n} consecutive output samples of channel 0 from n={wl.out_len // 2} "
+                      f"(FP64 time-domain oracle, {2 * wl.ir_len} flop-pairs per sample)"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return None
+    import oracle
+    wl = workload(args)
+    probe = 128
+    dt = _oracle_sample(wl, probe)
+    per_step = int(max(probe, probe * args.ref_step_seconds / max(dt, 1e-6)))
+    for _ in range(args.warmup):
+        _oracle_sample(wl, per_step)
+    total = 0.0
+    for _ in range(args.steps):
+        total += _oracle_sample(wl, per_step)
+    value = per_step * args.steps / total
+    return {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": wl.name + f"_N{wl.N}_ir{wl.ir_len}", "channels": wl.n_out,
+                       "L": wl.L, "M": wl.M, "per_step_units": per_step},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{per_step} consecutive output samples of channel 0 "
+                                       "per step (FP64 time-domain oracle)"},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--channels", type=int, default=64)
+    ap.add_argument("--samples", type=int, default=480000)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the multiply-accumulate kernel")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    ap.add_argument("--skip-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        out = run_reference(args)
+    else:
+        out = run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

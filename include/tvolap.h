@@ -1,0 +1,217 @@
+/*
+ * tvolap.h -- C ABI of the GB300 (sm_103a) TVOLAP library.
+ *
+ * Time-variant overlap-add in partitions (arxiv 2310.00319, Section 2): each
+ * input channel is cut into 2L-sample blocks every L samples (Eq. 1), weighted
+ * by a periodic Hann window (Eq. "w_hann"; this library uses the amplitude 1/2
+ * under which hop-L windows sum to one), zero padded to 4L (Eq. 3) and
+ * transformed (Eq. 5). Impulse responses are cut into M partitions of 2L taps
+ * (Eq. 2), padded (Eq. 4) and transformed (Eq. 6). Output block l is
+ *     Y(k, l) = sum_{m<M} H_l(k, m) X(k, l - 2m)                       (Eq. 7)
+ * with H_l the filter current at block l (all partitions exchanged at once,
+ * Section 2), followed by the inverse transform (Eq. 8) and the two-step
+ * overlap-add (Eqs. 9-12, read with the same-parity predecessor l - 2).
+ *
+ * Spectra in this library are taken on the half-bin grid (k + 1/2) / 4L rather
+ * than the paper's k / 4L. Because every product in Eq. 7 is the transform of
+ * a linear convolution shorter than 4L, both grids give the same time-domain
+ * output; the half-bin grid has exactly 2L independent complex bins per real
+ * block (no separate DC/Nyquist bins), stored as interleaved float pairs
+ * (re, im). A spectrum is P = 2L complex values, 8*P bytes.
+ *
+ * Conventions for every call:
+ *  - Pointers named *_dev are device pointers; the caller owns them and keeps
+ *    them valid until the handle's CUDA stream has passed the call.
+ *  - Every call is enqueued on the stream given to tvolap_create and returns
+ *    without waiting for the GPU, unless stated otherwise.
+ *  - Every call returns TVOLAP_OK or a negative tvolap_status. A call that
+ *    returns TVOLAP_ERR_ARG has enqueued nothing and changed nothing.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *  - Schedules index output blocks by t = l + 1: block l = -1 (L zeros of
+ *    history followed by the first L input samples) is entry 0. Output
+ *    samples [0, out_len) need n_blocks = floor((out_len - 1) / L) + 2 entries.
+ *  - A slot index outside [0, tvolap_slot_count) in a schedule or selection
+ *    is replaced on the device by an all-zero filter and recorded; the next
+ *    tvolap_check returns TVOLAP_ERR_ARG.
+ */
+#ifndef TVOLAP_H
+#define TVOLAP_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TVOLAP_API __attribute__((visibility("default")))
+#else
+#define TVOLAP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tvolap_plan *tvolap_t;
+
+typedef enum tvolap_status {
+    TVOLAP_OK = 0,
+    TVOLAP_ERR_ARG = -1,      /* invalid argument (nothing enqueued) */
+    TVOLAP_ERR_OOM = -2,      /* a device allocation failed */
+    TVOLAP_ERR_CUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+    TVOLAP_ERR_STATE = -4,    /* handle is NULL or unusable */
+    TVOLAP_ERR_CAPACITY = -5, /* request exceeds a stated capacity */
+    TVOLAP_ERR_TIMEOUT = -6   /* a bounded device wait gave up */
+} tvolap_status;
+
+/* Human-readable name of a status code (static string, never NULL). */
+TVOLAP_API const char *tvolap_strerror(int status);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+TVOLAP_API int tvolap_version(void);
+
+/*
+ * Create a plan (Section 2: hop L, M partitions of 2L taps, transform length
+ * 4L, c channels processed side by side).
+ *   out         receives the handle
+ *   L           hop; a power of two in [16, 1024]
+ *   partitions  M >= 1; impulse responses may have up to 2*L*M taps
+ *   fft_len     must be 4*L (Eq. 3: double-length zero padding), or 0 for 4*L
+ *   n_in        input channels >= 1
+ *   n_out       output channels >= 1
+ *   out_to_in   host array [n_out]: input channel feeding each output
+ *               (several outputs may share one input, e.g. binaural pairs);
+ *               NULL means identity and requires n_in == n_out
+ *   n_slots     stored filter slots >= 1 shared by all outputs (filled by
+ *               tvolap_load_bank); the plan also keeps one private slot per
+ *               output for tvolap_set_filter, so tvolap_slot_count(h) is
+ *               n_slots + n_out
+ *   stream      cudaStream_t for every call on this handle (NULL = legacy
+ *               default stream)
+ * Allocates device memory for the filter bank, the frequency-domain delay
+ * line and the overlap state; synchronises the stream before returning.
+ * Errors: TVOLAP_ERR_ARG, TVOLAP_ERR_OOM, TVOLAP_ERR_CUDA.
+ */
+TVOLAP_API int tvolap_create(tvolap_t *out, int L, int partitions, int fft_len, int n_in, int n_out,
+                  const int32_t *out_to_in, int n_slots, void *stream);
+
+/* Synchronise the stream and free everything the handle owns. NULL is a no-op. */
+TVOLAP_API int tvolap_destroy(tvolap_t h);
+
+/* Plan geometry: L, M, P = 2L (complex bins per spectrum), channels, slots. */
+TVOLAP_API int tvolap_get_dims(tvolap_t h, int *L, int *M, int *P, int *n_in, int *n_out, int *n_slots);
+
+/* Total addressable filter slots: n_slots + n_out (private set_filter slots). */
+TVOLAP_API int tvolap_slot_count(tvolap_t h);
+
+/*
+ * Zero the streaming state (delay line, input history, overlap state, block
+ * counter) and reset every output's selection to its private slot. The bank
+ * keeps its contents.
+ */
+TVOLAP_API int tvolap_reset(tvolap_t h);
+
+/*
+ * Transform impulse responses into filter slots [first_slot, first_slot+count)
+ * (Eqs. 2, 4, 6): partition m of slot s holds taps [2mL, 2mL + 2L) of
+ * ir_dev[s - first_slot]. Taps at or beyond ir_len are zero.
+ *   ir_dev     device float [count][ir_stride]
+ *   ir_len     taps per response, 1 <= ir_len <= 2*L*M
+ *   ir_stride  floats between consecutive responses, >= ir_len
+ * first_slot + count must not exceed n_slots (the private slots are written
+ * only by tvolap_set_filter).
+ */
+TVOLAP_API int tvolap_load_bank(tvolap_t h, int first_slot, int count, const float *ir_dev, int ir_len,
+                     int64_t ir_stride);
+
+/*
+ * Exchange the filter of one output (Section 2: all partitions at once): the
+ * response is transformed into the output's private slot and selected alone.
+ * Takes effect from the next tvolap_process_block on this handle.
+ */
+TVOLAP_API int tvolap_set_filter(tvolap_t h, int out_ch, const float *ir_dev, int ir_len);
+
+/*
+ * Select the filter of one output for the following streamed blocks:
+ * H = (1 - alpha) * H[slot_a] + alpha * H[slot_b]. A mix of transfer functions
+ * equals the transfer function of the mixed taps (linearity of Eq. 6).
+ */
+TVOLAP_API int tvolap_select(tvolap_t h, int out_ch, int slot_a, int slot_b, float alpha);
+
+/*
+ * Stream one hop (one streaming tick): consume L new samples per input,
+ * emit L samples per output. Tick t processes block l = t - 1 (the previous
+ * L samples of history and the L new ones), so the emitted samples are the
+ * offline output delayed by exactly L samples (block latency 2L in total,
+ * Table 1).
+ *   in_dev    device float [n_in][L]
+ *   out_dev   device float [n_out][L]
+ *   sel_a, sel_b, sel_alpha   optional device arrays [n_out] giving this
+ *             tick's selection (and keeping it for later ticks); NULL keeps
+ *             the current selection. sel_b / sel_alpha may be NULL on their
+ *             own (then b = a, alpha = 0).
+ */
+TVOLAP_API int tvolap_process_block(tvolap_t h, const float *in_dev, float *out_dev, const int32_t *sel_a,
+                         const int32_t *sel_b, const float *sel_alpha);
+
+/*
+ * Whole-signal (offline) TVOLAP; the streaming state is not touched. Every
+ * block of every channel is independent (Eq. 7 has no recurrence), so all run
+ * in parallel: forward transforms, partition MAC, inverse transforms with the
+ * overlap-add.
+ *   x_dev        device float [n_in][x_stride], N valid samples per channel
+ *   sched_a      device int32 [n_out][sched_stride] slot per block (t = l+1)
+ *   sched_b      device int32 [n_out][sched_stride] or NULL (b = a)
+ *   sched_alpha  device float [n_out][sched_stride] or NULL (alpha = 0)
+ *   sched_stride >= n_blocks = floor((out_len - 1) / L) + 2
+ *   y_dev        device float [n_out][y_stride]; samples [0, out_len) written,
+ *                aligned with x (no delay); out_len may exceed N (tail)
+ * Uses a device workspace owned by the handle of
+ * 8 * P * n_blocks * (n_in + n_out) bytes, grown (cudaMalloc) when needed.
+ */
+TVOLAP_API int tvolap_process_signal(tvolap_t h, const float *x_dev, int64_t N, int64_t x_stride,
+                          const int32_t *sched_a, const int32_t *sched_b,
+                          const float *sched_alpha, int64_t sched_stride, float *y_dev,
+                          int64_t out_len, int64_t y_stride);
+
+/* Bytes of workspace tvolap_process_signal needs for out_len samples. */
+TVOLAP_API int64_t tvolap_signal_workspace_bytes(tvolap_t h, int64_t out_len);
+
+/*
+ * Stage 1 of tvolap_process_signal on its own (Eqs. 1, 3, 5): the spectra of
+ * input blocks l = -1 .. n_blocks - 2 of every input channel.
+ *   X_dev  device float2 [n_in][n_blocks][P]
+ */
+TVOLAP_API int tvolap_forward_spectra(tvolap_t h, const float *x_dev, int64_t N, int64_t x_stride,
+                           int n_blocks, float *X_dev);
+
+/*
+ * Stage 2 on its own (Eq. 7 with the block's filter): for every output o and
+ * block t < n_blocks, Y[o][t] = sum_{m < M, t - 2m >= 0} H_t(m) X[in(o)][t - 2m].
+ *   X_dev  device float2 [n_in][n_blocks][P];  Y_dev device float2 [n_out][n_blocks][P]
+ */
+TVOLAP_API int tvolap_mac(tvolap_t h, const float *X_dev, int n_blocks, const int32_t *sched_a,
+               const int32_t *sched_b, const float *sched_alpha, int64_t sched_stride,
+               float *Y_dev);
+
+/*
+ * Stage 3 on its own (Eqs. 8-12): inverse transform of every block's Y and
+ * overlap-add into y[o][0 .. out_len); n_blocks must equal
+ * floor((out_len - 1) / L) + 2.
+ */
+TVOLAP_API int tvolap_inverse_ola(tvolap_t h, const float *Y_dev, int n_blocks, float *y_dev,
+                       int64_t out_len, int64_t y_stride);
+
+/* Copy the M partition spectra of one slot to out_dev (device float2 [M][P]). */
+TVOLAP_API int tvolap_bank_spectra(tvolap_t h, int slot, float *out_dev);
+
+/*
+ * Synchronise the stream and report deferred device-side errors: returns
+ * TVOLAP_ERR_ARG if any kernel since the previous check met an invalid slot
+ * index (the error record is cleared), TVOLAP_ERR_CUDA on a CUDA error,
+ * otherwise TVOLAP_OK.
+ */
+TVOLAP_API int tvolap_check(tvolap_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TVOLAP_H */

@@ -1,0 +1,359 @@
+// C ABI of the TVOLAP library: argument checks, device state, launches.
+// Declarations and the contract of every entry point are in include/tvolap.h.
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "internal.h"
+
+using namespace tvolap;
+
+namespace {
+
+int ilog2_exact(int v)
+{
+    int lg = 0;
+    while ((1 << lg) < v) ++lg;
+    return ((1 << lg) == v) ? lg : -1;
+}
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return TVOLAP_OK;
+    if (e == cudaErrorMemoryAllocation) return TVOLAP_ERR_OOM;
+    return TVOLAP_ERR_CUDA;
+}
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+}
+
+void free_plan(tvolap_plan *h)
+{
+    if (!h) return;
+    void *ptrs[] = {h->tw, h->rot, h->post, h->win, h->bank, h->out_to_in, h->sel_a, h->sel_b,
+                    h->sel_alpha, h->err, h->ring, h->hist, h->ola, h->Ystream, h->ws};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete h;
+}
+
+int64_t blocks_for(const tvolap_plan *h, int64_t out_len)
+{
+    return out_len <= 0 ? 0 : (out_len - 1) / h->L + 2;
+}
+
+// Device memory for process_signal: X [n_in][nb][P] then Y [n_out][nb][P].
+int64_t workspace_bytes(const tvolap_plan *h, int64_t nb)
+{
+    return (int64_t)sizeof(float2) * h->P * nb * (h->n_in + h->n_out);
+}
+
+int ensure_workspace(tvolap_plan *h, size_t bytes)
+{
+    if (bytes <= h->ws_bytes) return TVOLAP_OK;
+    if (h->ws) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&h->ws, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->ws = nullptr;
+        return TVOLAP_ERR_OOM;
+    }
+    h->ws_bytes = bytes;
+    return TVOLAP_OK;
+}
+
+int reset_state(tvolap_plan *h)
+{
+    cudaError_t e;
+    const size_t P = h->P;
+    if ((e = cudaMemsetAsync(h->ring, 0, sizeof(float2) * h->n_in * 2 * h->M * P, h->stream)) ||
+        (e = cudaMemsetAsync(h->hist, 0, sizeof(float) * h->n_in * h->L, h->stream)) ||
+        (e = cudaMemsetAsync(h->ola, 0, sizeof(float) * h->n_out * 3 * h->L, h->stream)) ||
+        (e = cudaMemsetAsync(h->sel_alpha, 0, sizeof(float) * h->n_out, h->stream)))
+        return cuda_status(e);
+    // every output starts on its private (zero) slot
+    int32_t *init = (int32_t *)malloc(sizeof(int32_t) * h->n_out);
+    if (!init) return TVOLAP_ERR_OOM;
+    for (int o = 0; o < h->n_out; ++o) init[o] = h->n_user_slots + o;
+    e = cudaMemcpyAsync(h->sel_a, init, sizeof(int32_t) * h->n_out, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->sel_b, init, sizeof(int32_t) * h->n_out, cudaMemcpyHostToDevice,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // init is pageable and freed below
+    free(init);
+    h->tick = 0;
+    return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tvolap_strerror(int status)
+{
+    switch (status) {
+    case TVOLAP_OK: return "TVOLAP_OK";
+    case TVOLAP_ERR_ARG: return "TVOLAP_ERR_ARG: invalid argument";
+    case TVOLAP_ERR_OOM: return "TVOLAP_ERR_OOM: device allocation failed";
+    case TVOLAP_ERR_CUDA: return "TVOLAP_ERR_CUDA: CUDA runtime or launch failure";
+    case TVOLAP_ERR_STATE: return "TVOLAP_ERR_STATE: invalid handle";
+    case TVOLAP_ERR_CAPACITY: return "TVOLAP_ERR_CAPACITY: capacity exceeded";
+    case TVOLAP_ERR_TIMEOUT: return "TVOLAP_ERR_TIMEOUT: bounded device wait gave up";
+    default: return "TVOLAP: unknown status";
+    }
+}
+
+int tvolap_version(void) { return 10000; }
+
+int tvolap_create(tvolap_t *out, int L, int partitions, int fft_len, int n_in, int n_out,
+                  const int32_t *out_to_in, int n_slots, void *stream)
+{
+    if (!out) return TVOLAP_ERR_ARG;
+    *out = nullptr;
+    const int lgL = ilog2_exact(L);
+    if (lgL < 4 || lgL > 10) return TVOLAP_ERR_ARG;              // L in 16 .. 1024
+    if (partitions < 1 || (fft_len != 0 && fft_len != 4 * L)) return TVOLAP_ERR_ARG;
+    if (n_in < 1 || n_out < 1 || n_slots < 1) return TVOLAP_ERR_ARG;
+    if (!out_to_in && n_in != n_out) return TVOLAP_ERR_ARG;
+    if (out_to_in)
+        for (int o = 0; o < n_out; ++o)
+            if (out_to_in[o] < 0 || out_to_in[o] >= n_in) return TVOLAP_ERR_ARG;
+    if ((int64_t)n_slots + n_out + 1 > (1 << 30)) return TVOLAP_ERR_ARG;
+
+    tvolap_plan *h = new (std::nothrow) tvolap_plan;
+    if (!h) return TVOLAP_ERR_OOM;
+    memset(h, 0, sizeof(*h));
+    h->L = L;
+    h->M = partitions;
+    h->P = 2 * L;
+    h->lgP = lgL + 1;
+    h->n_in = n_in;
+    h->n_out = n_out;
+    h->n_user_slots = n_slots;
+    h->n_slots_total = n_slots + n_out;
+    h->null_slot = n_slots + n_out;
+    h->stream = (cudaStream_t)stream;
+
+    const size_t P = h->P, M = h->M;
+    cudaError_t e;
+    if ((e = dalloc(&h->tw, P)) || (e = dalloc(&h->rot, P)) || (e = dalloc(&h->post, P / 2)) ||
+        (e = dalloc(&h->win, 2 * (size_t)L)) ||
+        (e = dalloc(&h->bank, (size_t)(h->n_slots_total + 1) * M * P)) ||
+        (e = dalloc(&h->out_to_in, (size_t)n_out)) || (e = dalloc(&h->sel_a, (size_t)n_out)) ||
+        (e = dalloc(&h->sel_b, (size_t)n_out)) || (e = dalloc(&h->sel_alpha, (size_t)n_out)) ||
+        (e = dalloc(&h->err, 1)) || (e = dalloc(&h->ring, (size_t)n_in * 2 * M * P)) ||
+        (e = dalloc(&h->hist, (size_t)n_in * L)) || (e = dalloc(&h->ola, (size_t)n_out * 3 * L)) ||
+        (e = dalloc(&h->Ystream, (size_t)n_out * P))) {
+        cudaGetLastError();
+        free_plan(h);
+        return cuda_status(e);
+    }
+    int32_t *o2i = (int32_t *)malloc(sizeof(int32_t) * n_out);
+    if (!o2i) {
+        free_plan(h);
+        return TVOLAP_ERR_OOM;
+    }
+    for (int o = 0; o < n_out; ++o) o2i[o] = out_to_in ? out_to_in[o] : o;
+    e = cudaMemcpyAsync(h->out_to_in, o2i, sizeof(int32_t) * n_out, cudaMemcpyHostToDevice,
+                        h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->bank, 0, sizeof(float2) * (h->n_slots_total + 1) * M * P, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream);
+    if (e == cudaSuccess) e = launch_tables(h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    free(o2i);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(h);
+        return cuda_status(e);
+    }
+    int st = reset_state(h);
+    if (st != TVOLAP_OK) {
+        free_plan(h);
+        return st;
+    }
+    *out = h;
+    return TVOLAP_OK;
+}
+
+int tvolap_destroy(tvolap_t h)
+{
+    if (!h) return TVOLAP_OK;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    free_plan(h);
+    return cuda_status(e);
+}
+
+int tvolap_get_dims(tvolap_t h, int *L, int *M, int *P, int *n_in, int *n_out, int *n_slots)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (L) *L = h->L;
+    if (M) *M = h->M;
+    if (P) *P = h->P;
+    if (n_in) *n_in = h->n_in;
+    if (n_out) *n_out = h->n_out;
+    if (n_slots) *n_slots = h->n_user_slots;
+    return TVOLAP_OK;
+}
+
+int tvolap_slot_count(tvolap_t h)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    return h->n_slots_total;
+}
+
+int tvolap_reset(tvolap_t h)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    return reset_state(h);
+}
+
+int tvolap_load_bank(tvolap_t h, int first_slot, int count, const float *ir_dev, int ir_len,
+                     int64_t ir_stride)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (first_slot < 0 || count < 0 || (int64_t)first_slot + count > h->n_user_slots)
+        return TVOLAP_ERR_ARG;
+    if (count == 0) return TVOLAP_OK;
+    if (!ir_dev || ir_len < 1 || (int64_t)ir_len > 2LL * h->L * h->M || ir_stride < ir_len)
+        return TVOLAP_ERR_ARG;
+    return cuda_status(launch_bank(h, first_slot, count, ir_dev, ir_len, ir_stride));
+}
+
+int tvolap_set_filter(tvolap_t h, int out_ch, const float *ir_dev, int ir_len)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (out_ch < 0 || out_ch >= h->n_out || !ir_dev || ir_len < 1 ||
+        (int64_t)ir_len > 2LL * h->L * h->M)
+        return TVOLAP_ERR_ARG;
+    const int slot = h->n_user_slots + out_ch;
+    cudaError_t e = launch_bank(h, slot, 1, ir_dev, ir_len, ir_len);
+    if (e == cudaSuccess) e = launch_select(h, out_ch, slot, slot, 0.f);
+    return cuda_status(e);
+}
+
+int tvolap_select(tvolap_t h, int out_ch, int slot_a, int slot_b, float alpha)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (out_ch < 0 || out_ch >= h->n_out || slot_a < 0 || slot_a >= h->n_slots_total ||
+        slot_b < 0 || slot_b >= h->n_slots_total)
+        return TVOLAP_ERR_ARG;
+    return cuda_status(launch_select(h, out_ch, slot_a, slot_b, alpha));
+}
+
+int tvolap_process_block(tvolap_t h, const float *in_dev, float *out_dev, const int32_t *sel_a,
+                         const int32_t *sel_b, const float *sel_alpha)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (!in_dev || !out_dev) return TVOLAP_ERR_ARG;
+    if (!sel_a && (sel_b || sel_alpha)) return TVOLAP_ERR_ARG;
+    cudaError_t e = launch_forward_stream(h, in_dev);
+    if (e == cudaSuccess) e = launch_mac_stream(h, sel_a, sel_b, sel_alpha);
+    if (e == cudaSuccess) e = launch_inverse_stream(h, out_dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    h->tick += 1;
+    return TVOLAP_OK;
+}
+
+int64_t tvolap_signal_workspace_bytes(tvolap_t h, int64_t out_len)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (out_len < 0) return TVOLAP_ERR_ARG;
+    return workspace_bytes(h, blocks_for(h, out_len));
+}
+
+int tvolap_process_signal(tvolap_t h, const float *x_dev, int64_t N, int64_t x_stride,
+                          const int32_t *sched_a, const int32_t *sched_b,
+                          const float *sched_alpha, int64_t sched_stride, float *y_dev,
+                          int64_t out_len, int64_t y_stride)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (N < 0 || out_len < 0 || x_stride < N || y_stride < out_len) return TVOLAP_ERR_ARG;
+    if (out_len == 0) return TVOLAP_OK;
+    if ((N > 0 && !x_dev) || !y_dev || !sched_a) return TVOLAP_ERR_ARG;
+    const int64_t nb = blocks_for(h, out_len);
+    if (nb > (int64_t)0x7fffffff / 2 || sched_stride < nb) return TVOLAP_ERR_ARG;
+    int st = ensure_workspace(h, (size_t)workspace_bytes(h, nb));
+    if (st != TVOLAP_OK) return st;
+    float2 *X = reinterpret_cast<float2 *>(h->ws);
+    float2 *Y = X + (int64_t)h->n_in * nb * h->P;
+    cudaError_t e = launch_forward_signal(h, x_dev, N, x_stride, (int)nb, X);
+    if (e == cudaSuccess)
+        e = launch_mac_signal(h, X, (int)nb, sched_a, sched_b, sched_alpha, sched_stride, Y);
+    if (e == cudaSuccess) e = launch_inverse_ola(h, Y, (int)nb, y_dev, out_len, y_stride);
+    return cuda_status(e);
+}
+
+int tvolap_forward_spectra(tvolap_t h, const float *x_dev, int64_t N, int64_t x_stride,
+                           int n_blocks, float *X_dev)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (N < 0 || x_stride < N || n_blocks < 0 || (N > 0 && !x_dev) || (n_blocks > 0 && !X_dev))
+        return TVOLAP_ERR_ARG;
+    return cuda_status(
+        launch_forward_signal(h, x_dev, N, x_stride, n_blocks, reinterpret_cast<float2 *>(X_dev)));
+}
+
+int tvolap_mac(tvolap_t h, const float *X_dev, int n_blocks, const int32_t *sched_a,
+               const int32_t *sched_b, const float *sched_alpha, int64_t sched_stride,
+               float *Y_dev)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (n_blocks < 0 || sched_stride < n_blocks) return TVOLAP_ERR_ARG;
+    if (n_blocks == 0) return TVOLAP_OK;
+    if (!X_dev || !Y_dev || !sched_a) return TVOLAP_ERR_ARG;
+    return cuda_status(launch_mac_signal(h, reinterpret_cast<const float2 *>(X_dev), n_blocks,
+                                         sched_a, sched_b, sched_alpha, sched_stride,
+                                         reinterpret_cast<float2 *>(Y_dev)));
+}
+
+int tvolap_inverse_ola(tvolap_t h, const float *Y_dev, int n_blocks, float *y_dev,
+                       int64_t out_len, int64_t y_stride)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (out_len < 0 || y_stride < out_len || n_blocks != blocks_for(h, out_len))
+        return TVOLAP_ERR_ARG;
+    if (out_len == 0) return TVOLAP_OK;
+    if (!Y_dev || !y_dev) return TVOLAP_ERR_ARG;
+    return cuda_status(launch_inverse_ola(h, reinterpret_cast<const float2 *>(Y_dev), n_blocks,
+                                          y_dev, out_len, y_stride));
+}
+
+int tvolap_bank_spectra(tvolap_t h, int slot, float *out_dev)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (slot < 0 || slot >= h->n_slots_total || !out_dev) return TVOLAP_ERR_ARG;
+    const size_t bytes = sizeof(float2) * (size_t)h->M * h->P;
+    return cuda_status(cudaMemcpyAsync(out_dev, h->bank + (int64_t)slot * h->M * h->P, bytes,
+                                       cudaMemcpyDeviceToDevice, h->stream));
+}
+
+int tvolap_check(tvolap_t h)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    unsigned err = 0;
+    cudaError_t e = cudaMemcpyAsync(&err, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (err) {
+        e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        return TVOLAP_ERR_ARG;
+    }
+    return TVOLAP_OK;
+}
+
+}  // extern "C"

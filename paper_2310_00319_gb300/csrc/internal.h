@@ -1,0 +1,63 @@
+// Internal plan layout and kernel launchers of the TVOLAP library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tvolap.h"
+
+struct tvolap_plan {
+    int L, M, P;                  // hop, partitions, complex bins per spectrum (2L)
+    int lgP;                      // log2(P)
+    int n_in, n_out;
+    int n_user_slots;             // slots written by tvolap_load_bank
+    int n_slots_total;            // user + one private slot per output
+    int null_slot;                // all-zero slot that replaces invalid indices
+    cudaStream_t stream;
+
+    // transform tables (FP32, generated in FP64 on the device)
+    float2 *tw;                   // [P]   e^{-2 pi i n / P}
+    float2 *rot;                  // [P]   e^{-i pi r / P}
+    float2 *post;                 // [P/2] e^{-i pi (2k+1) / 2P}
+    float *win;                   // [2L]  (1 - cos(pi n / L)) / 2
+
+    float2 *bank;                 // [n_slots_total + 1][M][P]
+    int32_t *out_to_in;           // [n_out]
+    int32_t *sel_a, *sel_b;       // [n_out] current selection (streaming)
+    float *sel_alpha;             // [n_out]
+    unsigned int *err;            // [1] device error record (bit 0: invalid slot)
+
+    // streaming state
+    float2 *ring;                 // [n_in][2M][P] frequency-domain delay line
+    float *hist;                  // [n_in][L] previous L input samples
+    float *ola;                   // [n_out][3L] pending overlap-add sums
+    float2 *Ystream;              // [n_out][P] this tick's output spectra
+    int64_t tick;
+
+    // process_signal workspace
+    void *ws;
+    size_t ws_bytes;
+};
+
+namespace tvolap {
+
+// kernels_fft.cu
+cudaError_t launch_tables(tvolap_plan *h);
+cudaError_t launch_forward_signal(tvolap_plan *h, const float *x, int64_t N, int64_t x_stride,
+                                  int n_blocks, float2 *X);
+cudaError_t launch_bank(tvolap_plan *h, int first_slot, int count, const float *ir, int ir_len,
+                        int64_t ir_stride);
+cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, float *y,
+                               int64_t out_len, int64_t y_stride);
+cudaError_t launch_forward_stream(tvolap_plan *h, const float *in);
+cudaError_t launch_inverse_stream(tvolap_plan *h, float *out);
+
+// kernels_mac.cu
+cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, const int32_t *sa,
+                              const int32_t *sb, const float *sal, int64_t sched_stride,
+                              float2 *Y);
+cudaError_t launch_mac_stream(tvolap_plan *h, const int32_t *sa, const int32_t *sb,
+                              const float *sal);
+cudaError_t launch_select(tvolap_plan *h, int out_ch, int a, int b, float alpha);
+
+}  // namespace tvolap

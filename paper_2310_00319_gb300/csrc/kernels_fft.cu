@@ -1,0 +1,395 @@
+// Transform kernels of the TVOLAP path (sm_103a):
+//   k_tables            FP64-generated FP32 twiddle, rotation and window tables
+//   k_forward_signal    Eqs. 1, 3, 5 for every block of every input channel
+//   k_bank              Eqs. 2, 4, 6 for every partition of a set of responses
+//   k_inverse_ola       Eq. 8 and the overlap-add of Eqs. 9-12, offline
+//   k_forward_stream    one new block per input into the delay line
+//   k_inverse_stream    one block per output, overlap-add against the state
+// Every transform is P = 2L complex points (see fft_core.cuh); T = P/8 threads
+// run one transform, F = max(1, 256/T) transforms share a 256-thread CTA.
+#include "fft_core.cuh"
+#include "internal.h"
+
+namespace tvolap {
+
+namespace {
+
+template <int P>
+struct Geo {
+    static constexpr int T = P / 8;                    // threads per transform
+    static constexpr int F = (256 / T) > 0 ? 256 / T : 1;   // transforms per CTA
+    static constexpr int THREADS = T * F;
+};
+
+__global__ void k_tables(float2 *tw, float2 *rot, float2 *post, float *win, int L)
+{
+    const int P = 2 * L;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(2.0 * (double)i / (double)P, &s, &c);      // e^{-2 pi i n / P}
+        tw[i] = make_float2((float)c, (float)-s);
+        sincospi((double)i / (double)P, &s, &c);            // e^{-i pi r / P}
+        rot[i] = make_float2((float)c, (float)-s);
+        if (i < P / 2) {
+            sincospi((2.0 * i + 1.0) / (2.0 * P), &s, &c);  // W_{4L}^{k + 1/2}
+            post[i] = make_float2((float)c, (float)-s);
+        }
+        // periodic Hann of length 2L with amplitude 1/2 (hop-L windows sum to 1)
+        win[i] = (float)(0.5 * (1.0 - cospi((double)i / (double)L)));
+    }
+}
+
+// Forward real transform of one zero-padded block whose first 2L samples are
+// given by src(n) (n < 2L): fills A, runs the FFT, splits into X via st.
+template <int P, class Src, class Store>
+__device__ __forceinline__ void forward_block(float2 *A, float2 *B, int j, bool active, Src src,
+                                              const float2 *__restrict__ rot,
+                                              const float2 *__restrict__ post,
+                                              const float2 *__restrict__ tw, Store st)
+{
+    constexpr int T = P / 8;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int r = j + s * T;
+        float2 z = make_float2(0.f, 0.f);
+        if (s < 4 && active) {                 // r < P/2 = L; the upper half is the zero padding
+            z = cmul(src(2 * r), __ldg(rot + r));
+        }
+        A[r] = z;
+    }
+    __syncthreads();
+    float2 *Z = fft_complex<P, false>(A, B, j, tw);
+    split_forward<P>(Z, j, post, st);
+}
+
+template <int LG>
+__global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
+k_forward_signal(const float *__restrict__ x, int64_t N, int64_t x_stride, int L, int n_blocks,
+                 int64_t total, const float *__restrict__ win, const float2 *__restrict__ rot,
+                 const float2 *__restrict__ post, const float2 *__restrict__ tw,
+                 float2 *__restrict__ X)
+{
+    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F;
+    extern __shared__ float2 sm[];
+    const int f = threadIdx.x / T, j = threadIdx.x % T;
+    float2 *A = sm + f * P, *B = sm + (F + f) * P;
+    const int64_t g = (int64_t)blockIdx.x * F + f;     // transform = (channel, block)
+    const bool active = g < total;
+    const int64_t c = active ? g / n_blocks : 0;
+    const int64_t t = active ? g % n_blocks : 0;
+    const int64_t start = (t - 1) * (int64_t)L;        // block l = t - 1 starts at l*L
+    const float *xc = x + c * x_stride;
+    auto src = [&](int n) {
+        const int64_t i0 = start + n;
+        const float a = (i0 >= 0 && i0 < N) ? __ldg(xc + i0) : 0.f;
+        const float b = (i0 + 1 >= 0 && i0 + 1 < N) ? __ldg(xc + i0 + 1) : 0.f;
+        return make_float2(a * __ldg(win + n), b * __ldg(win + n + 1));
+    };
+    float2 *Xo = X + g * P;
+    forward_block<P>(A, B, j, active, src, rot, post, tw, [&](int k, float2 v) {
+        if (active) Xo[k] = v;
+    });
+}
+
+template <int LG>
+__global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
+k_bank(const float *__restrict__ ir, int ir_len, int64_t ir_stride, int M, int L, int64_t total,
+       const float2 *__restrict__ rot, const float2 *__restrict__ post,
+       const float2 *__restrict__ tw, float2 *__restrict__ bank_out)
+{
+    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F;
+    extern __shared__ float2 sm[];
+    const int f = threadIdx.x / T, j = threadIdx.x % T;
+    float2 *A = sm + f * P, *B = sm + (F + f) * P;
+    const int64_t g = (int64_t)blockIdx.x * F + f;     // transform = (response, partition)
+    const bool active = g < total;
+    const int64_t s = active ? g / M : 0;
+    const int64_t m = active ? g % M : 0;
+    const float *h = ir + s * ir_stride;
+    const int64_t base = 2 * m * (int64_t)L;            // partition m: taps [2mL, 2mL + 2L)
+    auto src = [&](int n) {
+        const int64_t i0 = base + n;
+        const float a = (i0 < ir_len) ? __ldg(h + i0) : 0.f;
+        const float b = (i0 + 1 < ir_len) ? __ldg(h + i0 + 1) : 0.f;
+        return make_float2(a, b);
+    };
+    float2 *Ho = bank_out + g * P;                     // slots are consecutive [s][m][P]
+    forward_block<P>(A, B, j, active, src, rot, post, tw, [&](int k, float2 v) {
+        if (active) Ho[k] = v;
+    });
+}
+
+// Offline inverse + overlap-add. CTA (segment, output channel) owns output
+// samples [s0, s0 + seg*L) and transforms every block that reaches them
+// (l = s0/L - 3 .. s0/L + seg - 1), F at a time; each output sample sums its
+// contributions in increasing block order, so the result does not depend on
+// the tiling.
+template <int LG>
+__global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
+k_inverse_ola(const float2 *__restrict__ Y, int n_blocks, int L, int seg, float *__restrict__ y,
+              int64_t out_len, int64_t y_stride, const float2 *__restrict__ rot,
+              const float2 *__restrict__ post, const float2 *__restrict__ tw)
+{
+    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F;
+    extern __shared__ float2 sm[];
+    float *acc = reinterpret_cast<float *>(sm + 2 * F * P);
+    const int f = threadIdx.x / T, j = threadIdx.x % T;
+    float2 *A = sm + f * P, *B = sm + (F + f) * P;
+    const int o = blockIdx.y;
+    const int64_t tile0 = (int64_t)blockIdx.x * seg;    // first output hop of the segment
+    const int64_t s0 = tile0 * L;
+    const int nseg = seg * L;
+    for (int i = threadIdx.x; i < nseg; i += blockDim.x) acc[i] = 0.f;
+    const float2 *Yo = Y + (int64_t)o * n_blocks * P;
+    const int64_t t_lo = tile0 - 2 > 0 ? tile0 - 2 : 0;
+    int64_t t_hi = tile0 + seg;
+    if (t_hi > n_blocks - 1) t_hi = n_blocks - 1;
+    const float inv_p = 1.0f / (float)P;
+    for (int64_t tb = t_lo; tb <= t_hi; tb += F) {
+        const int64_t t = tb + f;
+        const bool active = t <= t_hi;
+        const float2 *Yt = Yo + (active ? t : 0) * P;
+        merge_inverse<P>(A, j, post, [&](int k) {
+            return active ? Yt[k] : make_float2(0.f, 0.f);
+        });
+        __syncthreads();
+        float2 *Z = fft_complex<P, true>(A, B, j, tw);
+        // undo the pre-rotation and scale: y(2r) + i y(2r+1) = Z(r) e^{+i pi r/P} / P
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int r = j + s * T;
+            Z[r] = cscale(cmulc(Z[r], __ldg(rot + r)), inv_p);
+        }
+        __syncthreads();
+        // overlap-add: the round's blocks cover samples [(tb-1)L, (tb+F-1)L + 4L)
+        const float2 *Zbase = Z - f * P;               // all transforms end in the same half
+        const int64_t w0 = (tb - 1) * L;               // first sample of block tb
+        const int span = (F + 3) * L;
+        for (int p = threadIdx.x; p < span; p += blockDim.x) {
+            const int64_t n = w0 + p;                  // absolute sample
+            const int64_t a = n - s0;                  // index in acc
+            if (a < 0 || a >= nseg) continue;
+            float v = acc[a];
+#pragma unroll 4
+            for (int ff = 0; ff < F; ++ff) {
+                if (tb + ff > t_hi) break;
+                const int i = p - ff * L;              // position within block tb+ff
+                if (i >= 0 && i < 4 * L) v += reinterpret_cast<const float *>(Zbase + ff * P)[i];
+            }
+            acc[a] = v;
+        }
+        __syncthreads();
+    }
+    float *yo = y + (int64_t)o * y_stride;
+    for (int i = threadIdx.x; i < nseg; i += blockDim.x) {
+        const int64_t n = s0 + i;
+        if (n < out_len) yo[n] = acc[i];
+    }
+}
+
+// Streaming forward: one block per input channel from the L samples of
+// history and the L new samples; spectrum into delay-line slot tick mod 2M.
+template <int LG>
+__global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
+k_forward_stream(const float *__restrict__ in, float *__restrict__ hist, int L, int n_in, int R,
+                 int slot, const float *__restrict__ win, const float2 *__restrict__ rot,
+                 const float2 *__restrict__ post, const float2 *__restrict__ tw,
+                 float2 *__restrict__ ring)
+{
+    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F;
+    extern __shared__ float2 sm[];
+    const int f = threadIdx.x / T, j = threadIdx.x % T;
+    float2 *A = sm + f * P, *B = sm + (F + f) * P;
+    const int c = blockIdx.x * F + f;
+    const bool active = c < n_in;
+    const float *hc = hist + (int64_t)(active ? c : 0) * L;
+    const float *ic = in + (int64_t)(active ? c : 0) * L;
+    auto src = [&](int n) {       // n even, so n and n + 1 lie on the same side of L
+        const float *p = (n < L) ? (hc + n) : (ic + n - L);
+        return make_float2(p[0] * __ldg(win + n), p[1] * __ldg(win + n + 1));
+    };
+    float2 *Xo = ring + ((int64_t)(active ? c : 0) * R + slot) * P;
+    forward_block<P>(A, B, j, active, src, rot, post, tw, [&](int k, float2 v) {
+        if (active) Xo[k] = v;
+    });
+    // history reads happened before the first barrier inside forward_block
+    if (active) {
+        float *hw = hist + (int64_t)c * L;
+        for (int i = j; i < L; i += T) hw[i] = ic[i];
+    }
+}
+
+// Streaming inverse: output block -> L samples, with the 3L pending sums.
+template <int LG>
+__global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
+k_inverse_stream(const float2 *__restrict__ Ys, float *__restrict__ ola, float *__restrict__ out,
+                 int L, int n_out, const float2 *__restrict__ rot, const float2 *__restrict__ post,
+                 const float2 *__restrict__ tw)
+{
+    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F;
+    extern __shared__ float2 sm[];
+    const int f = threadIdx.x / T, j = threadIdx.x % T;
+    float2 *A = sm + f * P, *B = sm + (F + f) * P;
+    const int o = blockIdx.x * F + f;
+    const bool active = o < n_out;
+    const float2 *Yo = Ys + (int64_t)(active ? o : 0) * P;
+    merge_inverse<P>(A, j, post, [&](int k) { return active ? Yo[k] : make_float2(0.f, 0.f); });
+    __syncthreads();
+    float2 *Z = fft_complex<P, true>(A, B, j, tw);
+    const float inv_p = 1.0f / (float)P;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int r = j + s * T;
+        Z[r] = cscale(cmulc(Z[r], __ldg(rot + r)), inv_p);
+    }
+    __syncthreads();
+    const float *yb = reinterpret_cast<const float *>(Z);
+    float *st = ola + (int64_t)(active ? o : 0) * 3 * L;
+    float *ou = out + (int64_t)(active ? o : 0) * L;
+    // read every pending sum this thread rewrites before any thread writes;
+    // T = L/4 threads cover the 3L pending sums in exactly 12 steps
+    float keep[12];
+#pragma unroll
+    for (int u = 0; u < 12; ++u) {
+        const int i = j + u * T;
+        float v = yb[i + L];
+        if (i < 2 * L) v += st[i + L];
+        keep[u] = v;
+    }
+    if (active)
+        for (int i = j; i < L; i += T) ou[i] = st[i] + yb[i];
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int u = 0; u < 12; ++u) st[j + u * T] = keep[u];
+    }
+}
+
+template <int LG>
+size_t smem_fft()
+{
+    constexpr int P = 1 << LG;
+    return (size_t)2 * Geo<P>::F * P * sizeof(float2);
+}
+
+// Segment length (output hops per CTA) of the offline inverse.
+int inverse_seg(int L)
+{
+    int seg = 12288 / L - 3;            // about 48 KB of accumulator
+    if (seg > 29) seg = 29;
+    if (seg < 4) seg = 4;
+    return seg;
+}
+
+}  // namespace
+
+cudaError_t launch_tables(tvolap_plan *h)
+{
+    k_tables<<<(h->P + 255) / 256, 256, 0, h->stream>>>(h->tw, h->rot, h->post, h->win, h->L);
+    return cudaGetLastError();
+}
+
+#define TVOLAP_DISPATCH(LGV, ...)             \
+    switch (LGV) {                            \
+    case 5: { constexpr int LG = 5; __VA_ARGS__; } break;   \
+    case 6: { constexpr int LG = 6; __VA_ARGS__; } break;   \
+    case 7: { constexpr int LG = 7; __VA_ARGS__; } break;   \
+    case 8: { constexpr int LG = 8; __VA_ARGS__; } break;   \
+    case 9: { constexpr int LG = 9; __VA_ARGS__; } break;   \
+    case 10: { constexpr int LG = 10; __VA_ARGS__; } break; \
+    case 11: { constexpr int LG = 11; __VA_ARGS__; } break; \
+    default: return cudaErrorInvalidValue;    \
+    }
+
+template <class Kern>
+static cudaError_t set_smem(Kern k, size_t bytes)
+{
+    if (bytes > 48 * 1024)
+        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaSuccess;
+}
+
+cudaError_t launch_forward_signal(tvolap_plan *h, const float *x, int64_t N, int64_t x_stride,
+                                  int n_blocks, float2 *X)
+{
+    const int64_t total = (int64_t)h->n_in * n_blocks;
+    if (total == 0) return cudaSuccess;
+    TVOLAP_DISPATCH(h->lgP, {
+        constexpr int P = 1 << LG;
+        const int64_t grid = (total + Geo<P>::F - 1) / Geo<P>::F;
+        const size_t sm = smem_fft<LG>();
+        cudaError_t e = set_smem(k_forward_signal<LG>, sm);
+        if (e != cudaSuccess) return e;
+        k_forward_signal<LG><<<(unsigned)grid, Geo<P>::THREADS, sm, h->stream>>>(
+            x, N, x_stride, h->L, n_blocks, total, h->win, h->rot, h->post, h->tw, X);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bank(tvolap_plan *h, int first_slot, int count, const float *ir, int ir_len,
+                        int64_t ir_stride)
+{
+    const int64_t total = (int64_t)count * h->M;
+    if (total == 0) return cudaSuccess;
+    float2 *dst = h->bank + (int64_t)first_slot * h->M * h->P;
+    TVOLAP_DISPATCH(h->lgP, {
+        constexpr int P = 1 << LG;
+        const int64_t grid = (total + Geo<P>::F - 1) / Geo<P>::F;
+        const size_t sm = smem_fft<LG>();
+        cudaError_t e = set_smem(k_bank<LG>, sm);
+        if (e != cudaSuccess) return e;
+        k_bank<LG><<<(unsigned)grid, Geo<P>::THREADS, sm, h->stream>>>(
+            ir, ir_len, ir_stride, h->M, h->L, total, h->rot, h->post, h->tw, dst);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, float *y,
+                               int64_t out_len, int64_t y_stride)
+{
+    if (out_len <= 0) return cudaSuccess;
+    const int seg = inverse_seg(h->L);
+    const int64_t n_seg = (out_len + (int64_t)seg * h->L - 1) / ((int64_t)seg * h->L);
+    TVOLAP_DISPATCH(h->lgP, {
+        constexpr int P = 1 << LG;
+        const size_t sm = smem_fft<LG>() + (size_t)seg * h->L * sizeof(float);
+        cudaError_t e = set_smem(k_inverse_ola<LG>, sm);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)n_seg, (unsigned)h->n_out);
+        k_inverse_ola<LG><<<grid, Geo<P>::THREADS, sm, h->stream>>>(
+            Y, n_blocks, h->L, seg, y, out_len, y_stride, h->rot, h->post, h->tw);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_stream(tvolap_plan *h, const float *in)
+{
+    const int R = 2 * h->M;
+    const int slot = (int)(h->tick % R);
+    TVOLAP_DISPATCH(h->lgP, {
+        constexpr int P = 1 << LG;
+        const int grid = (h->n_in + Geo<P>::F - 1) / Geo<P>::F;
+        const size_t sm = smem_fft<LG>();
+        cudaError_t e = set_smem(k_forward_stream<LG>, sm);
+        if (e != cudaSuccess) return e;
+        k_forward_stream<LG><<<grid, Geo<P>::THREADS, sm, h->stream>>>(
+            in, h->hist, h->L, h->n_in, R, slot, h->win, h->rot, h->post, h->tw, h->ring);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_stream(tvolap_plan *h, float *out)
+{
+    TVOLAP_DISPATCH(h->lgP, {
+        constexpr int P = 1 << LG;
+        const int grid = (h->n_out + Geo<P>::F - 1) / Geo<P>::F;
+        const size_t sm = smem_fft<LG>();
+        cudaError_t e = set_smem(k_inverse_stream<LG>, sm);
+        if (e != cudaSuccess) return e;
+        k_inverse_stream<LG><<<grid, Geo<P>::THREADS, sm, h->stream>>>(
+            h->Ystream, h->ola, out, h->L, h->n_out, h->rot, h->post, h->tw);
+    });
+    return cudaGetLastError();
+}
+
+}  // namespace tvolap

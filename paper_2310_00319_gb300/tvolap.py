@@ -1,0 +1,205 @@
+"""Python face of the TVOLAP C ABI (include/tvolap.h).
+
+Thin: it checks tensor devices, dtypes and shapes, passes raw device
+pointers and the plan's CUDA stream to the C library, and returns tensors.
+PyTorch only supplies device memory and streams; every step of the method runs
+in the library's kernels. Spectra are complex64 tensors of P = 2L bins on the
+half-bin grid (k + 1/2) / 4L.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _need(t, dtype, device, name, ndim=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.device != device:
+        raise ValueError(f"{name} must be on {device}, got {t.device}")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dims, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def n_blocks_for(out_len: int, L: int) -> int:
+    """Schedule entries for output samples [0, out_len): t = l + 1, l = -1 ..
+    floor((out_len - 1) / L)."""
+    return 0 if out_len <= 0 else (out_len - 1) // L + 2
+
+
+class Plan:
+    """One TVOLAP plan: hop L, M partitions, n_in inputs, n_out outputs,
+    n_slots stored filters. Calls run on ``stream`` (default: the current
+    torch stream of ``device`` at creation)."""
+
+    def __init__(self, L: int, M: int, n_in: int = 1, n_out: int | None = None,
+                 out_to_in=None, n_slots: int = 1, device=None, stream=None):
+        self.lib = _lib.load()
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.type != "cuda":
+            raise ValueError("TVOLAP plans live on a CUDA device")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        n_out = n_in if n_out is None else n_out
+        self.L, self.M, self.P = int(L), int(M), 2 * int(L)
+        self.n_in, self.n_out, self.n_slots = int(n_in), int(n_out), int(n_slots)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            o2i = None
+            if out_to_in is not None:
+                vals = [int(v) for v in out_to_in]
+                if len(vals) != n_out:
+                    raise ValueError("out_to_in must have n_out entries")
+                o2i = (ctypes.c_int32 * n_out)(*vals)
+            h = ctypes.c_void_p()
+            st = self.lib.tvolap_create(ctypes.byref(h), self.L, self.M, 4 * self.L, self.n_in,
+                                        self.n_out, o2i, self.n_slots,
+                                        ctypes.c_void_p(self.stream.cuda_stream))
+            _lib.check(st, "tvolap_create")
+        self.h = h
+        self.out_to_in = list(out_to_in) if out_to_in is not None else list(range(n_out))
+
+    # ------------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            with torch.cuda.device(self.device):
+                _lib.check(self.lib.tvolap_destroy(self.h), "tvolap_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _call(self, name, *args):
+        with torch.cuda.device(self.device):
+            return _lib.check(getattr(self.lib, name)(self.h, *args), name)
+
+    @property
+    def slot_count(self) -> int:
+        return self._call("tvolap_slot_count")
+
+    def reset(self):
+        self._call("tvolap_reset")
+
+    def check(self):
+        """Synchronise and raise if a kernel met an invalid slot index."""
+        self._call("tvolap_check")
+
+    # ------------------------------------------------------------------ filters
+    def load_bank(self, first_slot: int, irs: torch.Tensor):
+        """Transform irs [count, ir_len] (float32, on device) into slots
+        first_slot .. first_slot + count - 1."""
+        irs = _need(irs, torch.float32, self.device, "irs", 2)
+        self._call("tvolap_load_bank", int(first_slot), irs.shape[0], _ptr(irs), irs.shape[1],
+                   irs.shape[1])
+
+    def set_filter(self, out_ch: int, ir: torch.Tensor):
+        ir = _need(ir, torch.float32, self.device, "ir", 1)
+        self._call("tvolap_set_filter", int(out_ch), _ptr(ir), ir.shape[0])
+
+    def select(self, out_ch: int, slot_a: int, slot_b: int | None = None, alpha: float = 0.0):
+        slot_b = slot_a if slot_b is None else slot_b
+        self._call("tvolap_select", int(out_ch), int(slot_a), int(slot_b), float(alpha))
+
+    def bank_spectra(self, slot: int) -> torch.Tensor:
+        out = torch.empty((self.M, self.P), dtype=torch.complex64, device=self.device)
+        self._call("tvolap_bank_spectra", int(slot), _ptr(out))
+        return out
+
+    # ------------------------------------------------------------------ streaming
+    def process_block(self, x: torch.Tensor, out: torch.Tensor | None = None, sel_a=None,
+                      sel_b=None, sel_alpha=None) -> torch.Tensor:
+        """One hop: x [n_in, L] -> [n_out, L] (the offline output delayed by L)."""
+        x = _need(x, torch.float32, self.device, "x", 2)
+        if tuple(x.shape) != (self.n_in, self.L):
+            raise ValueError(f"x must be [{self.n_in}, {self.L}]")
+        if out is None:
+            out = torch.empty((self.n_out, self.L), dtype=torch.float32, device=self.device)
+        _need(out, torch.float32, self.device, "out", 2)
+        for t, nm, dt in ((sel_a, "sel_a", torch.int32), (sel_b, "sel_b", torch.int32),
+                          (sel_alpha, "sel_alpha", torch.float32)):
+            if t is not None:
+                _need(t, dt, self.device, nm, 1)
+                if t.shape[0] != self.n_out:
+                    raise ValueError(f"{nm} must have n_out entries")
+        self._call("tvolap_process_block", _ptr(x), _ptr(out), _ptr(sel_a), _ptr(sel_b),
+                   _ptr(sel_alpha))
+        return out
+
+    # ------------------------------------------------------------------ offline
+    def _sched(self, sched_a, sched_b, sched_alpha, nb):
+        sched_a = _need(sched_a, torch.int32, self.device, "sched_a", 2)
+        if sched_a.shape[0] != self.n_out or sched_a.shape[1] < nb:
+            raise ValueError(f"sched_a must be [{self.n_out}, >= {nb}]")
+        stride = sched_a.shape[1]
+        for t, nm, dt in ((sched_b, "sched_b", torch.int32),
+                          (sched_alpha, "sched_alpha", torch.float32)):
+            if t is not None:
+                _need(t, dt, self.device, nm, 2)
+                if tuple(t.shape) != tuple(sched_a.shape):
+                    raise ValueError(f"{nm} must match sched_a's shape")
+        return sched_a, sched_b, sched_alpha, stride
+
+    def process_signal(self, x: torch.Tensor, sched_a, sched_b=None, sched_alpha=None,
+                       out_len: int | None = None, out: torch.Tensor | None = None):
+        """Offline TVOLAP of x [n_in, N] -> y [n_out, out_len] (aligned with x)."""
+        x = _need(x, torch.float32, self.device, "x", 2)
+        if x.shape[0] != self.n_in:
+            raise ValueError(f"x must have {self.n_in} rows")
+        N = x.shape[1]
+        out_len = N if out_len is None else int(out_len)
+        nb = n_blocks_for(out_len, self.L)
+        sa, sb, sal, stride = self._sched(sched_a, sched_b, sched_alpha, nb)
+        if out is None:
+            out = torch.empty((self.n_out, out_len), dtype=torch.float32, device=self.device)
+        _need(out, torch.float32, self.device, "out", 2)
+        if out.shape[0] != self.n_out or out.shape[1] < out_len:
+            raise ValueError("out too small")
+        self._call("tvolap_process_signal", _ptr(x), N, N, _ptr(sa), _ptr(sb), _ptr(sal),
+                   stride, _ptr(out), out_len, out.shape[1])
+        return out
+
+    def workspace_bytes(self, out_len: int) -> int:
+        return self._call("tvolap_signal_workspace_bytes", int(out_len))
+
+    def forward_spectra(self, x: torch.Tensor, n_blocks: int) -> torch.Tensor:
+        """X [n_in, n_blocks, P] of input blocks l = -1 .. n_blocks - 2."""
+        x = _need(x, torch.float32, self.device, "x", 2)
+        X = torch.empty((self.n_in, n_blocks, self.P), dtype=torch.complex64, device=self.device)
+        self._call("tvolap_forward_spectra", _ptr(x), x.shape[1], x.shape[1], int(n_blocks),
+                   _ptr(X))
+        return X
+
+    def mac(self, X: torch.Tensor, sched_a, sched_b=None, sched_alpha=None) -> torch.Tensor:
+        X = _need(X, torch.complex64, self.device, "X", 3)
+        nb = X.shape[1]
+        sa, sb, sal, stride = self._sched(sched_a, sched_b, sched_alpha, nb)
+        Y = torch.empty((self.n_out, nb, self.P), dtype=torch.complex64, device=self.device)
+        self._call("tvolap_mac", _ptr(X), nb, _ptr(sa), _ptr(sb), _ptr(sal), stride, _ptr(Y))
+        return Y
+
+    def inverse_ola(self, Y: torch.Tensor, out_len: int) -> torch.Tensor:
+        Y = _need(Y, torch.complex64, self.device, "Y", 3)
+        y = torch.empty((self.n_out, out_len), dtype=torch.float32, device=self.device)
+        self._call("tvolap_inverse_ola", _ptr(Y), Y.shape[1], _ptr(y), int(out_len), int(out_len))
+        return y

@@ -1,0 +1,114 @@
+"""C-ABI library checks that need no GPU: it builds, loads, exports every
+symbol include/tvolap.h declares, and rejects bad arguments before touching
+CUDA. Plus the paper's operation-count model against Tables 1-2."""
+import ctypes
+import json
+import os
+import subprocess
+
+import pytest
+
+from paper_2310_00319_gb300 import _lib, build, costmodel
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    syms = _lib.header_symbols()
+    for s in ["tvolap_create", "tvolap_set_filter", "tvolap_process_block",
+              "tvolap_process_signal", "tvolap_load_bank", "tvolap_destroy"]:
+        assert s in syms
+    assert sorted(_lib.SIGNATURES) == syms
+
+
+def test_library_exports_every_header_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.lib_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for s in _lib.header_symbols():
+        assert s in exported, s
+        assert hasattr(lib, s)
+    # nothing else of ours leaks out of the library
+    ours = {e for e in exported if e.startswith("tvolap")}
+    assert ours == set(_lib.header_symbols())
+
+
+def test_sm103a_only(lib):
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_strerror_and_version(lib):
+    assert lib.tvolap_strerror(0) == b"TVOLAP_OK"
+    assert b"TVOLAP_ERR_ARG" in lib.tvolap_strerror(-1)
+    assert lib.tvolap_version() >= 10000
+
+
+@pytest.mark.parametrize("args", [
+    (0, 4, 0, 1, 1, 1),        # L = 0
+    (24, 4, 0, 1, 1, 1),       # L not a power of two
+    (2048, 4, 0, 1, 1, 1),     # L too large
+    (64, 0, 0, 1, 1, 1),       # M = 0
+    (64, 4, 128, 1, 1, 1),     # fft_len != 4L
+    (64, 4, 0, 0, 1, 1),       # no inputs
+    (64, 4, 0, 2, 3, 1),       # n_in != n_out without routing
+    (64, 4, 0, 1, 1, 0),       # no slots
+])
+def test_create_rejects_bad_arguments_without_gpu(lib, args):
+    L, M, fl, ni, no, ns = args
+    h = ctypes.c_void_p()
+    st = lib.tvolap_create(ctypes.byref(h), L, M, fl, ni, no, None, ns, None)
+    assert st == -1
+    assert not h.value
+
+
+def test_bad_routing_rejected(lib):
+    h = ctypes.c_void_p()
+    o2i = (ctypes.c_int32 * 2)(0, 5)
+    assert lib.tvolap_create(ctypes.byref(h), 64, 2, 0, 2, 2, o2i, 1, None) == -1
+
+
+def test_null_handle_calls(lib):
+    assert lib.tvolap_destroy(None) == 0
+    assert lib.tvolap_check(None) == -4
+    assert lib.tvolap_reset(None) == -4
+    assert lib.tvolap_process_block(None, None, None, None, None, None) == -4
+
+
+def test_paper_op_counts_tables():
+    """Section 3 arithmetic and Tables 1-2 (tests/golden/paper_tables.json)."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_tables.json")))
+    t1, t2 = g["table1"], g["table2"]
+    fs = g["fs"]
+    assert costmodel.mflops(costmodel.direct_ops_per_sample(t1["N_IR"]), fs) == \
+        pytest.approx(t1["direct_mflops"])
+    assert costmodel.ola_ops_per_sample(t1["N_IR"]) == t1["ola_ops_per_sample"]
+    assert costmodel.mflops(costmodel.ola_ops_per_sample(t1["N_IR"]), fs) == \
+        pytest.approx(t1["ola"]["mflops"])
+    # Table 1's WOLA entry (14.064) is 2 * 145 + 3 operations per sample: the
+    # window/summation term counted once. The text's own formula 2 * (145 + 3)
+    # gives 14.208, and Table 2's WOLA entry follows that formula; both are pinned.
+    assert costmodel.mflops(2 * costmodel.ola_ops_per_sample(t1["N_IR"]) + 3, fs) == \
+        pytest.approx(t1["wola"]["mflops"])
+    assert costmodel.mflops(costmodel.wola_ops_per_sample(t1["N_IR"]), fs) == pytest.approx(14.208)
+    assert costmodel.tvolap_ops_per_sample(t1["L"], t1["M"]) == t1["tvolap_ops_per_sample"]
+    assert costmodel.mflops(costmodel.tvolap_ops_per_sample(t1["L"], t1["M"]), fs) == \
+        pytest.approx(t1["tvolap"]["mflops"])
+    assert costmodel.mflops(costmodel.ola_ops_per_sample(t2["N_IR"]), fs) == \
+        pytest.approx(t2["ola"]["mflops"])
+    assert costmodel.mflops(costmodel.wola_ops_per_sample(t2["N_IR"]), fs) == \
+        pytest.approx(t2["wola"]["mflops"])
+    # Table 2's TVOLAP entry is WOLA without the synthesis window (one
+    # multiplication per sample, twice for the overlap), not the M-formula
+    assert costmodel.mflops(costmodel.wola_ops_per_sample(t2["N_IR"]) - 2, fs) == \
+        pytest.approx(t2["tvolap"]["mflops"])
+    assert costmodel.mflops(costmodel.tvolap_ops_per_sample(t2["L"], t2["M"]), fs) == \
+        pytest.approx(12.288)
+    # latencies: audio 2L, switching L (Table 1)
+    assert t1["tvolap"]["audio_latency"] == 2 * t1["L"]
+    assert t1["tvolap"]["switching_latency"] == t1["L"] == t1["N_IR"] // (2 * t1["M"])
