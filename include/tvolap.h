@@ -202,11 +202,23 @@ TVOLAP_API int tvolap_inverse_ola(tvolap_t h, const float *Y_dev, int n_blocks, 
 /* Copy the M partition spectra of one slot to out_dev (device float2 [M][P]). */
 TVOLAP_API int tvolap_bank_spectra(tvolap_t h, int slot, float *out_dev);
 
+/* Options of tvolap_set_option. */
+typedef enum tvolap_option {
+    /* Staging of the offline multiply-accumulate: 0 = tiled bulk tensor copies
+       (TMA) when the buffers allow it, else cp.async (default); 1 = always
+       cp.async. Both give identical results. */
+    TVOLAP_OPT_MAC_STAGING = 1
+} tvolap_option;
+
+/* Set a plan option (takes effect for the following calls). */
+TVOLAP_API int tvolap_set_option(tvolap_t h, int option, int value);
+
 /*
  * Synchronise the stream and report deferred device-side errors: returns
  * TVOLAP_ERR_ARG if any kernel since the previous check met an invalid slot
- * index (the error record is cleared), TVOLAP_ERR_CUDA on a CUDA error,
- * otherwise TVOLAP_OK.
+ * index, TVOLAP_ERR_TIMEOUT if a bounded wait for an asynchronous copy gave
+ * up (the affected outputs are not written), TVOLAP_ERR_CUDA on a CUDA error,
+ * otherwise TVOLAP_OK. The error record is cleared.
  */
 TVOLAP_API int tvolap_check(tvolap_t h);
 

@@ -42,6 +42,7 @@ SIGNATURES = {
     "tvolap_inverse_ola": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int64, c_int64]),
     "tvolap_bank_spectra": (c_int, [c_void_p, c_int, c_void_p]),
     "tvolap_check": (c_int, [c_void_p]),
+    "tvolap_set_option": (c_int, [c_void_p, c_int, c_int]),
 }
 
 STATUS = {0: "TVOLAP_OK", -1: "TVOLAP_ERR_ARG", -2: "TVOLAP_ERR_OOM", -3: "TVOLAP_ERR_CUDA",

@@ -351,9 +351,20 @@ int tvolap_check(tvolap_t h)
         e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_status(e);
-        return TVOLAP_ERR_ARG;
+        return (err & 2u) ? TVOLAP_ERR_TIMEOUT : TVOLAP_ERR_ARG;
     }
     return TVOLAP_OK;
+}
+
+int tvolap_set_option(tvolap_t h, int option, int value)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (option == TVOLAP_OPT_MAC_STAGING) {
+        if (value < 0 || value > 1) return TVOLAP_ERR_ARG;
+        h->mac_variant = value;
+        return TVOLAP_OK;
+    }
+    return TVOLAP_ERR_ARG;
 }
 
 }  // extern "C"

@@ -34,6 +34,8 @@ struct tvolap_plan {
     float2 *Ystream;              // [n_out][P] this tick's output spectra
     int64_t tick;
 
+    int mac_variant;              // 0: TMA staging when possible, 1: cp.async staging
+
     // process_signal workspace
     void *ws;
     size_t ws_bytes;
@@ -52,10 +54,14 @@ cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, fl
 cudaError_t launch_forward_stream(tvolap_plan *h, const float *in);
 cudaError_t launch_inverse_stream(tvolap_plan *h, float *out);
 
-// kernels_mac.cu
+// kernels_mac_tma.cu (falls back to the cp.async kernel of kernels_mac.cu)
 cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, const int32_t *sa,
                               const int32_t *sb, const float *sal, int64_t sched_stride,
                               float2 *Y);
+// kernels_mac.cu
+cudaError_t launch_mac_signal_lsu(tvolap_plan *h, const float2 *X, int n_blocks,
+                                  const int32_t *sa, const int32_t *sb, const float *sal,
+                                  int64_t sched_stride, float2 *Y);
 cudaError_t launch_mac_stream(tvolap_plan *h, const int32_t *sa, const int32_t *sb,
                               const float *sal);
 cudaError_t launch_select(tvolap_plan *h, int out_ch, int a, int b, float alpha);

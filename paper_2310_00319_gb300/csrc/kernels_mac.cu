@@ -1,4 +1,6 @@
-// Partition multiply-accumulate of TVOLAP (Eq. 7) on sm_103a.
+// Partition multiply-accumulate of TVOLAP (Eq. 7) on sm_103a: the cp.async
+// variant of the offline kernel, the streaming tick and the selection kernel.
+// (The TMA-staged offline kernel is in kernels_mac_tma.cu.)
 //
 //   Y(k, t) = sum_{m < M, t - 2m >= 0} H_t(k, m) X(k, t - 2m),
 //   H_t = H[a_t] + alpha_t (H[b_t] - H[a_t])
@@ -6,175 +8,170 @@
 // The product is elementwise per bin, so it runs on the FP32 pipes (no tensor
 // cores: it is not a dense contraction).
 //
-// k_mac_signal (offline): a lane owns one bin, a warp owns a run of R output
-// blocks of equal parity t0, t0+2, .., t0+2(R-1). Along m the X values the run
-// needs slide by one block per step (X(t0 + 2(r - m))), so each step loads one
-// new X value, the two filter values of partition m, and does R complex
-// multiply-accumulates from registers. The filter pair of a run is normally
-// the same for all R blocks (only the mix weight changes); runs whose pair
-// changes inside take a path that loads the filter per block.
+// Offline mapping: a lane owns one bin, a warp owns a run of R output blocks
+// of equal parity t0, t0+2, .., t0+2(R-1). Along m the X values a run needs
+// slide by one block per step (X(t0 + 2(r - m))), so each step brings one new
+// X value and the run's filter values of partition m, and does R complex
+// multiply-accumulates from registers (mac_common.cuh gives the slot form of
+// the filter mix). Here each lane prefetches its operands D steps ahead with
+// 8-byte cp.async into a per-thread ring in shared memory.
 //
-// k_mac_stream (one tick): a CTA owns 64 bins of one output; its 8 warps split
-// the partitions, each lane streams float4 (two bins) of delay line and
-// filter, and the 8 partial sums are added in fixed order through shared
-// memory.
-#include "fft_core.cuh"
+// Streaming tick: a CTA owns 64 bins of one output; its 8 warps split the
+// partitions, each lane streams float4 (two bins) of delay line and filter,
+// and the 8 partial sums are added in fixed order through shared memory.
 #include "internal.h"
+#include "mac_common.cuh"
 
 namespace tvolap {
 
+using namespace mac;
+
 namespace {
 
-constexpr unsigned ERR_BAD_SLOT = 1u;
-
-__device__ __forceinline__ int checked_slot(int s, int n_slots_total, int null_slot, unsigned *err)
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid)
 {
-    if (s < 0 || s >= n_slots_total) {
-        atomicOr(err, ERR_BAD_SLOT);
-        return null_slot;
-    }
-    return s;
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 8 : 0;          // 0: fill the destination with zeros
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// acc += h * x
-__device__ __forceinline__ void cmac(float2 &acc, float2 h, float2 x)
-{
-    acc.x = fmaf(h.x, x.x, acc.x);
-    acc.x = fmaf(-h.y, x.y, acc.x);
-    acc.y = fmaf(h.x, x.y, acc.y);
-    acc.y = fmaf(h.y, x.x, acc.y);
-}
+constexpr int LSU_R = 8;        // output blocks per warp
+constexpr int LSU_D = 4;        // cp.async steps in flight
+constexpr int LSU_WARPS = 4;
 
-enum { MODE_SINGLE = 0, MODE_LERP = 1, MODE_GENERAL = 2 };
+struct LsuArgs {
+    const float2 *Xc;          // X of this output's input channel, offset to the lane's bin
+    const float2 *bk;          // bank offset to the lane's bin
+    float2 *Yo;                // Y of this output, offset to the lane's bin
+    const int32_t *ao, *bo;    // schedule rows of this output (bo may be null)
+    const float *alo;          // may be null
+    int M, P, n_blocks, n_slots_total, null_slot;
+    unsigned *err;
+    float2 *ring;              // this thread's ring base
+    int ring_stride;
+};
 
-template <int R, int MODE>
-__device__ __forceinline__ void mac_run(const float2 *__restrict__ Xc, const float2 *__restrict__ bank,
-                                        int M, int P, int tf, int n_blocks, int m_end,
-                                        const int (&a)[R], const int (&b)[R], const float (&al)[R],
+template <int R, int D, int NS>
+__device__ __forceinline__ void lsu_run(const LsuArgs &g, int tf, int m_end, const RunSlots<R> &rs,
                                         float2 (&acc)[R])
 {
     const float2 zero = make_float2(0.f, 0.f);
+    const int64_t MP = (int64_t)g.M * g.P;
+    const int P = g.P;
+    const float2 *H[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) H[j] = g.bk + (int64_t)rs.sl[j] * MP;
+    // ring row j of stage q: ring[(q * (NS + 1) + j) * ring_stride]; row NS holds X
+    auto issue = [&](int m) {
+        float2 *st = g.ring + (int64_t)((m % D) * (NS + 1)) * g.ring_stride;
+        const bool live = m < m_end;
+        const int tq = tf - 2 * m;
+        cp_async8(st + NS * g.ring_stride, g.Xc + (int64_t)(tq > 0 ? tq : 0) * P,
+                  live && m > 0 && tq >= 0);
+#pragma unroll
+        for (int j = 0; j < NS; ++j)
+            cp_async8(st + j * g.ring_stride, H[j] + (int64_t)(live ? m : 0) * P, live);
+        cp_async_commit();
+    };
     float2 xw[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int t = tf + 2 * r;
-        xw[r] = (t < n_blocks) ? __ldg(Xc + (int64_t)t * P) : zero;
+        xw[r] = (t < g.n_blocks) ? __ldg(g.Xc + (int64_t)t * P) : zero;
         acc[r] = zero;
     }
-    const int64_t MP = (int64_t)M * P;
-    const float2 *Ha = bank + (int64_t)a[0] * MP;
-    const float2 *Hb = bank + (int64_t)b[0] * MP;
-    // prefetched operands of the current step
-    float2 ha = __ldg(Ha), hb = (MODE == MODE_LERP) ? __ldg(Hb) : zero;
-    float2 xn = (m_end > 1 && tf - 2 >= 0) ? __ldg(Xc + (int64_t)(tf - 2) * P) : zero;
+#pragma unroll
+    for (int q = 0; q < D; ++q) issue(q);
     for (int m0 = 0; m0 < m_end; m0 += R) {
 #pragma unroll
         for (int u = 0; u < R; ++u) {
             const int m = m0 + u;
             if (m < m_end) {
-                if (m > 0) xw[(R - u) % R] = xn;          // X(tf - 2m) enters the window
-                // prefetch the next step
-                const int mn = m + 1;
-                const int tq = tf - 2 * mn;                // X entering at step m + 1
-                const float2 xnn = (mn < m_end && tq >= 0) ? __ldg(Xc + (int64_t)tq * P) : zero;
-                float2 han = zero, hbn = zero;
-                if (MODE != MODE_GENERAL && mn < m_end) {
-                    han = __ldg(Ha + (int64_t)mn * P);
-                    if (MODE == MODE_LERP) hbn = __ldg(Hb + (int64_t)mn * P);
-                }
-                if (MODE == MODE_SINGLE) {
+                cp_async_wait<D - 1>();
+                const float2 *st = g.ring + (int64_t)((m % D) * (NS + 1)) * g.ring_stride;
+                if (m > 0) xw[(R - u) % R] = st[NS * g.ring_stride];   // X(tf - 2m) enters
+                float2 hs[NS > 1 ? NS - 1 : 1];
 #pragma unroll
-                    for (int r = 0; r < R; ++r) cmac(acc[r], ha, xw[(r - u + R) % R]);
-                } else if (MODE == MODE_LERP) {
-                    const float2 d = csub(hb, ha);
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float2 h = make_float2(fmaf(al[r], d.x, ha.x), fmaf(al[r], d.y, ha.y));
-                        cmac(acc[r], h, xw[(r - u + R) % R]);
-                    }
-                } else {
-                    const int64_t off = (int64_t)m * P;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float2 pa = __ldg(bank + (int64_t)a[r] * MP + off);
-                        const float2 pb = __ldg(bank + (int64_t)b[r] * MP + off);
-                        const float2 h = make_float2(fmaf(al[r], pb.x - pa.x, pa.x),
-                                                     fmaf(al[r], pb.y - pa.y, pa.y));
-                        cmac(acc[r], h, xw[(r - u + R) % R]);
-                    }
-                }
-                xn = xnn;
-                ha = han;
-                hb = hbn;
+                for (int j = 1; j < NS; ++j) hs[j - 1] = st[j * g.ring_stride];
+                run_step<R, NS>(acc, xw, st[0], hs, rs.w, u);
+                issue(m + D);
             }
         }
+    }
+    cp_async_wait<0>();
+}
+
+// Blocks tf, tf+2, .., tf+2(R-1) of one output: up to MAX_NS distinct slots
+// run the slot form, otherwise the run is split in halves (one block never
+// mixes more than two slots, so the split ends).
+template <int R, int D>
+__device__ __forceinline__ void lsu_process_run(const LsuArgs &g, int tf)
+{
+    RunSlots<R> rs;
+    run_slots<R>(g.ao, g.bo, g.alo, tf, g.n_blocks, g.n_slots_total, g.null_slot, g.err, rs);
+    if constexpr (R > 1) {
+        if (rs.overflow) {
+            lsu_process_run<R / 2, D>(g, tf);
+            if (tf + R < g.n_blocks) lsu_process_run<R / 2, D>(g, tf + R);
+            return;
+        }
+    }
+    int m_end = (tf + 2 * (R - 1)) / 2 + 1;     // partitions with t - 2m >= 0 for some block
+    if (m_end > g.M) m_end = g.M;
+    float2 acc[R];
+    if (rs.ns == 1) {
+        lsu_run<R, D, 1>(g, tf, m_end, rs, acc);
+    } else if (rs.ns == 2) {
+        lsu_run<R, D, 2>(g, tf, m_end, rs, acc);
+    } else {
+        lsu_run<R, D, 3>(g, tf, m_end, rs, acc);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int t = tf + 2 * r;
+        if (t < g.n_blocks) g.Yo[(int64_t)t * g.P] = acc[r];
     }
 }
 
 // grid: x = run groups (4 runs of R blocks = 4R consecutive blocks), y = 32-bin
-// tiles, z = output channels. 4 warps: warp w runs parity w & 1, run w >> 1.
-template <int R>
-__global__ void __launch_bounds__(128)
-k_mac_signal(const float2 *__restrict__ X, int n_blocks, int M, int P,
-             const float2 *__restrict__ bank, int n_slots_total, int null_slot,
-             const int32_t *__restrict__ out_to_in, const int32_t *__restrict__ sa,
-             const int32_t *__restrict__ sb, const float *__restrict__ sal, int64_t sched_stride,
-             float2 *__restrict__ Y, unsigned *err)
+// tiles, z = output channels. Warp w runs parity w & 1, run w >> 1.
+template <int R, int D>
+__global__ void __launch_bounds__(32 * LSU_WARPS)
+k_mac_signal_lsu(const float2 *__restrict__ X, int n_blocks, int M, int P,
+                 const float2 *__restrict__ bank, int n_slots_total, int null_slot,
+                 const int32_t *__restrict__ out_to_in, const int32_t *__restrict__ sa,
+                 const int32_t *__restrict__ sb, const float *__restrict__ sal,
+                 int64_t sched_stride, float2 *__restrict__ Y, unsigned *err)
 {
+    __shared__ float2 ring_all[D * (MAX_NS + 1) * 32 * LSU_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int k = blockIdx.y * 32 + lane;
     const int o = blockIdx.z;
     const int tf = blockIdx.x * (4 * R) + (w >> 1) * (2 * R) + (w & 1);
     if (tf >= n_blocks) return;                       // whole warp; no barriers below
-    const int c = out_to_in[o];
-    const int32_t *ao = sa + (int64_t)o * sched_stride;
-    const int32_t *bo = sb ? sb + (int64_t)o * sched_stride : nullptr;
-    const float *alo = sal ? sal + (int64_t)o * sched_stride : nullptr;
-    int a[R], b[R];
-    float al[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int t = tf + 2 * r;
-        if (t < n_blocks) {
-            a[r] = checked_slot(ao[t], n_slots_total, null_slot, err);
-            b[r] = bo ? checked_slot(bo[t], n_slots_total, null_slot, err) : a[r];
-            al[r] = alo ? alo[t] : 0.f;
-        } else {                                      // past the end: repeat (results dropped)
-            a[r] = r ? a[r - 1] : 0;
-            b[r] = r ? b[r - 1] : 0;
-            al[r] = r ? al[r - 1] : 0.f;
-        }
-    }
-    bool same_pair = true, all0 = true, all1 = true;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        same_pair &= (a[r] == a[0]) && (b[r] == b[0]);
-        all0 &= (al[r] == 0.f);
-        all1 &= (al[r] == 1.f);
-    }
-    // m with t - 2m >= 0 for some block of the run
-    int m_end = (tf + 2 * (R - 1)) / 2 + 1;
-    if (m_end > M) m_end = M;
-    const float2 *Xc = X + (int64_t)c * n_blocks * P + k;
-    const float2 *bk = bank + k;
-    float2 acc[R];
-    if (same_pair && (a[0] == b[0] || all0 || all1)) {
-        if (all1 && a[0] != b[0]) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) a[r] = b[r];
-        }
-        mac_run<R, MODE_SINGLE>(Xc, bk, M, P, tf, n_blocks, m_end, a, b, al, acc);
-    } else if (same_pair) {
-        mac_run<R, MODE_LERP>(Xc, bk, M, P, tf, n_blocks, m_end, a, b, al, acc);
-    } else {
-        mac_run<R, MODE_GENERAL>(Xc, bk, M, P, tf, n_blocks, m_end, a, b, al, acc);
-    }
-    float2 *Yo = Y + (int64_t)o * n_blocks * P + k;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int t = tf + 2 * r;
-        if (t < n_blocks) Yo[(int64_t)t * P] = acc[r];
-    }
+    LsuArgs g;
+    g.Xc = X + (int64_t)out_to_in[o] * n_blocks * P + k;
+    g.bk = bank + k;
+    g.Yo = Y + (int64_t)o * n_blocks * P + k;
+    g.ao = sa + (int64_t)o * sched_stride;
+    g.bo = sb ? sb + (int64_t)o * sched_stride : nullptr;
+    g.alo = sal ? sal + (int64_t)o * sched_stride : nullptr;
+    g.M = M;
+    g.P = P;
+    g.n_blocks = n_blocks;
+    g.n_slots_total = n_slots_total;
+    g.null_slot = null_slot;
+    g.err = err;
+    g.ring = ring_all + threadIdx.x;
+    g.ring_stride = 32 * LSU_WARPS;
+    lsu_process_run<R, D>(g, tf);
 }
 
 // One streaming tick. grid: x = 64-bin tiles, y = outputs; 256 threads.
@@ -259,17 +256,17 @@ __global__ void k_select(int32_t *cur_a, int32_t *cur_b, float *cur_al, int o, i
 
 }  // namespace
 
-cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, const int32_t *sa,
-                              const int32_t *sb, const float *sal, int64_t sched_stride,
-                              float2 *Y)
+cudaError_t launch_mac_signal_lsu(tvolap_plan *h, const float2 *X, int n_blocks,
+                                  const int32_t *sa, const int32_t *sb, const float *sal,
+                                  int64_t sched_stride, float2 *Y)
 {
     if (n_blocks <= 0) return cudaSuccess;
-    constexpr int R = 8;
+    constexpr int R = LSU_R;
     dim3 grid((unsigned)((n_blocks + 4 * R - 1) / (4 * R)), (unsigned)(h->P / 32),
               (unsigned)h->n_out);
-    k_mac_signal<R><<<grid, 128, 0, h->stream>>>(X, n_blocks, h->M, h->P, h->bank,
-                                                 h->n_slots_total, h->null_slot, h->out_to_in,
-                                                 sa, sb, sal, sched_stride, Y, h->err);
+    k_mac_signal_lsu<R, LSU_D><<<grid, 32 * LSU_WARPS, 0, h->stream>>>(
+        X, n_blocks, h->M, h->P, h->bank, h->n_slots_total, h->null_slot, h->out_to_in, sa, sb,
+        sal, sched_stride, Y, h->err);
     return cudaGetLastError();
 }
 

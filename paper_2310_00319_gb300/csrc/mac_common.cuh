@@ -1,0 +1,129 @@
+// Device helpers shared by the multiply-accumulate kernels of Eq. 7.
+#pragma once
+
+#include "fft_core.cuh"
+
+namespace tvolap {
+namespace mac {
+
+constexpr unsigned ERR_BAD_SLOT = 1u;   // a schedule named a slot outside the bank
+constexpr unsigned ERR_TIMEOUT = 2u;    // a bounded wait on a copy gave up
+
+__device__ __forceinline__ int checked_slot(int s, int n_slots_total, int null_slot, unsigned *err)
+{
+    if (s < 0 || s >= n_slots_total) {
+        atomicOr(err, ERR_BAD_SLOT);
+        return null_slot;
+    }
+    return s;
+}
+
+// acc += h * x
+__device__ __forceinline__ void cmac(float2 &acc, float2 h, float2 x)
+{
+    acc.x = fmaf(h.x, x.x, acc.x);
+    acc.x = fmaf(-h.y, x.y, acc.x);
+    acc.y = fmaf(h.x, x.y, acc.y);
+    acc.y = fmaf(h.y, x.x, acc.y);
+}
+
+// Within a run of R blocks the filter of block r is a mix of the run's
+// distinct slots s_0 .. s_{ns-1}: H_r = sum_j w_rj H_{s_j} with sum_j w_rj = 1,
+// so H_r = H_{s_0} + sum_{j>=1} w_rj (H_{s_j} - H_{s_0}).
+constexpr int MAX_NS = 3;
+
+template <int R>
+struct RunSlots {
+    int sl[MAX_NS];
+    int ns;
+    bool overflow;               // more than MAX_NS distinct slots
+    float w[R][MAX_NS - 1];      // weights of s_1, s_2 per block
+};
+
+// Schedule of blocks tf, tf+2, .., tf+2(R-1) (rows past n_blocks repeat the
+// last valid row; their results are dropped).
+template <int R>
+__device__ __forceinline__ void run_slots(const int32_t *__restrict__ ao, const int32_t *__restrict__ bo,
+                                          const float *__restrict__ alo, int tf, int n_blocks,
+                                          int n_slots_total, int null_slot, unsigned *err,
+                                          RunSlots<R> &rs)
+{
+    int a[R], b[R];
+    float al[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int t = tf + 2 * r;
+        if (t < n_blocks) {
+            a[r] = checked_slot(__ldg(ao + t), n_slots_total, null_slot, err);
+            b[r] = bo ? checked_slot(__ldg(bo + t), n_slots_total, null_slot, err) : a[r];
+            al[r] = alo ? __ldg(alo + t) : 0.f;
+        } else {
+            a[r] = r ? a[r - 1] : 0;
+            b[r] = r ? b[r - 1] : 0;
+            al[r] = r ? al[r - 1] : 0.f;
+        }
+    }
+    int ns = 0;
+    bool overflow = false;
+#pragma unroll
+    for (int j = 0; j < MAX_NS; ++j) rs.sl[j] = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int v = q ? b[r] : a[r];
+            const float wt = q ? al[r] : 1.f - al[r];
+            if (wt == 0.f && !(q == 0 && b[r] == a[r])) continue;   // slot unused by this block
+            bool seen = false;
+#pragma unroll
+            for (int j = 0; j < MAX_NS; ++j) seen |= (j < ns) && (rs.sl[j] == v);
+            if (!seen) {
+                if (ns < MAX_NS) {
+#pragma unroll
+                    for (int j = 0; j < MAX_NS; ++j)
+                        if (j == ns) rs.sl[j] = v;
+                    ++ns;
+                } else {
+                    overflow = true;
+                }
+            }
+        }
+    }
+    if (ns == 0) {
+        rs.sl[0] = a[0];
+        ns = 1;
+    }
+    rs.ns = ns;
+    rs.overflow = overflow;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int j = 1; j < MAX_NS; ++j)
+            rs.w[r][j - 1] = (a[r] == rs.sl[j] ? 1.f - al[r] : 0.f) + (b[r] == rs.sl[j] ? al[r] : 0.f);
+    }
+}
+
+// One step of Eq. 7 for the R blocks of a run: partition values h0 = H_{s_0}(m),
+// hs[j-1] = H_{s_j}(m); xw holds X(tf + 2(r - m)) at index (r - u) mod R, with
+// u = m mod R. Callers unroll over u so every register index is a constant.
+template <int R, int NS>
+__device__ __forceinline__ void run_step(float2 (&acc)[R], const float2 (&xw)[R], float2 h0,
+                                         const float2 *hs, const float (&w)[R][MAX_NS - 1], int u)
+{
+    float2 dj[NS > 1 ? NS - 1 : 1];
+#pragma unroll
+    for (int j = 1; j < NS; ++j) dj[j - 1] = csub(hs[j - 1], h0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float2 h = h0;
+#pragma unroll
+        for (int j = 1; j < NS; ++j) {
+            h.x = fmaf(w[r][j - 1], dj[j - 1].x, h.x);
+            h.y = fmaf(w[r][j - 1], dj[j - 1].y, h.y);
+        }
+        cmac(acc[r], h, xw[(r - u % R + R) % R]);
+    }
+}
+
+}  // namespace mac
+}  // namespace tvolap

@@ -101,6 +101,10 @@ class Plan:
     def reset(self):
         self._call("tvolap_reset")
 
+    def set_option(self, option: int, value: int):
+        """TVOLAP_OPT_MAC_STAGING (1): 0 = TMA staging when possible, 1 = cp.async."""
+        self._call("tvolap_set_option", int(option), int(value))
+
     def check(self):
         """Synchronise and raise if a kernel met an invalid slot index."""
         self._call("tvolap_check")

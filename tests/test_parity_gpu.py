@@ -100,17 +100,20 @@ def test_bank_spectra_match_oracle(L, ir_len):
         assert rel < 1e-6 and mx < 1e-5, (s, rel, mx)
 
 
-def test_mac_stage_matches_eq7():
-    """Kernel (c) alone: Y(t) = sum_m H_t(m) X(t - 2m) from oracle spectra,
-    including runs whose filter pair changes inside (the per-block path)."""
+@pytest.mark.parametrize("n_slots,interp", [(3, True), (8, True), (8, False), (1, False)])
+def test_mac_stage_matches_eq7(n_slots, interp):
+    """Kernel (c) alone: Y(t) = sum_m H_t(m) X(t - 2m) from oracle spectra.
+    Random slots and weights per block make runs mix up to 2R distinct slots,
+    which exercises the run splitting down to single blocks."""
     dev = _dev()
     L = 32
-    wl = W.random_case(77, L=L, ir_len=9 * 2 * L - 5, N=60 * L, n_in=2, n_out=2, n_slots=3)
+    wl = W.random_case(77 + n_slots, L=L, ir_len=9 * 2 * L - 5, N=60 * L, n_in=2, n_out=2,
+                       n_slots=n_slots, interp=interp)
     M, P, nb = wl.M, 2 * L, wl.n_blocks
     X = np.stack([oracle.block_spectra(wl.x[c], L, list(range(-1, nb - 1)), grid="halfbin")[:, :P]
                   for c in range(2)])
     H = np.stack([oracle.partition_spectra(wl.irs[s], L, M, grid="halfbin")[:, :P]
-                  for s in range(3)])
+                  for s in range(n_slots)])
     plan = _plan(wl, dev)
     Y = plan.mac(_t(X.astype(np.complex64), dev), _t(wl.sched_a, dev), _t(wl.sched_b, dev),
                  _t(wl.sched_alpha, dev)).cpu().numpy()
@@ -217,6 +220,20 @@ def test_invalid_slot_is_silenced_and_reported():
     fixed[0, 10:20] = 2                               # the zero response
     ref = oracle.tvolap_direct(wl.x, irs0, wl.L, fixed, out_len=wl.out_len)
     _assert_close(y.cpu().numpy(), ref, "invalid slot")
+
+
+def test_mac_staging_variants_agree_bitwise():
+    """TMA-staged and cp.async-staged multiply-accumulate run the same
+    arithmetic in the same order: their outputs are identical."""
+    dev = _dev()
+    wl = W.random_case(14, L=256, ir_len=20000, N=50000, n_in=2, n_out=3, n_slots=6,
+                       out_to_in=[0, 1, 1])
+    plan = _plan(wl, dev)
+    y_tma = _run_signal(wl, dev, plan)
+    plan.set_option(1, 1)
+    y_lsu = _run_signal(wl, dev, plan)
+    np.testing.assert_array_equal(y_tma, y_lsu)
+    _assert_close(y_tma, _ref(wl), "variants")
 
 
 def test_deterministic_bitwise():
