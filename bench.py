@@ -169,7 +169,7 @@ def run_ours(args):
         if ev:
             ev[4].record(stream)
 
-    launches_per_step = 4
+    launches_per_step = 5     # bank, forward, MAC group + overflow, inverse
     for _ in range(args.warmup):
         step()
     plan.check()

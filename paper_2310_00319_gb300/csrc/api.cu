@@ -36,8 +36,9 @@ cudaError_t dalloc(T **p, size_t count)
 void free_plan(tvolap_plan *h)
 {
     if (!h) return;
-    void *ptrs[] = {h->tw, h->rot, h->post, h->win, h->bank, h->out_to_in, h->sel_a, h->sel_b,
-                    h->sel_alpha, h->err, h->ring, h->hist, h->ola, h->Ystream, h->ws};
+    void *ptrs[] = {h->tw,   h->rot,  h->post, h->win,     h->bank, h->out_to_in,
+                    h->sel_a, h->sel_b, h->sel_alpha, h->err, h->ring, h->hist,
+                    h->ola,  h->Ystream, h->ws,  h->ovf_list, h->ovf_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -98,6 +99,30 @@ int reset_state(tvolap_plan *h)
 }
 
 }  // namespace
+
+namespace tvolap {
+
+cudaError_t ensure_overflow(tvolap_plan *h, int64_t entries)
+{
+    if (!h->ovf_count) {
+        cudaError_t e = cudaMalloc(&h->ovf_count, sizeof(int));
+        if (e != cudaSuccess) return e;
+    }
+    if (entries <= h->ovf_cap) return cudaSuccess;
+    if (h->ovf_list) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return e;
+        cudaFree(h->ovf_list);
+        h->ovf_list = nullptr;
+        h->ovf_cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&h->ovf_list, sizeof(int4) * (size_t)entries);
+    if (e != cudaSuccess) return e;
+    h->ovf_cap = entries;
+    return cudaSuccess;
+}
+
+}  // namespace tvolap
 
 extern "C" {
 

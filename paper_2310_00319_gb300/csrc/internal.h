@@ -35,6 +35,9 @@ struct tvolap_plan {
     int64_t tick;
 
     int mac_variant;              // 0: TMA staging when possible, 1: cp.async staging
+    int4 *ovf_list;               // groups the group kernel hands to the per-warp kernel
+    int *ovf_count;
+    int64_t ovf_cap;
 
     // process_signal workspace
     void *ws;
@@ -58,6 +61,9 @@ cudaError_t launch_inverse_stream(tvolap_plan *h, float *out);
 cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, const int32_t *sa,
                               const int32_t *sb, const float *sal, int64_t sched_stride,
                               float2 *Y);
+// api.cu: grow the overflow list of the offline multiply-accumulate
+cudaError_t ensure_overflow(tvolap_plan *h, int64_t entries);
+
 // kernels_mac.cu
 cudaError_t launch_mac_signal_lsu(tvolap_plan *h, const float2 *X, int n_blocks,
                                   const int32_t *sa, const int32_t *sb, const float *sal,

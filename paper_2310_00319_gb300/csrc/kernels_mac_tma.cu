@@ -26,11 +26,12 @@ using namespace mac;
 namespace {
 
 constexpr int TMA_R = 8;          // output blocks per warp
-constexpr int TMA_D = 4;          // partitions per staged chunk
+constexpr int TMA_D = TMA_R;      // partitions per staged chunk (one register rotation)
 constexpr int TMA_WARPS = 4;
 constexpr int ROW_BYTES = 32 * 8; // 32 bins of float2
 constexpr int STAGE_ROWS = (1 + MAX_NS) * TMA_D;
 constexpr int WARP_BYTES = 128 + TMA_R * ROW_BYTES + 2 * STAGE_ROWS * ROW_BYTES;
+static_assert(TMA_R % TMA_D == 0 || TMA_D % TMA_R == 0, "chunk and rotation must nest");
 constexpr long long WAIT_CYCLES = 1LL << 32;   // about two seconds at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -127,6 +128,26 @@ __device__ __forceinline__ void issue_chunk(const TmaArgs &g, const int (&sl)[MA
         tma_load_3d(st + (1 + j) * TMA_D * 32, g.hmap, g.k0, m0, sl[j], bar);
 }
 
+// One chunk of D steps from stage buffer st; GUARD: the chunk may pass m_end.
+template <int R, int NS, bool GUARD>
+__device__ __forceinline__ void tma_chunk(const float2 *st, int c, int cu, int m_end,
+                                          const RunSlots<R> &rs, float2 (&xw)[R], float2 (&acc)[R])
+{
+    constexpr int D = TMA_D;
+#pragma unroll
+    for (int u = 0; u < D; ++u) {
+        const int m = c * D + u;
+        const int rot = (cu * D + u) % R;
+        if (!GUARD || m < m_end) {
+            if (m > 0) xw[(R - rot) % R] = st[(D - 1 - u) * 32];   // X(tf - 2m) enters
+            float2 hs[NS > 1 ? NS - 1 : 1];
+#pragma unroll
+            for (int j = 1; j < NS; ++j) hs[j - 1] = st[((1 + j) * D + u) * 32];
+            run_step<R, NS>(acc, xw, st[(D + u) * 32], hs, rs.w, rot);
+        }
+    }
+}
+
 template <int R, int NS>
 __device__ __forceinline__ void tma_run(const TmaArgs &g, Pipe &pp, int tf, int m_end,
                                         const RunSlots<R> &rs, float2 (&acc)[R])
@@ -169,18 +190,10 @@ __device__ __forceinline__ void tma_run(const TmaArgs &g, Pipe &pp, int tf, int 
                 pp.phase ^= (2u << q);
                 pp.inflight &= ~(2u << q);
                 const float2 *st = g.stage + q * STAGE_ROWS * 32 + lane;
-#pragma unroll
-                for (int u = 0; u < D; ++u) {
-                    const int m = c * D + u;
-                    const int rot = (cu * D + u) % R;
-                    if (m < m_end) {
-                        if (m > 0) xw[(R - rot) % R] = st[(D - 1 - u) * 32];   // X(tf - 2m)
-                        float2 hs[NS > 1 ? NS - 1 : 1];
-#pragma unroll
-                        for (int j = 1; j < NS; ++j) hs[j - 1] = st[((1 + j) * D + u) * 32];
-                        run_step<R, NS>(acc, xw, st[(D + u) * 32], hs, rs.w, rot);
-                    }
-                }
+                if ((c + 1) * D <= m_end)
+                    tma_chunk<R, NS, false>(st, c, cu, m_end, rs, xw, acc);
+                else
+                    tma_chunk<R, NS, true>(st, c, cu, m_end, rs, xw, acc);
                 __syncwarp();
                 if (c + 2 < nchunks) {
                     pp.inflight |= (2u << q);
@@ -221,34 +234,35 @@ __device__ __forceinline__ void tma_process_run(const TmaArgs &g, Pipe &pp, int 
     }
 }
 
-// grid: x = run groups (4 runs of R blocks = 4R consecutive blocks), y = 32-bin
-// tiles, z = output channels. Warp w runs parity w & 1, run w >> 1.
+// A group: 4 consecutive runs of one parity, blocks t = T0 + 2i, i < 32, with
+// T0 = parity + 64 * group; run w of the group starts at tf = T0 + 16 w.
+constexpr int GW = 4;                           // runs (warps) per group
+constexpr int GROUP_ROWS = GW * TMA_R;          // same-parity blocks per group
+
+__device__ __forceinline__ void group_origin(int p, int grp, int &T0) { T0 = p + 2 * GROUP_ROWS * grp; }
+
+// Per-warp kernel for groups whose runs together mix more than MAX_NS slots
+// (listed by the group kernel): each warp stages its own run's slots.
+// Persistent: CTA b takes list entries b, b + gridDim.x, ...
 __global__ void __launch_bounds__(32 * TMA_WARPS)
-k_mac_signal_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap hmap,
-                 int n_blocks, int M, int P, int n_slots_total, int null_slot,
-                 const int32_t *__restrict__ out_to_in, const int32_t *__restrict__ sa,
-                 const int32_t *__restrict__ sb, const float *__restrict__ sal,
-                 int64_t sched_stride, float2 *__restrict__ Y, unsigned *err)
+k_mac_overflow_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap hmap,
+                   int n_blocks, int M, int P, int n_slots_total, int null_slot,
+                   const int32_t *__restrict__ out_to_in, const int32_t *__restrict__ sa,
+                   const int32_t *__restrict__ sb, const float *__restrict__ sal,
+                   int64_t sched_stride, float2 *__restrict__ Y, unsigned *err,
+                   const int4 *__restrict__ list, const int *__restrict__ count)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     constexpr int R = TMA_R;
-    const int tf = blockIdx.x * (4 * R) + (w >> 1) * (2 * R) + (w & 1);
-    if (tf >= n_blocks) return;                       // whole warp; no CTA barriers used
-    // once any wait has expired, the remaining warps leave at once
+    const int n = *count;
+    if ((int)blockIdx.x >= n) return;
     if (*(volatile unsigned *)err & ERR_TIMEOUT) return;
     unsigned char *base = smem_raw + w * WARP_BYTES;
     TmaArgs g;
     g.xmap = &xmap;
     g.hmap = &hmap;
-    g.k0 = blockIdx.y * 32;
     g.lane = lane;
-    const int o = blockIdx.z;
-    g.cin = out_to_in[o];
-    g.Yo = Y + (int64_t)o * n_blocks * P + g.k0 + lane;
-    g.ao = sa + (int64_t)o * sched_stride;
-    g.bo = sb ? sb + (int64_t)o * sched_stride : nullptr;
-    g.alo = sal ? sal + (int64_t)o * sched_stride : nullptr;
     g.M = M;
     g.P = P;
     g.n_blocks = n_blocks;
@@ -264,7 +278,21 @@ k_mac_signal_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant
     }
     __syncwarp();
     Pipe pp{0u, 0u, true};
-    tma_process_run<R>(g, pp, tf);
+    for (int e = blockIdx.x; e < n && pp.ok; e += gridDim.x) {
+        const int4 ent = list[e];                      // (output, bin tile, parity, group)
+        int T0;
+        group_origin(ent.z, ent.w, T0);
+        const int tf = T0 + 2 * R * w;
+        if (tf >= n_blocks) continue;
+        const int o = ent.x;
+        g.k0 = ent.y * 32;
+        g.cin = out_to_in[o];
+        g.Yo = Y + (int64_t)o * n_blocks * P + g.k0 + lane;
+        g.ao = sa + (int64_t)o * sched_stride;
+        g.bo = sb ? sb + (int64_t)o * sched_stride : nullptr;
+        g.alo = sal ? sal + (int64_t)o * sched_stride : nullptr;
+        tma_process_run<R>(g, pp, tf);
+    }
     if (!pp.ok) {
         // a copy did not land in time: report it, then give each barrier with
         // copies outstanding another bounded wait before the CTA's shared
@@ -272,6 +300,238 @@ k_mac_signal_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant
         if (lane == 0) atomicOr(err, ERR_TIMEOUT);
         for (int q = 0; q < 3; ++q)
             if (pp.inflight & (1u << q)) mbar_wait(g.bar + q, (pp.phase >> q) & 1u);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Group kernel. The 4 consumer warps of a CTA take the 4 runs of a group; a
+// fifth warp only loads. Two facts make the loads cheap:
+//  * all four runs of a group share the group's slots, so one copy of each
+//    slot's rows serves four runs (groups mixing more than MAX_NS slots go to
+//    the overflow list and the per-warp kernel);
+//  * the runs are consecutive, so the X rows warp w needs at chunk c + 1 are
+//    the rows warp w - 1 used at chunk c: every chunk brings only 8 new X rows.
+// Rows of the group's parity are numbered i (block t = T0 + 2i) and kept in a
+// ring of XRING rows at slot (i + 7) mod XRING; the filter rows of chunk c sit
+// in stage c mod NSTAGE. The loader runs up to NSTAGE chunks ahead; consumers
+// release a stage on its 'empty' barrier. Rows before block 0 and partitions
+// at or past M arrive as zeros, so a chunk always runs all D steps: the extra
+// products are exact zeros.
+constexpr int NSTAGE = 3;
+constexpr int XRING = 64;                             // rows; chunk c writes slots [-8c, -8c+8) mod 64
+constexpr int HSTAGE_ROWS = MAX_NS * TMA_D;
+constexpr int GROUP_BYTES = 256 + XRING * ROW_BYTES + NSTAGE * HSTAGE_ROWS * ROW_BYTES;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct GroupSmem {
+    uint64_t bar[1 + 2 * NSTAGE];     // 0 window, 1.. full, 1+NSTAGE.. empty
+    int U, overflow, n_active;
+    int slot[MAX_NS];
+};
+
+__device__ __forceinline__ int ring_slot(int j) { return j & (XRING - 1); }
+
+template <int NS>
+__device__ __forceinline__ void group_chunk(const float2 *xs, const float2 *const (&hb)[MAX_NS],
+                                            int c, const RunSlots<TMA_R> &rs,
+                                            float2 (&xw)[TMA_R], float2 (&acc)[TMA_R])
+{
+    constexpr int D = TMA_D, R = TMA_R;
+#pragma unroll
+    for (int u = 0; u < D; ++u) {
+        if (c > 0 || u > 0) xw[(R - u) % R] = xs[(D - 1 - u) * 32];   // X(tf - 2m) enters
+        float2 hs[NS > 1 ? NS - 1 : 1];
+#pragma unroll
+        for (int j = 1; j < NS; ++j) hs[j - 1] = hb[j][u * 32];
+        run_step<R, NS>(acc, xw, hb[0][u * 32], hs, rs.w, u);
+    }
+}
+
+template <int NS>
+__device__ __forceinline__ bool group_consume(GroupSmem *gs, const float2 *xring, const float2 *hst,
+                                              int w, int lane, int nchunks, int m_end,
+                                              const RunSlots<TMA_R> &rs, const int (&idx)[MAX_NS],
+                                              float2 (&acc)[TMA_R])
+{
+    constexpr int D = TMA_D, R = TMA_R;
+    float2 xw[R];
+    // window rows i = 8w + r, r < R, at ring slots 8w + 7 + r (row 0 comes with chunk 0)
+    if (!mbar_wait(gs->bar, 0u) || !mbar_wait(gs->bar + 1, 0u)) return false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        xw[r] = xring[ring_slot(R * w + 7 + r) * 32 + lane];
+        acc[r] = make_float2(0.f, 0.f);
+    }
+    for (int c = 0; c < nchunks; ++c) {
+        const int q = c % NSTAGE;
+        if (c > 0 && !mbar_wait(gs->bar + 1 + q, (uint32_t)(c / NSTAGE) & 1u)) return false;
+        if (c * D < m_end) {
+            // rows i = 8w - 8c - u, u < 8: ring slots 8(w - c) .. 8(w - c) + 7, row 7 - u
+            const float2 *xs = xring + ring_slot(D * (w - c)) * 32 + lane;
+            const float2 *st = hst + q * HSTAGE_ROWS * 32 + lane;
+            const float2 *hb[MAX_NS];
+#pragma unroll
+            for (int j = 0; j < MAX_NS; ++j) hb[j] = st + idx[j] * D * 32;
+            group_chunk<NS>(xs, hb, c, rs, xw, acc);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(gs->bar + 1 + NSTAGE + q);
+    }
+    return true;
+}
+
+// grid: x = (group, parity) pairs, y = 32-bin tiles, z = output channels;
+// 4 consumer warps + 1 loader warp.
+__global__ void __launch_bounds__(32 * (GW + 1), 4)
+k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap hmap,
+                   int n_blocks, int M, int P, int n_slots_total, int null_slot,
+                   const int32_t *__restrict__ out_to_in, const int32_t *__restrict__ sa,
+                   const int32_t *__restrict__ sb, const float *__restrict__ sal,
+                   int64_t sched_stride, float2 *__restrict__ Y, unsigned *err,
+                   int4 *__restrict__ list, int *__restrict__ count)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int R = TMA_R, D = TMA_D;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int p = blockIdx.x & 1, grp = blockIdx.x >> 1;
+    int T0;
+    group_origin(p, grp, T0);
+    if (T0 >= n_blocks) return;                        // whole CTA
+    if (*(volatile unsigned *)err & ERR_TIMEOUT) return;
+    GroupSmem *gs = reinterpret_cast<GroupSmem *>(smem_raw);
+    float2 *xring = reinterpret_cast<float2 *>(smem_raw + 256);
+    float2 *hst = reinterpret_cast<float2 *>(smem_raw + 256 + XRING * ROW_BYTES);
+    const int o = blockIdx.z, k0 = blockIdx.y * 32;
+    const int32_t *ao = sa + (int64_t)o * sched_stride;
+    const int32_t *bo = sb ? sb + (int64_t)o * sched_stride : nullptr;
+    const float *alo = sal ? sal + (int64_t)o * sched_stride : nullptr;
+    if (w == GW) {
+        // loader warp: distinct slots with nonzero weight over the group's
+        // 32 blocks (lane i: block T0 + 2i), then the barriers
+        const int t = T0 + 2 * lane;
+        int a = 0, b = 0;
+        bool va = false, vb = false;
+        if (t < n_blocks) {
+            a = checked_slot(__ldg(ao + t), n_slots_total, null_slot, err);
+            b = bo ? checked_slot(__ldg(bo + t), n_slots_total, null_slot, err) : a;
+            const float al = alo ? __ldg(alo + t) : 0.f;
+            va = (al != 1.f) || (a == b);
+            vb = (al != 0.f) && (b != a);
+        }
+        int U = 0, ovf = 0;
+        for (int it = 0; it <= MAX_NS; ++it) {
+            const unsigned ma = __ballot_sync(0xffffffffu, va), mb = __ballot_sync(0xffffffffu, vb);
+            if (!ma && !mb) break;
+            const int v = ma ? __shfl_sync(0xffffffffu, a, __ffs(ma) - 1)
+                             : __shfl_sync(0xffffffffu, b, __ffs(mb) - 1);
+            if (U == MAX_NS) {
+                ovf = 1;
+                break;
+            }
+            if (lane == 0) gs->slot[U] = v;
+            ++U;
+            va = va && (a != v);
+            vb = vb && (b != v);
+        }
+        int n_active = (n_blocks - T0 + 2 * R - 1) / (2 * R);
+        if (n_active > GW) n_active = GW;
+        if (lane == 0) {
+            gs->U = U;
+            gs->overflow = ovf;
+            gs->n_active = n_active;
+            mbar_init(gs->bar, 1);
+            for (int q = 0; q < NSTAGE; ++q) {
+                mbar_init(gs->bar + 1 + q, 1);
+                mbar_init(gs->bar + 1 + NSTAGE + q, n_active);
+            }
+            mbar_init_fence();
+        }
+    }
+    __syncthreads();
+    if (gs->overflow) {
+        if (threadIdx.x == 0) list[atomicAdd(count, 1)] = make_int4(o, blockIdx.y, p, grp);
+        return;
+    }
+    const int n_active = gs->n_active;
+    const int U = gs->U;
+    const int cin = out_to_in[o];
+    // the chunks cover the partitions of the group's last run (the longest)
+    const int t_last = T0 + 2 * R * (n_active - 1);
+    int m_all = (t_last + 2 * (R - 1)) / 2 + 1;
+    if (m_all > M) m_all = M;
+    const int nchunks = (m_all + D - 1) / D;
+
+    if (w == GW) {                                     // ---- loader
+        uint32_t filled = 0, ppar = 0;                 // bit q: stage q was filled; its last parity
+        bool ok = true;
+        if (lane == 0) {
+            // window rows i = 1 .. 32 (ring slots 8 .. 39); row i = 0 comes with chunk 0
+            mbar_expect_tx(gs->bar, (uint32_t)(4 * D * ROW_BYTES));
+            for (int k = 0; k < 4; ++k)
+                tma_load_3d(xring + (8 + k * D) * 32, &xmap, k0, T0 + 2 + 2 * k * D, cin, gs->bar);
+        }
+        for (int c = 0; c < nchunks && ok; ++c) {
+            const int q = c % NSTAGE;
+            if (c >= NSTAGE) {
+                // stage q last held chunk c - NSTAGE; the X slots this chunk
+                // overwrites were last read by chunk c - 5 < c - NSTAGE
+                ok = mbar_wait(gs->bar + 1 + NSTAGE + q, (uint32_t)((c - NSTAGE) / NSTAGE) & 1u);
+                if (!ok) break;
+            }
+            filled |= 1u << q;
+            ppar = (ppar & ~(1u << q)) | ((uint32_t)(c / NSTAGE & 1) << q);
+            if (lane == 0) {
+                uint64_t *bar = gs->bar + 1 + q;
+                mbar_expect_tx(bar, (uint32_t)((1 + U) * D * ROW_BYTES));
+                // new X rows i = -8c - 7 .. -8c (blocks T0 - 16c - 14 .. T0 - 16c)
+                tma_load_3d(xring + ring_slot(-D * c) * 32, &xmap, k0, T0 - 2 * D * c - 2 * (D - 1),
+                            cin, bar);
+                for (int j = 0; j < U; ++j)
+                    tma_load_3d(hst + (q * HSTAGE_ROWS + j * D) * 32, &hmap, k0, c * D, gs->slot[j], bar);
+            }
+        }
+        if (!ok) {
+            // give every copy this warp issued a bounded chance to land before
+            // the CTA's shared memory is released (a completed fill returns at once)
+            if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+            mbar_wait(gs->bar, 0u);
+            for (int q = 0; q < NSTAGE; ++q)
+                if (filled & (1u << q)) mbar_wait(gs->bar + 1 + q, (ppar >> q) & 1u);
+        }
+        return;
+    }
+    if (w >= n_active) return;                        // ---- consumers (no CTA barriers below)
+    const int tf = T0 + 2 * R * w;
+    RunSlots<R> rs;
+    run_slots<R>(ao, bo, alo, tf, n_blocks, n_slots_total, null_slot, err, rs);
+    int idx[MAX_NS] = {0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < MAX_NS; ++j)
+        for (int q = 0; q < U; ++q)
+            if (j < rs.ns && gs->slot[q] == rs.sl[j]) idx[j] = q;
+    int m_end = (tf + 2 * (R - 1)) / 2 + 1;
+    if (m_end > M) m_end = M;
+    float2 acc[R];
+    bool ok;
+    if (rs.ns == 1)
+        ok = group_consume<1>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
+    else if (rs.ns == 2)
+        ok = group_consume<2>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
+    else
+        ok = group_consume<3>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
+    if (!ok) {
+        if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+        return;
+    }
+    float2 *Yo = Y + (int64_t)o * n_blocks * P + k0 + lane;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int t = tf + 2 * r;
+        if (t < n_blocks) Yo[(int64_t)t * P] = acc[r];
     }
 }
 
@@ -319,23 +579,42 @@ cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, con
                               float2 *Y)
 {
     if (n_blocks <= 0) return cudaSuccess;
-    CUtensorMap xmap, hmap;
+    CUtensorMap xrun, hmap;
     const bool tma = h->mac_variant != 1 &&
-                     encode_spectra(&xmap, X, h->P, n_blocks, h->n_in, TMA_D, 2) &&
+                     encode_spectra(&xrun, X, h->P, n_blocks, h->n_in, TMA_D, 2) &&
                      encode_spectra(&hmap, h->bank, h->P, h->M, h->n_slots_total + 1, TMA_D, 1);
     if (!tma) return launch_mac_signal_lsu(h, X, n_blocks, sa, sb, sal, sched_stride, Y);
-    constexpr int R = TMA_R;
-    dim3 grid((unsigned)((n_blocks + 4 * R - 1) / (4 * R)), (unsigned)(h->P / 32),
-              (unsigned)h->n_out);
-    const size_t smem = (size_t)TMA_WARPS * WARP_BYTES;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_mac_signal_tma,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int tiles = h->P / 32;
+    const int groups = ((n_blocks + 1) / 2 + GROUP_ROWS - 1) / GROUP_ROWS;
+    const int64_t max_entries = (int64_t)2 * groups * tiles * h->n_out;
+    cudaError_t e = ensure_overflow(h, max_entries);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(h->ovf_count, 0, sizeof(int), h->stream);
+    if (e != cudaSuccess) return e;
+    const size_t gsmem = GROUP_BYTES;
+    if (gsmem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_mac_signal_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gsmem);
         if (e != cudaSuccess) return e;
     }
-    k_mac_signal_tma<<<grid, 32 * TMA_WARPS, smem, h->stream>>>(
-        xmap, hmap, n_blocks, h->M, h->P, h->n_slots_total, h->null_slot, h->out_to_in, sa, sb, sal,
-        sched_stride, Y, h->err);
+    dim3 grid((unsigned)(2 * groups), (unsigned)tiles, (unsigned)h->n_out);
+    k_mac_signal_group<<<grid, 32 * (GW + 1), gsmem, h->stream>>>(
+        xrun, hmap, n_blocks, h->M, h->P, h->n_slots_total, h->null_slot, h->out_to_in, sa, sb,
+        sal, sched_stride, Y, h->err, h->ovf_list, h->ovf_count);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t wsmem = (size_t)TMA_WARPS * WARP_BYTES;
+    if (wsmem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_mac_overflow_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)wsmem);
+        if (e != cudaSuccess) return e;
+    }
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    const int64_t ogrid = max_entries < 2LL * sms ? max_entries : 2LL * sms;
+    k_mac_overflow_tma<<<(unsigned)ogrid, 32 * TMA_WARPS, wsmem, h->stream>>>(
+        xrun, hmap, n_blocks, h->M, h->P, h->n_slots_total, h->null_slot, h->out_to_in, sa, sb, sal,
+        sched_stride, Y, h->err, h->ovf_list, h->ovf_count);
     return cudaGetLastError();
 }
 
