@@ -52,6 +52,11 @@ def _peaks():
 # FP32 FMA peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops x clock.
 SMS, FP32_LANES = 152, 128
 
+# DRAM bytes (read + write) of one launch of the multiply-accumulate group kernel at the
+# default 64-channel workload: ncu capture at 32 channels (profiles/
+# k_mac_signal_group_plain_at_scale_32ch.md) scaled by the channel count.
+MAC_TRAFFIC_BYTES = 2 * (311.548160e6 + 215.897088e6)
+
 
 def fp32_peak_tflops(mhz: float) -> float:
     return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
@@ -206,9 +211,12 @@ def run_ours(args):
     flops = mac_terms(nb, M) * P * wl.n_out * costmodel.mac_flops_per_block_bin_partition(True)
     achieved = flops / (mac_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    traffic = args.traffic
+    if traffic is None and args.channels == 64 and args.samples == 480000:
+        traffic = MAC_TRAFFIC_BYTES
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": args.traffic, "kernel": "k_mac_signal",
+                "traffic": traffic, "kernel": "k_mac_signal_group",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}
     # the transform stages are memory bound: algorithmic bytes / time vs measured HBM copy
     bytes_fwd = 4.0 * n_ch * N + 8.0 * P * n_ch * nb
