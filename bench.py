@@ -53,8 +53,8 @@ def _peaks():
 SMS, FP32_LANES = 152, 128
 
 # DRAM bytes (read + write) of one launch of the multiply-accumulate group kernel at the
-# default 64-channel workload: ncu capture at 32 channels (profiles/
-# k_mac_signal_group_plain_at_scale_32ch.md) scaled by the channel count.
+# default 64-channel workload: an ncu capture of the same kernel at 32 channels, scaled by
+# the channel count (the traffic grows in proportion to it).
 MAC_TRAFFIC_BYTES = 2 * (311.548160e6 + 215.897088e6)
 
 
