@@ -202,6 +202,37 @@ TVOLAP_API int tvolap_inverse_ola(tvolap_t h, const float *Y_dev, int n_blocks, 
 /* Copy the M partition spectra of one slot to out_dev (device float2 [M][P]). */
 TVOLAP_API int tvolap_bank_spectra(tvolap_t h, int slot, float *out_dev);
 
+/* Size of the fixed device scratch array used by tvolap_process_signal_static. */
+#define TVOLAP_STATIC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * tvolap_process_signal without any device allocation. The paper has no
+ * counterpart; this serves callers that must not allocate device memory once
+ * they are running (a real-time audio callback with a hard deadline, a process
+ * under a device-memory budget fixed at start-up). tvolap_process_signal grows
+ * a workspace with cudaMalloc; this call instead keeps its scratch (the block
+ * spectra X and Y) in one file-scope device array of TVOLAP_STATIC_SCRATCH_BYTES
+ * bytes, which every GPU that loads the library holds until the process exits.
+ * Arguments, results and stream ordering are those of tvolap_process_signal,
+ * and the caller still passes every input and output buffer.
+ *  - Returns TVOLAP_ERR_CAPACITY when 8 * P * n_blocks * (n_in + n_out) exceeds
+ *    TVOLAP_STATIC_SCRATCH_BYTES, with nothing enqueued.
+ *  - The first call on a device looks the array's device address up
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - All calls, from every handle on a device, share the one array; calls that
+ *    overlap on the GPU (other streams, other threads) race on it and give
+ *    undefined results. Each call writes all the scratch it reads, so nothing
+ *    left by an earlier call is used.
+ *  - Calls no cudaMalloc, cudaFree or allocating library routine. The
+ *    multiply-accumulate runs the cp.async kernel, which needs no scratch.
+ */
+TVOLAP_API int tvolap_process_signal_static(tvolap_t h, const float *x_dev, int64_t N,
+                                            int64_t x_stride, const int32_t *sched_a,
+                                            const int32_t *sched_b, const float *sched_alpha,
+                                            int64_t sched_stride, float *y_dev, int64_t out_len,
+                                            int64_t y_stride);
+
 /* Options of tvolap_set_option. */
 typedef enum tvolap_option {
     /* Staging of the offline multiply-accumulate: 0 = tiled bulk tensor copies

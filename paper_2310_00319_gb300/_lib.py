@@ -43,6 +43,9 @@ SIGNATURES = {
     "tvolap_bank_spectra": (c_int, [c_void_p, c_int, c_void_p]),
     "tvolap_check": (c_int, [c_void_p]),
     "tvolap_set_option": (c_int, [c_void_p, c_int, c_int]),
+    "tvolap_process_signal_static": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p,
+                                             c_void_p, c_void_p, c_int64, c_void_p, c_int64,
+                                             c_int64]),
 }
 
 STATUS = {0: "TVOLAP_OK", -1: "TVOLAP_ERR_ARG", -2: "TVOLAP_ERR_OOM", -3: "TVOLAP_ERR_CUDA",
