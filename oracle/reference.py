@@ -23,6 +23,14 @@ Functions and the passages of arxiv 2310.00319 they follow:
 * ``block_spectra``        -- Eqs. 1, 3, 5 for chosen blocks (input spectra X).
 * ``partition_spectra``    -- Eqs. 2, 4, 6 (transfer-function partitions H).
 * ``halfbin_dft``          -- the definition of the half-bin DFT, by summation.
+* ``params_forward``       -- Eqs. 5, 7, 8-12 with free per-block partition
+                              spectra P[t, m, k] in place of transforms of
+                              impulse responses (the trainable model).
+* ``params_grad``          -- the hand-derived adjoint of ``params_forward``
+                              (gradients w.r.t. P and x, PyTorch's convention
+                              dL/dRe + i dL/dIm for complex parameters); pinned
+                              against FP64 finite differences in
+                              tests/test_oracle_grad_pins.py.
 
 Readings of the paper that these functions take (each is pinned by a test in
 tests/test_oracle_pins.py):
@@ -369,3 +377,89 @@ def tvolap_spectral(x, irs, L, sched_a, sched_b=None, sched_alpha=None, out_len=
             if 0 <= n < out_len:
                 out[n] += yhat[i]
     return out[:out_len]
+
+
+# --------------------------------------------------------------------------- spectral parameters
+# A model whose filter partitions are free per-block spectra P[t, m, k] (k < 2L,
+# half-bin grid) instead of transforms of impulse responses: Eqs. 5, 7, 8-12 with
+# H_l(k, m) = P[t = l + 1, m, k]. A real block's spectrum on this grid is
+# determined by its 2L lower bins (X(4L-1-k) = conj X(k)); a parameter spectrum
+# is read the same way, so the inverse transform of each output block is real.
+
+def _halfbin_full(V):
+    """Extend lower-half bins [.., 2L] to the conjugate-symmetric 4L bins."""
+    return np.concatenate([V, np.conj(V[..., ::-1])], axis=-1)
+
+
+def params_forward(x, Pspec, L, out_len=None, pr_lag=2):
+    """y = TVOLAP of one channel x with per-block spectra Pspec[t, m, k]
+    (t = l + 1 < n_blocks, m < M, k < 2L), FP64, literal Eqs. 5, 7, 8-12."""
+    x = np.asarray(x, np.float64).ravel()
+    N = x.shape[0]
+    Pspec = np.asarray(Pspec, np.complex128)
+    nb, M, P2 = Pspec.shape
+    assert P2 == 2 * L
+    if out_len is None:
+        out_len = N
+    assert nb >= n_out_blocks(out_len, L)
+    X = block_spectra(x, L, list(range(-1, nb - 1)), grid="halfbin")[:, :2 * L]
+    out = np.zeros(out_len + 4 * L)
+    for t in range(nb):
+        Y = np.zeros(2 * L, np.complex128)
+        for m in range(M):
+            if t - 2 * m >= 0:
+                Y += Pspec[t, m] * X[t - 2 * m]
+        yb = np.real(_idft4l(_halfbin_full(Y), "halfbin"))       # Eq. 8, length 4L
+        l = t - 1
+        for i in range(4 * L):                                  # Eqs. 9-12: add at l*L
+            n = l * L + i
+            if 0 <= n < out_len:
+                out[n] += yb[i]
+    return out[:out_len]
+
+
+def params_grad(x, Pspec, L, g):
+    """Hand adjoint of params_forward for a real loss with dL/dy = g:
+    returns (dP, dx) with dP = dL/dRe P + i dL/dIm P.
+
+      G(t) = (1/2L) sum_{n<4L} g(l*L + n) e^{-i pi n (2k+1) / 4L}     (adjoint of Eq. 8)
+      dP(t, m) = G(t) conj X(t - 2m)                                  (adjoint of Eq. 7)
+      dX(q) = sum_m G(q + 2m) conj P(q + 2m, m)
+      dx(l*L + n) += w(n) Re sum_{k<2L} dX_q(k) e^{+i pi n (2k+1) / 4L}, n < 2L  (Eqs. 1, 5)
+    """
+    x = np.asarray(x, np.float64).ravel()
+    g = np.asarray(g, np.float64).ravel()
+    N, out_len = x.shape[0], g.shape[0]
+    Pspec = np.asarray(Pspec, np.complex128)
+    nb, M, _ = Pspec.shape
+    X = block_spectra(x, L, list(range(-1, nb - 1)), grid="halfbin")[:, :2 * L]
+    n4 = np.arange(4 * L)
+    k2 = np.arange(2 * L)
+    E = np.exp(-1j * np.pi * np.outer(n4, 2 * k2 + 1) / (4 * L))      # [4L, 2L]
+    G = np.zeros((nb, 2 * L), np.complex128)
+    for t in range(nb):
+        seg = np.zeros(4 * L)
+        for i in range(4 * L):
+            n = (t - 1) * L + i
+            if 0 <= n < out_len:
+                seg[i] = g[n]
+        G[t] = (seg @ E) / (2 * L)
+    dP = np.zeros_like(Pspec)
+    dX = np.zeros((nb, 2 * L), np.complex128)
+    for t in range(nb):
+        for m in range(M):
+            q = t - 2 * m
+            if q >= 0:
+                dP[t, m] = G[t] * np.conj(X[q])
+                dX[q] += G[t] * np.conj(Pspec[t, m])
+    w = hann_half(L)
+    dx = np.zeros(N)
+    Einv = np.exp(1j * np.pi * np.outer(np.arange(2 * L), 2 * k2 + 1) / (4 * L))   # [2L, 2L]
+    for q in range(nb):
+        dxw = np.real(Einv @ dX[q])
+        l = q - 1
+        for i in range(2 * L):
+            s = l * L + i
+            if 0 <= s < N:
+                dx[s] += w[i] * dxw[i]
+    return dP, dx
