@@ -379,6 +379,103 @@ def run_stream(args, wl, dev, stream, ticks=600, warm=50):
             "logical_gbs_per_tick": round(bpt / (ms.mean() * 1e-3) / 1e9, 1)}
 
 
+# --------------------------------------------------------------------------- adjoint
+def run_adjoint(args):
+    """Differentiable model at 16 channels x 240000 samples, L = 256, M = 47:
+    one training step = forward (block spectra, Eq. 7 with per-block parameter
+    spectra, inverse + overlap-add) and backward (gradient spectra, fused
+    adjoint of Eq. 7, input gradient), the input spectra recomputed per segment
+    of 32 blocks. The parameter kernels stream P (2.9 GB) and dP: HBM-bound."""
+    import torch
+    from paper_2310_00319_gb300 import Plan
+    from synth import workloads as W
+    dev = torch.device("cuda", 0)
+    d = W.differentiable(seed=4)
+    C, N = d["x"].shape
+    L, M, nb, P = d["L"], d["M"], d["n_blocks"], 2 * d["L"]
+    plan = Plan(L, M, n_in=C, n_out=C, n_slots=1, device=dev)
+    x = torch.from_numpy(d["x"]).to(dev)
+    Pm = torch.from_numpy(d["P"]).to(dev)
+    r = torch.from_numpy(d["r"]).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    K = 32
+    Y = torch.empty((C, nb, P), dtype=torch.complex64, device=dev)
+    dP = torch.empty_like(Pm)
+    dx = torch.empty_like(x)
+    names = ["fwd_spectra", "mac_params", "inverse_ola", "adjoint_output", "bwd_spectra",
+             "adjoint_mac", "adjoint_input"]
+
+    def step(ev):
+        tm = {k: 0.0 for k in names}
+        marks = []
+
+        def mark(name):
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            marks.append((name, e))
+        mark("start")
+        for t0 in range(0, nb, K):                      # forward, segments with history
+            tc = min(K, nb - t0)
+            x0 = max(0, t0 - 2 * (M - 1))
+            X = plan.block_spectra(x, x0, t0 + tc - x0)
+            mark("fwd_spectra")
+            Ys = plan.mac_params(X, x0, Pm, t0, tc)
+            mark("mac_params")
+            Y[:, t0:t0 + tc] = Ys
+            mark("copy")
+        plan.inverse_ola(Y, N)
+        mark("inverse_ola")
+        G = plan.adjoint_output(r, 0, nb)
+        mark("adjoint_output")
+        dx.zero_()
+        mark("copy")
+        for q0 in range(0, nb, K):
+            qc = min(K, nb - q0)
+            X = plan.block_spectra(x, q0, qc)
+            mark("bwd_spectra")
+            dX = plan.adjoint_mac(G, 0, X, q0, Pm, q0, qc, dP)
+            mark("adjoint_mac")
+            plan.adjoint_input(dX, q0, dx)
+            mark("adjoint_input")
+        ev.append(marks)
+
+    for _ in range(args.warmup):
+        step([])
+    torch.cuda.synchronize(dev)
+    evs = []
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        t0e.record(stream)
+        for _ in range(args.steps):
+            step(evs)
+        t1e.record(stream)
+        torch.cuda.synchronize(dev)
+    plan.check()
+    ms = t0e.elapsed_time(t1e) / args.steps
+    tot = {k: 0.0 for k in names + ["copy"]}
+    for marks in evs:
+        for (n0, e0), (n1, e1) in zip(marks[:-1], marks[1:]):
+            tot[n1] += e0.elapsed_time(e1)
+    tot = {k: v / args.steps for k, v in tot.items()}
+    pbytes = float(Pm.numel() * 8)
+    peaks, kind = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    adj_gbs = 2 * pbytes / (tot["adjoint_mac"] * 1e-3) / 1e9      # read P, write dP
+    fwd_gbs = pbytes / (tot["mac_params"] * 1e-3) / 1e9           # read P
+    return {"metric": "channel-samples/s (forward + backward)",
+            "value": round(C * N / (ms * 1e-3), 1), "unit": "channel-samples/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "differentiable_16ch_L256_M47_N240000", "segment_blocks": K,
+                       "param_bytes": pbytes},
+            "roofline": {"bound": "hbm", "achieved": round(adj_gbs, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(adj_gbs / hbm, 4), "traffic": None,
+                         "kernel": "k_adjoint_mac (read P, write dP)"},
+            "mac_params_gbs": round(fwd_gbs, 1),
+            "stages_ms": {k: round(v, 4) for k, v in tot.items()},
+            "peaks": kind, "clocks": clk.summary()}
+
+
 # --------------------------------------------------------------------------- oracle
 _F64 = {}
 
@@ -452,6 +549,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain_at_scale",
+                    choices=["plain_at_scale", "adjoint"])
     ap.add_argument("--channels", type=int, default=64)
     ap.add_argument("--samples", type=int, default=480000)
     ap.add_argument("--traffic", type=float, default=None,
@@ -465,6 +564,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         out = run_reference(args)
+    elif args.workload == "adjoint":
+        out = run_adjoint(args)
     else:
         out = run_ours(args)
     if out is not None:

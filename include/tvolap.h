@@ -199,6 +199,73 @@ TVOLAP_API int tvolap_mac(tvolap_t h, const float *X_dev, int n_blocks, const in
 TVOLAP_API int tvolap_inverse_ola(tvolap_t h, const float *Y_dev, int n_blocks, float *y_dev,
                        int64_t out_len, int64_t y_stride);
 
+/*
+ * ---- Differentiable TVOLAP (free per-block partition spectra) -------------
+ * A model in which the filter partitions of Eq. 7 are free spectra
+ * P[o][t][m][k] (t < p_blocks output blocks, m < M, k < P; the same half-bin
+ * grid and storage as every spectrum here) instead of transforms of impulse
+ * responses: Y(t) = sum_{m, t-2m >= 0} P(t, m) X(t - 2m), followed by Eqs. 8-12
+ * (tvolap_inverse_ola). Gradients use the convention dL/dRe + i dL/dIm for
+ * complex values. All buffers of these calls must be 16-byte aligned; block
+ * ranges let a caller recompute input spectra segment by segment.
+ */
+
+/* Spectra of input blocks t_first .. t_first + t_count - 1 (Eqs. 1, 3, 5):
+   X_dev float2 [n_in][t_count][P]. */
+TVOLAP_API int tvolap_block_spectra(tvolap_t h, const float *x_dev, int64_t N, int64_t x_stride,
+                                    int64_t t_first, int t_count, float *X_dev);
+
+/*
+ * Y[o][i] = sum_{m < M, t - 2m >= 0} P[o][t][m] * X[in(o)][t - 2m - x_first],
+ * t = t_first + i, i < t_count (Eq. 7 with the parameters as filter).
+ *   X_dev  float2 [n_in][x_count][P], rows x_first .. x_first + x_count - 1;
+ *          must hold every row needed: x_first <= max(0, t_first - 2(M-1)) and
+ *          x_first + x_count >= t_first + t_count
+ *   P_dev  float2 [n_out][p_blocks][M][P]; t_first + t_count <= p_blocks
+ *   Y_dev  float2 [n_out][t_count][P]
+ */
+TVOLAP_API int tvolap_mac_params(tvolap_t h, const float *X_dev, int64_t x_first, int x_count,
+                                 const float *P_dev, int64_t p_blocks, int64_t t_first,
+                                 int t_count, float *Y_dev);
+
+/*
+ * Adjoint of Eq. 8 (with the overlap-add of Eqs. 9-12) for g = dL/dy:
+ * G[o][i] = dL/dY(t) = (1/2L) sum_{n<4L} g[o][(t-1)L + n] e^{-i pi n (2k+1)/4L},
+ * t = t_first + i; samples outside [0, g_len) count as zero.
+ *   g_dev float [n_out][g_stride];  G_dev float2 [n_out][t_count][P]
+ */
+TVOLAP_API int tvolap_adjoint_output(tvolap_t h, const float *g_dev, int64_t g_len,
+                                     int64_t g_stride, int64_t t_first, int t_count,
+                                     float *G_dev);
+
+/*
+ * Adjoint of Eq. 7, for input blocks q = q_first .. q_first + q_count - 1:
+ *   dX[o][q - q_first] = sum_{m, q+2m < p_blocks} G(q + 2m) conj P(q + 2m, m)
+ *   dP(t, m) = G(t) conj X(q)   for every t, m with t - 2m = q
+ * and, when q_first == 0, dP(t, m) = 0 for t < 2m. Called over ranges that
+ * cover 0 .. p_blocks - 1, this writes all of dP.
+ *   G_dev  float2 [n_out][g_count][P], rows g_first ..; needs g_first <= q_first
+ *          and g_first + g_count >= min(p_blocks, q_first + q_count + 2(M-1))
+ *   X_dev  float2 [n_in][x_count][P], rows x_first ..; must cover the q range
+ *   P_dev, dP_dev  float2 [n_out][p_blocks][M][P];  dX_dev float2 [n_out][q_count][P]
+ * Requires identity routing (n_in == n_out, output o reads input o).
+ */
+TVOLAP_API int tvolap_adjoint_mac(tvolap_t h, const float *G_dev, int64_t g_first, int g_count,
+                                  const float *X_dev, int64_t x_first, int x_count,
+                                  const float *P_dev, int64_t p_blocks, int64_t q_first,
+                                  int q_count, float *dP_dev, float *dX_dev);
+
+/*
+ * Adjoint of Eqs. 1, 3, 5: for each block q of the range,
+ *   dx[c][(q-1)L + n] += w(n) Re sum_{k<P} dX[c][q - q_first](k) e^{+i pi n (2k+1)/4L},
+ * 0 <= n < 2L, samples outside [0, N) dropped. Adds to what dx_dev holds, so
+ * ranges can be processed one after another (zero dx_dev first).
+ *   dX_dev float2 [n_in][q_count][P];  dx_dev float [n_in][x_stride]
+ * Requires identity routing.
+ */
+TVOLAP_API int tvolap_adjoint_input(tvolap_t h, const float *dX_dev, int64_t q_first, int q_count,
+                                    float *dx_dev, int64_t N, int64_t x_stride);
+
 /* Copy the M partition spectra of one slot to out_dev (device float2 [M][P]). */
 TVOLAP_API int tvolap_bank_spectra(tvolap_t h, int slot, float *out_dev);
 

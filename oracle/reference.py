@@ -31,6 +31,8 @@ Functions and the passages of arxiv 2310.00319 they follow:
                               dL/dRe + i dL/dIm for complex parameters); pinned
                               against FP64 finite differences in
                               tests/test_oracle_grad_pins.py.
+* ``params_grad_sampled``  -- chosen entries of the same gradients, each from
+                              the definitions on its own (full-size checks).
 
 Readings of the paper that these functions take (each is pinned by a test in
 tests/test_oracle_pins.py):
@@ -462,4 +464,52 @@ def params_grad(x, Pspec, L, g):
             s = l * L + i
             if 0 <= s < N:
                 dx[s] += w[i] * dxw[i]
+    return dP, dx
+
+
+def params_grad_sampled(x, Pspec, L, g, dP_idx, dx_idx):
+    """Selected entries of params_grad, each computed on its own from the same
+    definitions: dP[t, m, k] for the (t, m, k) triples in dP_idx and
+    dx[s] for s in dx_idx, for one channel (x [N], Pspec [nb, M, 2L], g [out_len])."""
+    x = np.asarray(x, np.float64).ravel()
+    g = np.asarray(g, np.float64).ravel()
+    N, out_len = x.shape[0], g.shape[0]
+    nb, M = Pspec.shape[0], Pspec.shape[1]
+    k2 = np.arange(2 * L)
+    n4 = np.arange(4 * L)
+    E = np.exp(-1j * np.pi * np.outer(n4, 2 * k2 + 1) / (4 * L))
+    cacheG, cacheX = {}, {}
+
+    def G(t):
+        if t not in cacheG:
+            seg = np.zeros(4 * L)
+            for i in range(4 * L):
+                n = (t - 1) * L + i
+                if 0 <= n < out_len:
+                    seg[i] = g[n]
+            cacheG[t] = (seg @ E) / (2 * L)
+        return cacheG[t]
+
+    def X(q):
+        if q not in cacheX:
+            cacheX[q] = block_spectra(x, L, [q - 1], grid="halfbin")[0, :2 * L]
+        return cacheX[q]
+
+    dP = np.array([G(t)[k] * np.conj(X(t - 2 * m)[k]) if t - 2 * m >= 0 else 0.0
+                   for (t, m, k) in dP_idx], dtype=np.complex128)
+    w = hann_half(L)
+    dx = np.zeros(len(dx_idx))
+    for j, s in enumerate(dx_idx):
+        acc = 0.0
+        for q in (s // L, s // L + 1):
+            n = s - (q - 1) * L
+            if not (0 <= n < 2 * L) or q >= nb:
+                continue
+            dXq = np.zeros(2 * L, np.complex128)
+            for m in range(M):
+                t = q + 2 * m
+                if t < nb:
+                    dXq += G(t) * np.conj(np.asarray(Pspec[t, m], np.complex128))
+            acc += w[n] * np.real(np.sum(dXq * np.exp(1j * np.pi * n * (2 * k2 + 1) / (4 * L))))
+        dx[j] = acc
     return dP, dx

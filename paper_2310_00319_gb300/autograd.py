@@ -1,0 +1,66 @@
+"""TVOLAP with trainable per-block partition spectra, as a torch.autograd.Function.
+
+The forward and backward passes are the library's kernels (Eq. 7 with free
+spectra P, its adjoint, and the adjoints of the transforms) called through the
+C ABI; this module only orders the calls and holds the tensors.
+
+    y = spectral_tvolap(x, P, plan)          # x [C, N], P [C, n_blocks, M, 2L] complex64
+    loss = ((y - target) ** 2).mean(); loss.backward()
+
+With ``segment=K`` the input spectra X are never held for all blocks at once:
+the forward computes them per segment of K output blocks plus the 2(M-1)-block
+history the segment reads, and the backward recomputes them per segment of K
+blocks (the adjoint of Eq. 7 at block q reads only X(q)). Results are the same
+as without segments.
+"""
+from __future__ import annotations
+
+import torch
+
+from .tvolap import Plan, n_blocks_for
+
+
+class SpectralTvolap(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, Pspec, plan: Plan, out_len: int, segment: int | None):
+        C, N = x.shape
+        nb = n_blocks_for(out_len, plan.L)
+        if Pspec.shape != (plan.n_out, nb, plan.M, plan.P):
+            raise ValueError(f"P must be [{plan.n_out}, {nb}, {plan.M}, {plan.P}]")
+        x = x.contiguous()
+        Pspec = Pspec.contiguous()
+        K = nb if not segment else int(segment)
+        if K >= nb:
+            X = plan.block_spectra(x, 0, nb)
+            Y = plan.mac_params(X, 0, Pspec, 0, nb)
+        else:
+            Y = torch.empty((plan.n_out, nb, plan.P), dtype=torch.complex64, device=x.device)
+            for t0 in range(0, nb, K):
+                tc = min(K, nb - t0)
+                x0 = max(0, t0 - 2 * (plan.M - 1))
+                X = plan.block_spectra(x, x0, t0 + tc - x0)
+                Y[:, t0:t0 + tc] = plan.mac_params(X, x0, Pspec, t0, tc)
+        y = plan.inverse_ola(Y, out_len)
+        ctx.save_for_backward(x, Pspec)
+        ctx.plan, ctx.nb, ctx.K = plan, nb, K
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        x, Pspec = ctx.saved_tensors
+        plan, nb, K = ctx.plan, ctx.nb, ctx.K
+        G = plan.adjoint_output(gy.contiguous(), 0, nb)
+        dP = torch.empty_like(Pspec)
+        dx = torch.zeros_like(x) if ctx.needs_input_grad[0] else None
+        for q0 in range(0, nb, K):
+            qc = min(K, nb - q0)
+            X = plan.block_spectra(x, q0, qc)
+            dX = plan.adjoint_mac(G, 0, X, q0, Pspec, q0, qc, dP)
+            if dx is not None:
+                plan.adjoint_input(dX, q0, dx)
+        return dx, dP, None, None, None
+
+
+def spectral_tvolap(x, Pspec, plan: Plan, out_len: int | None = None, segment: int | None = None):
+    """y [C, out_len] from x [C, N] and per-block spectra Pspec [C, n_blocks, M, 2L]."""
+    return SpectralTvolap.apply(x, Pspec, plan, x.shape[1] if out_len is None else out_len, segment)

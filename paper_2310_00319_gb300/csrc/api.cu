@@ -190,7 +190,11 @@ int tvolap_create(tvolap_t *out, int L, int partitions, int fft_len, int n_in, i
         free_plan(h);
         return TVOLAP_ERR_OOM;
     }
-    for (int o = 0; o < n_out; ++o) o2i[o] = out_to_in ? out_to_in[o] : o;
+    h->identity_routing = (n_in == n_out);
+    for (int o = 0; o < n_out; ++o) {
+        o2i[o] = out_to_in ? out_to_in[o] : o;
+        if (o2i[o] != o) h->identity_routing = 0;
+    }
     e = cudaMemcpyAsync(h->out_to_in, o2i, sizeof(int32_t) * n_out, cudaMemcpyHostToDevice,
                         h->stream);
     if (e == cudaSuccess)
@@ -379,6 +383,82 @@ int tvolap_check(tvolap_t h)
         return (err & 2u) ? TVOLAP_ERR_TIMEOUT : TVOLAP_ERR_ARG;
     }
     return TVOLAP_OK;
+}
+
+static bool a16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int tvolap_block_spectra(tvolap_t h, const float *x_dev, int64_t N, int64_t x_stride,
+                         int64_t t_first, int t_count, float *X_dev)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (N < 0 || x_stride < N || t_first < 0 || t_count < 0 || (N > 0 && !x_dev) ||
+        (t_count > 0 && !X_dev))
+        return TVOLAP_ERR_ARG;
+    return cuda_status(launch_block_spectra(h, x_dev, N, x_stride, t_first, t_count,
+                                            reinterpret_cast<float2 *>(X_dev)));
+}
+
+int tvolap_mac_params(tvolap_t h, const float *X_dev, int64_t x_first, int x_count,
+                      const float *P_dev, int64_t p_blocks, int64_t t_first, int t_count,
+                      float *Y_dev)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (t_count < 0 || t_first < 0 || x_first < 0 || x_count < 0) return TVOLAP_ERR_ARG;
+    if (t_count == 0) return TVOLAP_OK;
+    if (!X_dev || !P_dev || !Y_dev || !a16(X_dev) || !a16(P_dev) || !a16(Y_dev)) return TVOLAP_ERR_ARG;
+    const int64_t need_lo = t_first - 2 * (int64_t)(h->M - 1) > 0 ? t_first - 2 * (int64_t)(h->M - 1) : 0;
+    if (t_first + t_count > p_blocks || x_first > need_lo || x_first + x_count < t_first + t_count)
+        return TVOLAP_ERR_ARG;
+    return cuda_status(launch_mac_params(h, reinterpret_cast<const float2 *>(X_dev), x_first, x_count,
+                                         reinterpret_cast<const float2 *>(P_dev), p_blocks, t_first,
+                                         t_count, reinterpret_cast<float2 *>(Y_dev)));
+}
+
+int tvolap_adjoint_output(tvolap_t h, const float *g_dev, int64_t g_len, int64_t g_stride,
+                          int64_t t_first, int t_count, float *G_dev)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (g_len < 0 || g_stride < g_len || t_first < 0 || t_count < 0 || (g_len > 0 && !g_dev) ||
+        (t_count > 0 && !G_dev))
+        return TVOLAP_ERR_ARG;
+    return cuda_status(launch_adjoint_output(h, g_dev, g_len, g_stride, t_first, t_count,
+                                             reinterpret_cast<float2 *>(G_dev)));
+}
+
+int tvolap_adjoint_mac(tvolap_t h, const float *G_dev, int64_t g_first, int g_count,
+                       const float *X_dev, int64_t x_first, int x_count, const float *P_dev,
+                       int64_t p_blocks, int64_t q_first, int q_count, float *dP_dev, float *dX_dev)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (!h->identity_routing) return TVOLAP_ERR_ARG;
+    if (q_count < 0 || q_first < 0 || g_first < 0 || x_first < 0 || g_count < 0 || x_count < 0)
+        return TVOLAP_ERR_ARG;
+    if (q_count == 0) return TVOLAP_OK;
+    if (!G_dev || !X_dev || !P_dev || !dP_dev || !dX_dev || !a16(G_dev) || !a16(X_dev) ||
+        !a16(P_dev) || !a16(dP_dev) || !a16(dX_dev))
+        return TVOLAP_ERR_ARG;
+    int64_t g_need = q_first + q_count + 2 * (int64_t)(h->M - 1);
+    if (g_need > p_blocks) g_need = p_blocks;
+    if (q_first + q_count > p_blocks || x_first > q_first || x_first + x_count < q_first + q_count ||
+        g_first > q_first || g_first + g_count < g_need)
+        return TVOLAP_ERR_ARG;
+    return cuda_status(launch_adjoint_mac(
+        h, reinterpret_cast<const float2 *>(G_dev), g_first, g_count,
+        reinterpret_cast<const float2 *>(X_dev), x_first, x_count,
+        reinterpret_cast<const float2 *>(P_dev), p_blocks, q_first, q_count,
+        reinterpret_cast<float2 *>(dP_dev), reinterpret_cast<float2 *>(dX_dev)));
+}
+
+int tvolap_adjoint_input(tvolap_t h, const float *dX_dev, int64_t q_first, int q_count,
+                         float *dx_dev, int64_t N, int64_t x_stride)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (!h->identity_routing) return TVOLAP_ERR_ARG;
+    if (q_first < 0 || q_count < 0 || N < 0 || x_stride < N) return TVOLAP_ERR_ARG;
+    if (q_count == 0 || N == 0) return TVOLAP_OK;
+    if (!dX_dev || !dx_dev) return TVOLAP_ERR_ARG;
+    return cuda_status(launch_adjoint_input(h, reinterpret_cast<const float2 *>(dX_dev), q_first,
+                                            q_count, dx_dev, N, x_stride));
 }
 
 int tvolap_set_option(tvolap_t h, int option, int value)

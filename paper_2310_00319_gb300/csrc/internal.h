@@ -10,6 +10,7 @@ struct tvolap_plan {
     int L, M, P;                  // hop, partitions, complex bins per spectrum (2L)
     int lgP;                      // log2(P)
     int n_in, n_out;
+    int identity_routing;         // n_in == n_out and output o reads input o
     int n_user_slots;             // slots written by tvolap_load_bank
     int n_slots_total;            // user + one private slot per output
     int null_slot;                // all-zero slot that replaces invalid indices
@@ -50,6 +51,12 @@ namespace tvolap {
 cudaError_t launch_tables(tvolap_plan *h);
 cudaError_t launch_forward_signal(tvolap_plan *h, const float *x, int64_t N, int64_t x_stride,
                                   int n_blocks, float2 *X);
+cudaError_t launch_block_spectra(tvolap_plan *h, const float *x, int64_t N, int64_t x_stride,
+                                 int64_t t_first, int n_blocks, float2 *X);
+cudaError_t launch_adjoint_output(tvolap_plan *h, const float *g, int64_t g_len, int64_t g_stride,
+                                  int64_t t_first, int n_blocks, float2 *G);
+cudaError_t launch_adjoint_input(tvolap_plan *h, const float2 *dX, int64_t q_first, int q_count,
+                                 float *dx, int64_t N, int64_t x_stride);
 cudaError_t launch_bank(tvolap_plan *h, int first_slot, int count, const float *ir, int ir_len,
                         int64_t ir_stride);
 cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, float *y,
@@ -63,6 +70,15 @@ cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, con
                               float2 *Y);
 // api.cu: grow the overflow list of the offline multiply-accumulate
 cudaError_t ensure_overflow(tvolap_plan *h, int64_t entries);
+
+// kernels_adjoint.cu
+cudaError_t launch_mac_params(tvolap_plan *h, const float2 *X, int64_t x_first, int x_count,
+                              const float2 *Pm, int64_t p_blocks, int64_t t_first, int t_count,
+                              float2 *Y);
+cudaError_t launch_adjoint_mac(tvolap_plan *h, const float2 *G, int64_t g_first, int g_count,
+                               const float2 *X, int64_t x_first, int x_count, const float2 *Pm,
+                               int64_t p_blocks, int64_t q_first, int q_count, float2 *dP,
+                               float2 *dX);
 
 // kernels_mac.cu
 cudaError_t launch_mac_signal_lsu(tvolap_plan *h, const float2 *X, int n_blocks,

@@ -1,0 +1,152 @@
+// Differentiable TVOLAP: Eq. 7 with free per-block partition spectra, and its
+// adjoint (sm_103a).
+//
+// Parameters P[o][t][m][k] (t < p_blocks, m < M, k < P) replace the filter
+// spectra of Eq. 7: Y(t) = sum_{m, t-2m >= 0} P(t, m) X(t - 2m). Nothing in P is
+// reused across blocks, so both kernels stream P once from HBM and are
+// bandwidth-bound; X and the gradient spectra G are small and come from L2.
+//
+//   k_mac_params   Y(t) for t in a range.
+//   k_adjoint_mac  for q in a range: dX(q) = sum_m G(q + 2m) conj P(q + 2m, m)
+//                  (the delay line run backwards) and, in the same pass, every
+//                  dP(t, m) with t - 2m = q: dP(t, m) = G(t) conj X(q). When the
+//                  range starts at 0, extra threads for q = -(2M-2) .. -1 write
+//                  the zero gradients of the P entries that only ever multiply
+//                  blocks before the signal.
+// A thread owns two bins (16-byte loads and stores); a CTA of 128 threads
+// covers 256 bins and loops over wider spectra.
+#include "fft_core.cuh"
+#include "internal.h"
+
+namespace tvolap {
+
+namespace {
+
+__device__ __forceinline__ void cmac4(float4 &acc, float4 a, float4 b)    // acc += a * b
+{
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+    acc.z = fmaf(a.z, b.z, acc.z);
+    acc.z = fmaf(-a.w, b.w, acc.z);
+    acc.w = fmaf(a.z, b.w, acc.w);
+    acc.w = fmaf(a.w, b.z, acc.w);
+}
+
+__device__ __forceinline__ void cmacc4(float4 &acc, float4 a, float4 b)   // acc += a * conj(b)
+{
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(a.y, b.y, acc.x);
+    acc.y = fmaf(a.y, b.x, acc.y);
+    acc.y = fmaf(-a.x, b.y, acc.y);
+    acc.z = fmaf(a.z, b.z, acc.z);
+    acc.z = fmaf(a.w, b.w, acc.z);
+    acc.w = fmaf(a.w, b.z, acc.w);
+    acc.w = fmaf(-a.z, b.w, acc.w);
+}
+
+__device__ __forceinline__ float4 mulc4(float4 a, float4 b)               // a * conj(b)
+{
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    cmacc4(r, a, b);
+    return r;
+}
+
+constexpr int AT = 128;   // threads per CTA
+
+// grid: x = t_count, y = outputs
+__global__ void __launch_bounds__(AT)
+k_mac_params(const float4 *__restrict__ X, int64_t x_first, int x_count, const float4 *__restrict__ Pm,
+             int64_t p_blocks, int M, int P4, int64_t t_first, int t_count,
+             const int32_t *__restrict__ out_to_in, float4 *__restrict__ Y)
+{
+    const int o = blockIdx.y;
+    const int64_t i = blockIdx.x;
+    const int64_t t = t_first + i;
+    const int c = out_to_in[o];
+    const float4 *Pt = Pm + ((int64_t)o * p_blocks + t) * M * P4;
+    const float4 *Xc = X + (int64_t)c * x_count * P4;
+    int m_end = (int)(t / 2) + 1;                       // t - 2m >= 0
+    if (m_end > M) m_end = M;
+    for (int k = threadIdx.x; k < P4; k += AT) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+        for (int m = 0; m < m_end; ++m) {
+            const int64_t xr = t - 2 * m - x_first;     // row of X(t - 2m) in the buffer
+            cmac4(acc, __ldg(Pt + (int64_t)m * P4 + k), __ldg(Xc + xr * P4 + k));
+        }
+        Y[((int64_t)o * t_count + i) * P4 + k] = acc;
+    }
+}
+
+// grid: x = q_count + extra (the virtual blocks q < 0 when q_first == 0), y = outputs
+__global__ void __launch_bounds__(AT)
+k_adjoint_mac(const float4 *__restrict__ G, int64_t g_first, int g_count,
+              const float4 *__restrict__ X, int64_t x_first, int x_count,
+              const float4 *__restrict__ Pm, int64_t p_blocks, int M, int P4, int64_t q_first,
+              int q_count, int extra, const int32_t *__restrict__ out_to_in,
+              float4 *__restrict__ dP, float4 *__restrict__ dX)
+{
+    const int o = blockIdx.y;
+    const int64_t q = (int64_t)blockIdx.x < q_count ? q_first + blockIdx.x
+                                                    : -(int64_t)(blockIdx.x - q_count) - 1;
+    const int c = out_to_in[o];
+    const float4 *Go = G + (int64_t)o * g_count * P4;
+    const float4 *Po = Pm + (int64_t)o * p_blocks * M * P4;
+    float4 *dPo = dP + (int64_t)o * p_blocks * M * P4;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = threadIdx.x; k < P4; k += AT) {
+        if (q < 0) {
+            // P(t, m) with t = q + 2m < 2m multiplies only blocks before the signal
+            for (int m = 0; m < M; ++m) {
+                const int64_t t = q + 2 * m;
+                if (t >= 0 && t < p_blocks) dPo[(t * M + m) * P4 + k] = zero;
+            }
+            continue;
+        }
+        const float4 xq = __ldg(X + ((int64_t)c * x_count + (q - x_first)) * P4 + k);
+        float4 acc = zero;
+#pragma unroll 4
+        for (int m = 0; m < M; ++m) {
+            const int64_t t = q + 2 * m;
+            if (t >= p_blocks) break;
+            const float4 g = __ldg(Go + (t - g_first) * P4 + k);
+            cmacc4(acc, g, __ldg(Po + (t * M + m) * P4 + k));
+            dPo[(t * M + m) * P4 + k] = mulc4(g, xq);
+        }
+        dX[((int64_t)o * q_count + (q - q_first)) * P4 + k] = acc;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_mac_params(tvolap_plan *h, const float2 *X, int64_t x_first, int x_count,
+                              const float2 *Pm, int64_t p_blocks, int64_t t_first, int t_count,
+                              float2 *Y)
+{
+    if (t_count <= 0) return cudaSuccess;
+    dim3 grid((unsigned)t_count, (unsigned)h->n_out);
+    k_mac_params<<<grid, AT, 0, h->stream>>>(reinterpret_cast<const float4 *>(X), x_first, x_count,
+                                             reinterpret_cast<const float4 *>(Pm), p_blocks, h->M,
+                                             h->P / 2, t_first, t_count, h->out_to_in,
+                                             reinterpret_cast<float4 *>(Y));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_mac(tvolap_plan *h, const float2 *G, int64_t g_first, int g_count,
+                               const float2 *X, int64_t x_first, int x_count, const float2 *Pm,
+                               int64_t p_blocks, int64_t q_first, int q_count, float2 *dP,
+                               float2 *dX)
+{
+    if (q_count <= 0) return cudaSuccess;
+    const int extra = (q_first == 0) ? 2 * (h->M - 1) : 0;
+    dim3 grid((unsigned)(q_count + extra), (unsigned)h->n_out);
+    k_adjoint_mac<<<grid, AT, 0, h->stream>>>(
+        reinterpret_cast<const float4 *>(G), g_first, g_count, reinterpret_cast<const float4 *>(X),
+        x_first, x_count, reinterpret_cast<const float4 *>(Pm), p_blocks, h->M, h->P / 2, q_first,
+        q_count, extra, h->out_to_in, reinterpret_cast<float4 *>(dP), reinterpret_cast<float4 *>(dX));
+    return cudaGetLastError();
+}
+
+}  // namespace tvolap

@@ -41,7 +41,7 @@ __global__ void k_tables(float2 *tw, float2 *rot, float2 *post, float *win, int 
 
 // Forward real transform of one zero-padded block whose first 2L samples are
 // given by src(n) (n < 2L): fills A, runs the FFT, splits into X via st.
-template <int P, class Src, class Store>
+template <int P, bool FULL = false, class Src, class Store>
 __device__ __forceinline__ void forward_block(float2 *A, float2 *B, int j, bool active, Src src,
                                               const float2 *__restrict__ rot,
                                               const float2 *__restrict__ post,
@@ -52,7 +52,8 @@ __device__ __forceinline__ void forward_block(float2 *A, float2 *B, int j, bool 
     for (int s = 0; s < 8; ++s) {
         const int r = j + s * T;
         float2 z = make_float2(0.f, 0.f);
-        if (s < 4 && active) {                 // r < P/2 = L; the upper half is the zero padding
+        // r < P/2 = L unless FULL: the upper half is the zero padding of Eqs. 3-4
+        if ((FULL || s < 4) && active) {
             z = cmul(src(2 * r), __ldg(rot + r));
         }
         A[r] = z;
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
 k_forward_signal(const float *__restrict__ x, int64_t N, int64_t x_stride, int L, int n_blocks,
                  int64_t total, const float *__restrict__ win, const float2 *__restrict__ rot,
                  const float2 *__restrict__ post, const float2 *__restrict__ tw,
-                 float2 *__restrict__ X)
+                 float2 *__restrict__ X, int64_t t_first)
 {
     constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F;
     extern __shared__ float2 sm[];
@@ -77,7 +78,7 @@ k_forward_signal(const float *__restrict__ x, int64_t N, int64_t x_stride, int L
     const bool active = g < total;
     const int64_t c = active ? g / n_blocks : 0;
     const int64_t t = active ? g % n_blocks : 0;
-    const int64_t start = (t - 1) * (int64_t)L;        // block l = t - 1 starts at l*L
+    const int64_t start = (t_first + t - 1) * (int64_t)L;   // block l = t - 1 starts at l*L
     const float *xc = x + c * x_stride;
     auto src = [&](int n) {
         const int64_t i0 = start + n;
@@ -116,6 +117,39 @@ k_bank(const float *__restrict__ ir, int ir_len, int64_t ir_stride, int M, int L
     float2 *Ho = bank_out + g * P;                     // slots are consecutive [s][m][P]
     forward_block<P>(A, B, j, active, src, rot, post, tw, [&](int k, float2 v) {
         if (active) Ho[k] = v;
+    });
+}
+
+// Adjoint of Eq. 8 for the gradient g = dL/dy of every output: for block
+// t = t_first + i, G[o][i] = (1/2L) * half-bin DFT of the 4L samples
+// g[o][(t-1)L .. (t+3)L) (zeros outside [0, g_len)): all 4L inputs, no window.
+template <int LG>
+__global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
+k_adjoint_output(const float *__restrict__ g, int64_t g_len, int64_t g_stride, int L,
+                 int n_blocks, int64_t total, int64_t t_first, const float2 *__restrict__ rot,
+                 const float2 *__restrict__ post, const float2 *__restrict__ tw,
+                 float2 *__restrict__ G)
+{
+    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F;
+    extern __shared__ float2 sm[];
+    const int f = threadIdx.x / T, j = threadIdx.x % T;
+    float2 *A = sm + f * P, *B = sm + (F + f) * P;
+    const int64_t gi = (int64_t)blockIdx.x * F + f;    // transform = (output, block)
+    const bool active = gi < total;
+    const int64_t o = active ? gi / n_blocks : 0;
+    const int64_t t = active ? gi % n_blocks : 0;
+    const int64_t start = (t_first + t - 1) * (int64_t)L;
+    const float *go = g + o * g_stride;
+    const float scale = 1.0f / (float)P;               // 1 / 2L
+    auto src = [&](int n) {
+        const int64_t i0 = start + n;
+        const float a = (i0 >= 0 && i0 < g_len) ? __ldg(go + i0) : 0.f;
+        const float b = (i0 + 1 >= 0 && i0 + 1 < g_len) ? __ldg(go + i0 + 1) : 0.f;
+        return make_float2(a * scale, b * scale);
+    };
+    float2 *Go = G + gi * P;
+    forward_block<P, true>(A, B, j, active, src, rot, post, tw, [&](int k, float2 v) {
+        if (active) Go[k] = v;
     });
 }
 
@@ -185,6 +219,70 @@ k_inverse_ola(const float2 *__restrict__ Y, int n_blocks, int L, int seg, float 
         const int64_t n = s0 + i;
         if (n < out_len) yo[n] = acc[i];
     }
+}
+
+// Adjoint of Eqs. 1, 3, 5 for the input: dx[c][s] += sum over blocks q of the
+// range with 0 <= n = s - (q-1)L < 2L of w(n) * Re sum_{k<2L} dX_q(k) e^{+i pi n (2k+1)/4L}.
+// The inverse transform below gives (1/2L) Re sum_k ..., so the 2L and the 1/P
+// of the inverse cancel. CTA (segment, channel) owns samples [s0, s0 + seg*L),
+// reached by blocks q = s0/L .. s0/L + seg; contributions are added in
+// increasing q to the value dx already holds.
+template <int LG>
+__global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
+k_adjoint_input(const float2 *__restrict__ dX, int q_count, int64_t q_first, int L, int seg,
+                float *__restrict__ dx, int64_t N, int64_t x_stride, const float *__restrict__ win,
+                const float2 *__restrict__ rot, const float2 *__restrict__ post,
+                const float2 *__restrict__ tw)
+{
+    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F;
+    extern __shared__ float2 sm[];
+    float *acc = reinterpret_cast<float *>(sm + 2 * F * P);
+    const int f = threadIdx.x / T, j = threadIdx.x % T;
+    float2 *A = sm + f * P, *B = sm + (F + f) * P;
+    const int c = blockIdx.y;
+    const int64_t tile0 = (int64_t)blockIdx.x * seg;
+    const int64_t s0 = tile0 * L;
+    const int nseg = seg * L;
+    float *xo = dx + (int64_t)c * x_stride;
+    for (int i = threadIdx.x; i < nseg; i += blockDim.x) acc[i] = (s0 + i < N) ? xo[s0 + i] : 0.f;
+    const float2 *dXc = dX + (int64_t)c * q_count * P;
+    int64_t q_lo = tile0, q_hi = tile0 + seg;             // blocks reaching the segment
+    if (q_lo < q_first) q_lo = q_first;
+    if (q_hi > q_first + q_count - 1) q_hi = q_first + q_count - 1;
+    for (int64_t qb = q_lo; qb <= q_hi; qb += F) {
+        const int64_t q = qb + f;
+        const bool active = q <= q_hi;
+        const float2 *Xq = dXc + (active ? q - q_first : 0) * P;
+        merge_inverse<P>(A, j, post, [&](int k) {
+            return active ? Xq[k] : make_float2(0.f, 0.f);
+        });
+        __syncthreads();
+        float2 *Z = fft_complex<P, true>(A, B, j, tw);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int r = j + s * T;
+            Z[r] = cmulc(Z[r], __ldg(rot + r));
+        }
+        __syncthreads();
+        const float2 *Zbase = Z - f * P;
+        const int64_t w0 = (qb - 1) * L;                 // first sample of block qb
+        const int span = (F + 1) * L;
+        for (int p = threadIdx.x; p < span; p += blockDim.x) {
+            const int64_t a = w0 + p - s0;
+            if (a < 0 || a >= nseg) continue;
+            float v = acc[a];
+            for (int ff = 0; ff < F; ++ff) {
+                if (qb + ff > q_hi) break;
+                const int n = p - ff * L;                // position within block qb+ff
+                if (n >= 0 && n < 2 * L)
+                    v = fmaf(__ldg(win + n), reinterpret_cast<const float *>(Zbase + ff * P)[n], v);
+            }
+            acc[a] = v;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < nseg; i += blockDim.x)
+        if (s0 + i < N) xo[s0 + i] = acc[i];
 }
 
 // Streaming forward: one block per input channel from the L samples of
@@ -312,6 +410,12 @@ static cudaError_t set_smem(Kern k, size_t bytes)
 cudaError_t launch_forward_signal(tvolap_plan *h, const float *x, int64_t N, int64_t x_stride,
                                   int n_blocks, float2 *X)
 {
+    return launch_block_spectra(h, x, N, x_stride, 0, n_blocks, X);
+}
+
+cudaError_t launch_block_spectra(tvolap_plan *h, const float *x, int64_t N, int64_t x_stride,
+                                 int64_t t_first, int n_blocks, float2 *X)
+{
     const int64_t total = (int64_t)h->n_in * n_blocks;
     if (total == 0) return cudaSuccess;
     TVOLAP_DISPATCH(h->lgP, {
@@ -321,7 +425,7 @@ cudaError_t launch_forward_signal(tvolap_plan *h, const float *x, int64_t N, int
         cudaError_t e = set_smem(k_forward_signal<LG>, sm);
         if (e != cudaSuccess) return e;
         k_forward_signal<LG><<<(unsigned)grid, Geo<P>::THREADS, sm, h->stream>>>(
-            x, N, x_stride, h->L, n_blocks, total, h->win, h->rot, h->post, h->tw, X);
+            x, N, x_stride, h->L, n_blocks, total, h->win, h->rot, h->post, h->tw, X, t_first);
     });
     return cudaGetLastError();
 }
@@ -358,6 +462,41 @@ cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, fl
         dim3 grid((unsigned)n_seg, (unsigned)h->n_out);
         k_inverse_ola<LG><<<grid, Geo<P>::THREADS, sm, h->stream>>>(
             Y, n_blocks, h->L, seg, y, out_len, y_stride, h->rot, h->post, h->tw);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_output(tvolap_plan *h, const float *g, int64_t g_len, int64_t g_stride,
+                                  int64_t t_first, int n_blocks, float2 *G)
+{
+    const int64_t total = (int64_t)h->n_out * n_blocks;
+    if (total == 0) return cudaSuccess;
+    TVOLAP_DISPATCH(h->lgP, {
+        constexpr int P = 1 << LG;
+        const int64_t grid = (total + Geo<P>::F - 1) / Geo<P>::F;
+        const size_t sm = smem_fft<LG>();
+        cudaError_t e = set_smem(k_adjoint_output<LG>, sm);
+        if (e != cudaSuccess) return e;
+        k_adjoint_output<LG><<<(unsigned)grid, Geo<P>::THREADS, sm, h->stream>>>(
+            g, g_len, g_stride, h->L, n_blocks, total, t_first, h->rot, h->post, h->tw, G);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_input(tvolap_plan *h, const float2 *dX, int64_t q_first, int q_count,
+                                 float *dx, int64_t N, int64_t x_stride)
+{
+    if (N <= 0 || q_count <= 0) return cudaSuccess;
+    const int seg = inverse_seg(h->L);
+    const int64_t n_seg = (N + (int64_t)seg * h->L - 1) / ((int64_t)seg * h->L);
+    TVOLAP_DISPATCH(h->lgP, {
+        constexpr int P = 1 << LG;
+        const size_t sm = smem_fft<LG>() + (size_t)seg * h->L * sizeof(float);
+        cudaError_t e = set_smem(k_adjoint_input<LG>, sm);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)n_seg, (unsigned)h->n_in);
+        k_adjoint_input<LG><<<grid, Geo<P>::THREADS, sm, h->stream>>>(
+            dX, q_count, q_first, h->L, seg, dx, N, x_stride, h->win, h->rot, h->post, h->tw);
     });
     return cudaGetLastError();
 }

@@ -207,3 +207,49 @@ class Plan:
         y = torch.empty((self.n_out, out_len), dtype=torch.float32, device=self.device)
         self._call("tvolap_inverse_ola", _ptr(Y), Y.shape[1], _ptr(y), int(out_len), int(out_len))
         return y
+
+    # ------------------------------------------------------------------ differentiable model
+    def block_spectra(self, x: torch.Tensor, t_first: int, t_count: int) -> torch.Tensor:
+        """X [n_in, t_count, P]: spectra of blocks t_first .. t_first + t_count - 1."""
+        x = _need(x, torch.float32, self.device, "x", 2)
+        X = torch.empty((self.n_in, t_count, self.P), dtype=torch.complex64, device=self.device)
+        self._call("tvolap_block_spectra", _ptr(x), x.shape[1], x.shape[1], int(t_first),
+                   int(t_count), _ptr(X))
+        return X
+
+    def mac_params(self, X: torch.Tensor, x_first: int, Pspec: torch.Tensor, t_first: int,
+                   t_count: int, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Y [n_out, t_count, P] = Eq. 7 with per-block parameter spectra
+        Pspec [n_out, p_blocks, M, P] for blocks t_first .. t_first + t_count - 1."""
+        X = _need(X, torch.complex64, self.device, "X", 3)
+        Pspec = _need(Pspec, torch.complex64, self.device, "Pspec", 4)
+        if out is None:
+            out = torch.empty((self.n_out, t_count, self.P), dtype=torch.complex64,
+                              device=self.device)
+        self._call("tvolap_mac_params", _ptr(X), int(x_first), X.shape[1], _ptr(Pspec),
+                   Pspec.shape[1], int(t_first), int(t_count), _ptr(out))
+        return out
+
+    def adjoint_output(self, g: torch.Tensor, t_first: int, t_count: int) -> torch.Tensor:
+        """G [n_out, t_count, P] = dL/dY of blocks t_first .. from g = dL/dy."""
+        g = _need(g, torch.float32, self.device, "g", 2)
+        G = torch.empty((self.n_out, t_count, self.P), dtype=torch.complex64, device=self.device)
+        self._call("tvolap_adjoint_output", _ptr(g), g.shape[1], g.shape[1], int(t_first),
+                   int(t_count), _ptr(G))
+        return G
+
+    def adjoint_mac(self, G, g_first, X, x_first, Pspec, q_first, q_count, dP, dX=None):
+        """dP (written in place for t - 2m in the q range) and dX [n_out, q_count, P]."""
+        if dX is None:
+            dX = torch.empty((self.n_out, q_count, self.P), dtype=torch.complex64,
+                             device=self.device)
+        self._call("tvolap_adjoint_mac", _ptr(G), int(g_first), G.shape[1], _ptr(X), int(x_first),
+                   X.shape[1], _ptr(Pspec), Pspec.shape[1], int(q_first), int(q_count), _ptr(dP),
+                   _ptr(dX))
+        return dX
+
+    def adjoint_input(self, dX: torch.Tensor, q_first: int, dx: torch.Tensor):
+        """dx [n_in, N] += the input gradient of blocks q_first .. + dX.shape[1] - 1."""
+        self._call("tvolap_adjoint_input", _ptr(dX), int(q_first), dX.shape[1], _ptr(dx),
+                   dx.shape[1], dx.shape[1])
+        return dx

@@ -173,3 +173,29 @@ def random_case(seed, L, ir_len, N, n_in=1, n_out=None, n_slots=3, out_len=None,
         out_to_in = np.arange(n_out) % n_in
     return Workload(f"random_s{seed}_L{L}", L, _f32(x), _f32(irs), _i32(a), _i32(b),
                     _f32(al), _i32(out_to_in), out_len, meta=dict(seed=seed))
+
+
+def differentiable(seed=4, n_ch=16, N=240000, L=256, ir_len=24000, scale=None, with_target=False):
+    """Trainable-spectra workload: n_ch channels of white noise (sigma 0.1),
+    L = 256, partitions of a 24000-tap response (M = 47), per-block parameter
+    spectra P [n_ch, n_blocks, M, 2L] drawn complex Gaussian with standard
+    deviation `scale` (default 1/sqrt(M) per component), and the weights r of
+    a linear loss sum(r * y) (dL/dy = r). With with_target, also a target bank
+    of 4 decaying responses of ir_len taps switched every 32 blocks."""
+    rng = np.random.default_rng(seed)
+    M = max(1, -(-ir_len // (2 * L)))
+    nb = blocks_for(N, L)
+    x = white(rng, (n_ch, N))
+    s = (1.0 / np.sqrt(M)) if scale is None else scale
+    P = np.empty((n_ch, nb, M, 2 * L), dtype=np.complex64)
+    for c in range(n_ch):
+        re = rng.standard_normal((nb, M, 2 * L), dtype=np.float32)
+        im = rng.standard_normal((nb, M, 2 * L), dtype=np.float32)
+        P[c] = (re + 1j * im) * np.float32(s)
+    r = rng.standard_normal((n_ch, N)).astype(np.float32)
+    out = dict(x=_f32(x), P=P, r=_f32(r), L=L, M=M, n_blocks=nb)
+    if with_target:
+        irs = np.stack([decaying_ir(rng, ir_len, rng.uniform(0.2, 1.0)) for _ in range(4)])
+        out["target_irs"] = _f32(irs)
+        out["target_sched"] = _i32(np.tile(cyclic_schedule(nb, 4, 32)[None, :], (n_ch, 1)))
+    return out

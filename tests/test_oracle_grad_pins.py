@@ -81,3 +81,16 @@ def test_adjoint_planted_mistake_fails():
           - np.dot(r, oracle.params_forward(x, Pm, 4, out_len))) / (2 * h)
     assert abs(fd - dP[2, 0, 1].real) < 1e-7
     assert abs(fd - wrong[1].real) > 1e-3
+
+
+def test_sampled_gradient_entries_equal_full_adjoint():
+    x, P, r, out_len = _case(9, L=4, M=3, N=50, out_len=57)
+    dP, dx = oracle.params_grad(x, P, 4, r)
+    rng = np.random.default_rng(1)
+    idx = [(int(rng.integers(0, P.shape[0])), int(rng.integers(0, 3)), int(rng.integers(0, 8)))
+           for _ in range(20)]
+    sidx = [int(v) for v in rng.integers(0, 50, 15)] + [0, 49]
+    sP, sx = oracle.params_grad_sampled(x, P, 4, r, idx, sidx)
+    for j, (t, m, k) in enumerate(idx):
+        assert abs(sP[j] - dP[t, m, k]) < 1e-12
+    assert np.max(np.abs(sx - dx[sidx])) < 1e-12
