@@ -385,7 +385,8 @@ def run_adjoint(args):
     one training step = forward (block spectra, Eq. 7 with per-block parameter
     spectra, inverse + overlap-add) and backward (gradient spectra, fused
     adjoint of Eq. 7, input gradient), the input spectra recomputed per segment
-    of 32 blocks. The parameter kernels stream P (2.9 GB) and dP: HBM-bound."""
+    of 32 blocks in the backward. The parameter kernels stream P (2.9 GB) and dP:
+    HBM-bound."""
     import torch
     from paper_2310_00319_gb300 import Plan
     from synth import workloads as W
@@ -401,6 +402,7 @@ def run_adjoint(args):
     K = 32
     Y = torch.empty((C, nb, P), dtype=torch.complex64, device=dev)
     dP = torch.empty_like(Pm)
+    dX = torch.empty((C, nb, P), dtype=torch.complex64, device=dev)
     dx = torch.empty_like(x)
     names = ["fwd_spectra", "mac_params", "inverse_ola", "adjoint_output", "bwd_spectra",
              "adjoint_mac", "adjoint_input"]
@@ -414,29 +416,24 @@ def run_adjoint(args):
             e.record(stream)
             marks.append((name, e))
         mark("start")
-        for t0 in range(0, nb, K):                      # forward, segments with history
-            tc = min(K, nb - t0)
-            x0 = max(0, t0 - 2 * (M - 1))
-            X = plan.block_spectra(x, x0, t0 + tc - x0)
-            mark("fwd_spectra")
-            Ys = plan.mac_params(X, x0, Pm, t0, tc)
-            mark("mac_params")
-            Y[:, t0:t0 + tc] = Ys
-            mark("copy")
+        X = plan.block_spectra(x, 0, nb)                 # forward: all blocks at once
+        mark("fwd_spectra")
+        plan.mac_params(X, 0, Pm, 0, nb, out=Y)
+        mark("mac_params")
         plan.inverse_ola(Y, N)
         mark("inverse_ola")
         G = plan.adjoint_output(r, 0, nb)
         mark("adjoint_output")
+        for q0 in range(0, nb, K):                       # backward: X recomputed per segment
+            qc = min(K, nb - q0)
+            Xs = plan.block_spectra(x, q0, qc)
+            mark("bwd_spectra")
+            plan.adjoint_mac(G, 0, Xs, q0, Pm, q0, qc, dP, dX=dX, dx_row=q0)
+            mark("adjoint_mac")
         dx.zero_()
         mark("copy")
-        for q0 in range(0, nb, K):
-            qc = min(K, nb - q0)
-            X = plan.block_spectra(x, q0, qc)
-            mark("bwd_spectra")
-            dX = plan.adjoint_mac(G, 0, X, q0, Pm, q0, qc, dP)
-            mark("adjoint_mac")
-            plan.adjoint_input(dX, q0, dx)
-            mark("adjoint_input")
+        plan.adjoint_input(dX, 0, dx)
+        mark("adjoint_input")
         ev.append(marks)
 
     for _ in range(args.warmup):

@@ -222,11 +222,12 @@ TVOLAP_API int tvolap_block_spectra(tvolap_t h, const float *x_dev, int64_t N, i
  *          must hold every row needed: x_first <= max(0, t_first - 2(M-1)) and
  *          x_first + x_count >= t_first + t_count
  *   P_dev  float2 [n_out][p_blocks][M][P]; t_first + t_count <= p_blocks
- *   Y_dev  float2 [n_out][t_count][P]
+ *   Y_dev  float2 [n_out][y_rows][P], rows 0 .. t_count - 1 written
+ *          (y_rows >= t_count: a segment can land inside a larger buffer)
  */
 TVOLAP_API int tvolap_mac_params(tvolap_t h, const float *X_dev, int64_t x_first, int x_count,
                                  const float *P_dev, int64_t p_blocks, int64_t t_first,
-                                 int t_count, float *Y_dev);
+                                 int t_count, float *Y_dev, int64_t y_rows);
 
 /*
  * Adjoint of Eq. 8 (with the overlap-add of Eqs. 9-12) for g = dL/dy:
@@ -247,13 +248,15 @@ TVOLAP_API int tvolap_adjoint_output(tvolap_t h, const float *g_dev, int64_t g_l
  *   G_dev  float2 [n_out][g_count][P], rows g_first ..; needs g_first <= q_first
  *          and g_first + g_count >= min(p_blocks, q_first + q_count + 2(M-1))
  *   X_dev  float2 [n_in][x_count][P], rows x_first ..; must cover the q range
- *   P_dev, dP_dev  float2 [n_out][p_blocks][M][P];  dX_dev float2 [n_out][q_count][P]
+ *   P_dev, dP_dev  float2 [n_out][p_blocks][M][P]
+ *   dX_dev float2 [n_out][dx_rows][P], rows 0 .. q_count - 1 written (dx_rows >=
+ *          q_count: segments can land inside one buffer)
  * Requires identity routing (n_in == n_out, output o reads input o).
  */
 TVOLAP_API int tvolap_adjoint_mac(tvolap_t h, const float *G_dev, int64_t g_first, int g_count,
                                   const float *X_dev, int64_t x_first, int x_count,
                                   const float *P_dev, int64_t p_blocks, int64_t q_first,
-                                  int q_count, float *dP_dev, float *dX_dev);
+                                  int q_count, float *dP_dev, float *dX_dev, int64_t dx_rows);
 
 /*
  * Adjoint of Eqs. 1, 3, 5: for each block q of the range,

@@ -46,11 +46,12 @@ SIGNATURES = {
     "tvolap_block_spectra": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int,
                                      c_void_p]),
     "tvolap_mac_params": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int64,
-                                  c_int, c_void_p]),
+                                  c_int, c_void_p, c_int64]),
     "tvolap_adjoint_output": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int,
                                       c_void_p]),
     "tvolap_adjoint_mac": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int,
-                                   c_void_p, c_int64, c_int64, c_int, c_void_p, c_void_p]),
+                                   c_void_p, c_int64, c_int64, c_int, c_void_p, c_void_p,
+                                   c_int64]),
     "tvolap_adjoint_input": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_void_p, c_int64,
                                      c_int64]),
     "tvolap_process_signal_static": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p,

@@ -7,11 +7,12 @@ C ABI; this module only orders the calls and holds the tensors.
     y = spectral_tvolap(x, P, plan)          # x [C, N], P [C, n_blocks, M, 2L] complex64
     loss = ((y - target) ** 2).mean(); loss.backward()
 
-With ``segment=K`` the input spectra X are never held for all blocks at once:
-the forward computes them per segment of K output blocks plus the 2(M-1)-block
-history the segment reads, and the backward recomputes them per segment of K
-blocks (the adjoint of Eq. 7 at block q reads only X(q)). Results are the same
-as without segments.
+The input spectra X are not kept from the forward to the backward: the
+backward recomputes them, by default all at once, or with ``segment=K`` per
+segment of K blocks, so that at most K blocks of X are held (the adjoint of
+Eq. 7 at block q reads only X(q)). With ``fwd_segment=K`` the forward too
+holds X for at most K blocks plus the 2(M-1)-block history a segment reads.
+Results are the same with and without segments.
 """
 from __future__ import annotations
 
@@ -22,7 +23,8 @@ from .tvolap import Plan, n_blocks_for
 
 class SpectralTvolap(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x, Pspec, plan: Plan, out_len: int, segment: int | None):
+    def forward(ctx, x, Pspec, plan: Plan, out_len: int, segment: int | None,
+                fwd_segment: int | None):
         C, N = x.shape
         nb = n_blocks_for(out_len, plan.L)
         if Pspec.shape != (plan.n_out, nb, plan.M, plan.P):
@@ -30,16 +32,18 @@ class SpectralTvolap(torch.autograd.Function):
         x = x.contiguous()
         Pspec = Pspec.contiguous()
         K = nb if not segment else int(segment)
-        if K >= nb:
+        Kf = nb if not fwd_segment else int(fwd_segment)
+        if Kf >= nb:
             X = plan.block_spectra(x, 0, nb)
             Y = plan.mac_params(X, 0, Pspec, 0, nb)
         else:
             Y = torch.empty((plan.n_out, nb, plan.P), dtype=torch.complex64, device=x.device)
-            for t0 in range(0, nb, K):
-                tc = min(K, nb - t0)
+            for t0 in range(0, nb, Kf):
+                tc = min(Kf, nb - t0)
                 x0 = max(0, t0 - 2 * (plan.M - 1))
                 X = plan.block_spectra(x, x0, t0 + tc - x0)
-                Y[:, t0:t0 + tc] = plan.mac_params(X, x0, Pspec, t0, tc)
+                plan.mac_params(X, x0, Pspec, t0, tc, out=Y, out_row=t0)
+        del X
         y = plan.inverse_ola(Y, out_len)
         ctx.save_for_backward(x, Pspec)
         ctx.plan, ctx.nb, ctx.K = plan, nb, K
@@ -51,16 +55,20 @@ class SpectralTvolap(torch.autograd.Function):
         plan, nb, K = ctx.plan, ctx.nb, ctx.K
         G = plan.adjoint_output(gy.contiguous(), 0, nb)
         dP = torch.empty_like(Pspec)
-        dx = torch.zeros_like(x) if ctx.needs_input_grad[0] else None
+        dX = torch.empty((plan.n_out, nb, plan.P), dtype=torch.complex64, device=x.device)
         for q0 in range(0, nb, K):
             qc = min(K, nb - q0)
             X = plan.block_spectra(x, q0, qc)
-            dX = plan.adjoint_mac(G, 0, X, q0, Pspec, q0, qc, dP)
-            if dx is not None:
-                plan.adjoint_input(dX, q0, dx)
-        return dx, dP, None, None, None
+            plan.adjoint_mac(G, 0, X, q0, Pspec, q0, qc, dP, dX=dX, dx_row=q0)
+        dx = None
+        if ctx.needs_input_grad[0]:
+            dx = torch.zeros_like(x)
+            plan.adjoint_input(dX, 0, dx)
+        return dx, dP, None, None, None, None
 
 
-def spectral_tvolap(x, Pspec, plan: Plan, out_len: int | None = None, segment: int | None = None):
+def spectral_tvolap(x, Pspec, plan: Plan, out_len: int | None = None, segment: int | None = None,
+                    fwd_segment: int | None = None):
     """y [C, out_len] from x [C, N] and per-block spectra Pspec [C, n_blocks, M, 2L]."""
-    return SpectralTvolap.apply(x, Pspec, plan, x.shape[1] if out_len is None else out_len, segment)
+    return SpectralTvolap.apply(x, Pspec, plan, x.shape[1] if out_len is None else out_len,
+                                segment, fwd_segment)

@@ -400,18 +400,19 @@ int tvolap_block_spectra(tvolap_t h, const float *x_dev, int64_t N, int64_t x_st
 
 int tvolap_mac_params(tvolap_t h, const float *X_dev, int64_t x_first, int x_count,
                       const float *P_dev, int64_t p_blocks, int64_t t_first, int t_count,
-                      float *Y_dev)
+                      float *Y_dev, int64_t y_rows)
 {
     if (!h) return TVOLAP_ERR_STATE;
     if (t_count < 0 || t_first < 0 || x_first < 0 || x_count < 0) return TVOLAP_ERR_ARG;
     if (t_count == 0) return TVOLAP_OK;
     if (!X_dev || !P_dev || !Y_dev || !a16(X_dev) || !a16(P_dev) || !a16(Y_dev)) return TVOLAP_ERR_ARG;
     const int64_t need_lo = t_first - 2 * (int64_t)(h->M - 1) > 0 ? t_first - 2 * (int64_t)(h->M - 1) : 0;
-    if (t_first + t_count > p_blocks || x_first > need_lo || x_first + x_count < t_first + t_count)
+    if (t_first + t_count > p_blocks || x_first > need_lo || x_first + x_count < t_first + t_count ||
+        y_rows < t_count)
         return TVOLAP_ERR_ARG;
     return cuda_status(launch_mac_params(h, reinterpret_cast<const float2 *>(X_dev), x_first, x_count,
                                          reinterpret_cast<const float2 *>(P_dev), p_blocks, t_first,
-                                         t_count, reinterpret_cast<float2 *>(Y_dev)));
+                                         t_count, reinterpret_cast<float2 *>(Y_dev), y_rows));
 }
 
 int tvolap_adjoint_output(tvolap_t h, const float *g_dev, int64_t g_len, int64_t g_stride,
@@ -427,7 +428,8 @@ int tvolap_adjoint_output(tvolap_t h, const float *g_dev, int64_t g_len, int64_t
 
 int tvolap_adjoint_mac(tvolap_t h, const float *G_dev, int64_t g_first, int g_count,
                        const float *X_dev, int64_t x_first, int x_count, const float *P_dev,
-                       int64_t p_blocks, int64_t q_first, int q_count, float *dP_dev, float *dX_dev)
+                       int64_t p_blocks, int64_t q_first, int q_count, float *dP_dev, float *dX_dev,
+                       int64_t dx_rows)
 {
     if (!h) return TVOLAP_ERR_STATE;
     if (!h->identity_routing) return TVOLAP_ERR_ARG;
@@ -440,13 +442,13 @@ int tvolap_adjoint_mac(tvolap_t h, const float *G_dev, int64_t g_first, int g_co
     int64_t g_need = q_first + q_count + 2 * (int64_t)(h->M - 1);
     if (g_need > p_blocks) g_need = p_blocks;
     if (q_first + q_count > p_blocks || x_first > q_first || x_first + x_count < q_first + q_count ||
-        g_first > q_first || g_first + g_count < g_need)
+        g_first > q_first || g_first + g_count < g_need || dx_rows < q_count)
         return TVOLAP_ERR_ARG;
     return cuda_status(launch_adjoint_mac(
         h, reinterpret_cast<const float2 *>(G_dev), g_first, g_count,
         reinterpret_cast<const float2 *>(X_dev), x_first, x_count,
         reinterpret_cast<const float2 *>(P_dev), p_blocks, q_first, q_count,
-        reinterpret_cast<float2 *>(dP_dev), reinterpret_cast<float2 *>(dX_dev)));
+        reinterpret_cast<float2 *>(dP_dev), reinterpret_cast<float2 *>(dX_dev), dx_rows));
 }
 
 int tvolap_adjoint_input(tvolap_t h, const float *dX_dev, int64_t q_first, int q_count,

@@ -74,11 +74,11 @@ cudaError_t ensure_overflow(tvolap_plan *h, int64_t entries);
 // kernels_adjoint.cu
 cudaError_t launch_mac_params(tvolap_plan *h, const float2 *X, int64_t x_first, int x_count,
                               const float2 *Pm, int64_t p_blocks, int64_t t_first, int t_count,
-                              float2 *Y);
+                              float2 *Y, int64_t y_rows);
 cudaError_t launch_adjoint_mac(tvolap_plan *h, const float2 *G, int64_t g_first, int g_count,
                                const float2 *X, int64_t x_first, int x_count, const float2 *Pm,
                                int64_t p_blocks, int64_t q_first, int q_count, float2 *dP,
-                               float2 *dX);
+                               float2 *dX, int64_t dx_rows);
 
 // kernels_mac.cu
 cudaError_t launch_mac_signal_lsu(tvolap_plan *h, const float2 *X, int n_blocks,

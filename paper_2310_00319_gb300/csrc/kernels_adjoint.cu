@@ -13,8 +13,8 @@
 //                  range starts at 0, extra threads for q = -(2M-2) .. -1 write
 //                  the zero gradients of the P entries that only ever multiply
 //                  blocks before the signal.
-// A thread owns two bins (16-byte loads and stores); a CTA of 128 threads
-// covers 256 bins and loops over wider spectra.
+// A thread owns two bins (16-byte loads and stores) of one block; the partition
+// loop is unrolled 8 deep to keep enough loads in flight.
 #include "fft_core.cuh"
 #include "internal.h"
 
@@ -53,99 +53,104 @@ __device__ __forceinline__ float4 mulc4(float4 a, float4 b)               // a *
     return r;
 }
 
-constexpr int AT = 128;   // threads per CTA
+constexpr int AT = 128;   // threads per CTA (one bin pair each)
 
-// grid: x = t_count, y = outputs
+// grid: x = t_count, y = outputs, z = groups of AT bin pairs
 __global__ void __launch_bounds__(AT)
 k_mac_params(const float4 *__restrict__ X, int64_t x_first, int x_count, const float4 *__restrict__ Pm,
              int64_t p_blocks, int M, int P4, int64_t t_first, int t_count,
-             const int32_t *__restrict__ out_to_in, float4 *__restrict__ Y)
+             const int32_t *__restrict__ out_to_in, float4 *__restrict__ Y, int64_t y_rows)
 {
+    const int k = blockIdx.z * AT + threadIdx.x;
+    if (k >= P4) return;
     const int o = blockIdx.y;
     const int64_t i = blockIdx.x;
     const int64_t t = t_first + i;
     const int c = out_to_in[o];
-    const float4 *Pt = Pm + ((int64_t)o * p_blocks + t) * M * P4;
-    const float4 *Xc = X + (int64_t)c * x_count * P4;
+    const float4 *Pt = Pm + ((int64_t)o * p_blocks + t) * M * P4 + k;
+    const float4 *Xt = X + ((int64_t)c * x_count + (t - x_first)) * P4 + k;   // row of X(t)
     int m_end = (int)(t / 2) + 1;                       // t - 2m >= 0
     if (m_end > M) m_end = M;
-    for (int k = threadIdx.x; k < P4; k += AT) {
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-        for (int m = 0; m < m_end; ++m) {
-            const int64_t xr = t - 2 * m - x_first;     // row of X(t - 2m) in the buffer
-            cmac4(acc, __ldg(Pt + (int64_t)m * P4 + k), __ldg(Xc + xr * P4 + k));
-        }
-        Y[((int64_t)o * t_count + i) * P4 + k] = acc;
-    }
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
+    for (int m = 0; m < m_end; ++m)
+        cmac4(acc, __ldg(Pt + (int64_t)m * P4), __ldg(Xt - (int64_t)(2 * m) * P4));
+    Y[((int64_t)o * y_rows + i) * P4 + k] = acc;
 }
 
-// grid: x = q_count + extra (the virtual blocks q < 0 when q_first == 0), y = outputs
+// grid: x = q_count + extra (the virtual blocks q < 0 when q_first == 0),
+// y = outputs, z = groups of AT bin pairs
 __global__ void __launch_bounds__(AT)
 k_adjoint_mac(const float4 *__restrict__ G, int64_t g_first, int g_count,
               const float4 *__restrict__ X, int64_t x_first, int x_count,
               const float4 *__restrict__ Pm, int64_t p_blocks, int M, int P4, int64_t q_first,
-              int q_count, int extra, const int32_t *__restrict__ out_to_in,
-              float4 *__restrict__ dP, float4 *__restrict__ dX)
+              int q_count, const int32_t *__restrict__ out_to_in, float4 *__restrict__ dP,
+              float4 *__restrict__ dX, int64_t dx_rows)
 {
+    const int k = blockIdx.z * AT + threadIdx.x;
+    if (k >= P4) return;
     const int o = blockIdx.y;
     const int64_t q = (int64_t)blockIdx.x < q_count ? q_first + blockIdx.x
                                                     : -(int64_t)(blockIdx.x - q_count) - 1;
-    const int c = out_to_in[o];
-    const float4 *Go = G + (int64_t)o * g_count * P4;
-    const float4 *Po = Pm + (int64_t)o * p_blocks * M * P4;
-    float4 *dPo = dP + (int64_t)o * p_blocks * M * P4;
+    const int64_t MP4 = (int64_t)M * P4;
+    float4 *dPo = dP + (int64_t)o * p_blocks * MP4 + k;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int k = threadIdx.x; k < P4; k += AT) {
-        if (q < 0) {
-            // P(t, m) with t = q + 2m < 2m multiplies only blocks before the signal
-            for (int m = 0; m < M; ++m) {
-                const int64_t t = q + 2 * m;
-                if (t >= 0 && t < p_blocks) dPo[(t * M + m) * P4 + k] = zero;
-            }
-            continue;
-        }
-        const float4 xq = __ldg(X + ((int64_t)c * x_count + (q - x_first)) * P4 + k);
-        float4 acc = zero;
-#pragma unroll 4
+    if (q < 0) {
+        // P(t, m) with t = q + 2m < 2m multiplies only blocks before the signal
         for (int m = 0; m < M; ++m) {
             const int64_t t = q + 2 * m;
-            if (t >= p_blocks) break;
-            const float4 g = __ldg(Go + (t - g_first) * P4 + k);
-            cmacc4(acc, g, __ldg(Po + (t * M + m) * P4 + k));
-            dPo[(t * M + m) * P4 + k] = mulc4(g, xq);
+            if (t >= 0 && t < p_blocks) dPo[t * MP4 + (int64_t)m * P4] = zero;
         }
-        dX[((int64_t)o * q_count + (q - q_first)) * P4 + k] = acc;
+        return;
     }
+    const int c = out_to_in[o];
+    const float4 xq = __ldg(X + ((int64_t)c * x_count + (q - x_first)) * P4 + k);
+    const float4 *Gq = G + ((int64_t)o * g_count + (q - g_first)) * P4 + k;   // row of G(q)
+    const float4 *Pq = Pm + (int64_t)o * p_blocks * MP4 + q * MP4 + k;        // P(q, 0)
+    float4 *dPq = dPo + q * MP4;
+    int m_end = M;
+    if (q + 2 * (int64_t)(M - 1) >= p_blocks) m_end = (int)((p_blocks - 1 - q) / 2) + 1;
+    float4 acc = zero;
+    // row t = q + 2m of P(t, m) sits at (2m) * M * P4 + m * P4 from P(q, 0)
+#pragma unroll 8
+    for (int m = 0; m < m_end; ++m) {
+        const int64_t off = (int64_t)(2 * m) * MP4 + (int64_t)m * P4;
+        const float4 g = __ldg(Gq + (int64_t)(2 * m) * P4);
+        cmacc4(acc, g, __ldg(Pq + off));
+        dPq[off] = mulc4(g, xq);
+    }
+    dX[((int64_t)o * dx_rows + (q - q_first)) * P4 + k] = acc;
 }
 
 }  // namespace
 
 cudaError_t launch_mac_params(tvolap_plan *h, const float2 *X, int64_t x_first, int x_count,
                               const float2 *Pm, int64_t p_blocks, int64_t t_first, int t_count,
-                              float2 *Y)
+                              float2 *Y, int64_t y_rows)
 {
     if (t_count <= 0) return cudaSuccess;
-    dim3 grid((unsigned)t_count, (unsigned)h->n_out);
+    const int P4 = h->P / 2;
+    dim3 grid((unsigned)t_count, (unsigned)h->n_out, (unsigned)((P4 + AT - 1) / AT));
     k_mac_params<<<grid, AT, 0, h->stream>>>(reinterpret_cast<const float4 *>(X), x_first, x_count,
                                              reinterpret_cast<const float4 *>(Pm), p_blocks, h->M,
-                                             h->P / 2, t_first, t_count, h->out_to_in,
-                                             reinterpret_cast<float4 *>(Y));
+                                             P4, t_first, t_count, h->out_to_in,
+                                             reinterpret_cast<float4 *>(Y), y_rows);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_mac(tvolap_plan *h, const float2 *G, int64_t g_first, int g_count,
                                const float2 *X, int64_t x_first, int x_count, const float2 *Pm,
                                int64_t p_blocks, int64_t q_first, int q_count, float2 *dP,
-                               float2 *dX)
+                               float2 *dX, int64_t dx_rows)
 {
     if (q_count <= 0) return cudaSuccess;
     const int extra = (q_first == 0) ? 2 * (h->M - 1) : 0;
-    dim3 grid((unsigned)(q_count + extra), (unsigned)h->n_out);
+    const int P4 = h->P / 2;
+    dim3 grid((unsigned)(q_count + extra), (unsigned)h->n_out, (unsigned)((P4 + AT - 1) / AT));
     k_adjoint_mac<<<grid, AT, 0, h->stream>>>(
         reinterpret_cast<const float4 *>(G), g_first, g_count, reinterpret_cast<const float4 *>(X),
-        x_first, x_count, reinterpret_cast<const float4 *>(Pm), p_blocks, h->M, h->P / 2, q_first,
-        q_count, extra, h->out_to_in, reinterpret_cast<float4 *>(dP), reinterpret_cast<float4 *>(dX));
+        x_first, x_count, reinterpret_cast<const float4 *>(Pm), p_blocks, h->M, P4, q_first, q_count,
+        h->out_to_in, reinterpret_cast<float4 *>(dP), reinterpret_cast<float4 *>(dX), dx_rows);
     return cudaGetLastError();
 }
 

@@ -240,7 +240,9 @@ k_adjoint_input(const float2 *__restrict__ dX, int q_count, int64_t q_first, int
     const int f = threadIdx.x / T, j = threadIdx.x % T;
     float2 *A = sm + f * P, *B = sm + (F + f) * P;
     const int c = blockIdx.y;
-    const int64_t tile0 = (int64_t)blockIdx.x * seg;
+    // blocks q of the range reach samples [(q_first - 1)L, (q_first + q_count)L)
+    const int64_t tile_base = q_first > 0 ? (q_first - 1) / seg : 0;
+    const int64_t tile0 = (tile_base + blockIdx.x) * seg;
     const int64_t s0 = tile0 * L;
     const int nseg = seg * L;
     float *xo = dx + (int64_t)c * x_stride;
@@ -488,7 +490,13 @@ cudaError_t launch_adjoint_input(tvolap_plan *h, const float2 *dX, int64_t q_fir
 {
     if (N <= 0 || q_count <= 0) return cudaSuccess;
     const int seg = inverse_seg(h->L);
-    const int64_t n_seg = (N + (int64_t)seg * h->L - 1) / ((int64_t)seg * h->L);
+    // output hops (of L samples) the blocks of the range reach, in units of seg
+    const int64_t hop_lo = q_first > 0 ? q_first - 1 : 0;
+    int64_t hop_hi = q_first + q_count;                   // exclusive
+    const int64_t n_hops = (N + h->L - 1) / h->L;
+    if (hop_hi > n_hops) hop_hi = n_hops;
+    if (hop_hi <= hop_lo) return cudaSuccess;
+    const int64_t n_seg = (hop_hi - 1) / seg - hop_lo / seg + 1;
     TVOLAP_DISPATCH(h->lgP, {
         constexpr int P = 1 << LG;
         const size_t sm = smem_fft<LG>() + (size_t)seg * h->L * sizeof(float);

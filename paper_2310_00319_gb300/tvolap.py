@@ -218,16 +218,21 @@ class Plan:
         return X
 
     def mac_params(self, X: torch.Tensor, x_first: int, Pspec: torch.Tensor, t_first: int,
-                   t_count: int, out: torch.Tensor | None = None) -> torch.Tensor:
-        """Y [n_out, t_count, P] = Eq. 7 with per-block parameter spectra
-        Pspec [n_out, p_blocks, M, P] for blocks t_first .. t_first + t_count - 1."""
+                   t_count: int, out: torch.Tensor | None = None, out_row: int = 0) -> torch.Tensor:
+        """Eq. 7 with per-block parameter spectra Pspec [n_out, p_blocks, M, P] for
+        blocks t_first .. t_first + t_count - 1, written to rows out_row .. of
+        out [n_out, rows, P] (default: a new [n_out, t_count, P])."""
         X = _need(X, torch.complex64, self.device, "X", 3)
         Pspec = _need(Pspec, torch.complex64, self.device, "Pspec", 4)
         if out is None:
             out = torch.empty((self.n_out, t_count, self.P), dtype=torch.complex64,
                               device=self.device)
+        _need(out, torch.complex64, self.device, "out", 3)
+        if out_row < 0 or out_row + t_count > out.shape[1]:
+            raise ValueError("out rows out of range")
+        ptr = ctypes.c_void_p(out.data_ptr() + out_row * self.P * 8)
         self._call("tvolap_mac_params", _ptr(X), int(x_first), X.shape[1], _ptr(Pspec),
-                   Pspec.shape[1], int(t_first), int(t_count), _ptr(out))
+                   Pspec.shape[1], int(t_first), int(t_count), ptr, out.shape[1])
         return out
 
     def adjoint_output(self, g: torch.Tensor, t_first: int, t_count: int) -> torch.Tensor:
@@ -238,14 +243,20 @@ class Plan:
                    int(t_count), _ptr(G))
         return G
 
-    def adjoint_mac(self, G, g_first, X, x_first, Pspec, q_first, q_count, dP, dX=None):
-        """dP (written in place for t - 2m in the q range) and dX [n_out, q_count, P]."""
+    def adjoint_mac(self, G, g_first, X, x_first, Pspec, q_first, q_count, dP, dX=None,
+                    dx_row=0):
+        """dP (written in place for t - 2m in the q range) and the input-block
+        gradients, written to rows dx_row .. of dX [n_out, rows, P] (default: a
+        new [n_out, q_count, P])."""
         if dX is None:
             dX = torch.empty((self.n_out, q_count, self.P), dtype=torch.complex64,
                              device=self.device)
+        if dx_row < 0 or dx_row + q_count > dX.shape[1]:
+            raise ValueError("dX rows out of range")
+        ptr = ctypes.c_void_p(dX.data_ptr() + dx_row * self.P * 8)
         self._call("tvolap_adjoint_mac", _ptr(G), int(g_first), G.shape[1], _ptr(X), int(x_first),
                    X.shape[1], _ptr(Pspec), Pspec.shape[1], int(q_first), int(q_count), _ptr(dP),
-                   _ptr(dX))
+                   ptr, dX.shape[1])
         return dX
 
     def adjoint_input(self, dX: torch.Tensor, q_first: int, dx: torch.Tensor):

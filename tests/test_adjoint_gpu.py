@@ -49,7 +49,7 @@ def test_params_forward_matches_oracle(segment):
     x = torch.from_numpy(d["x"]).to(dev)
     P = torch.from_numpy(d["P"]).to(dev)
     with torch.no_grad():
-        y = spectral_tvolap(x, P, plan, segment=segment).cpu().numpy()
+        y = spectral_tvolap(x, P, plan, fwd_segment=segment).cpu().numpy()
     for c in range(d["x"].shape[0]):
         ref = oracle.params_forward(d["x"][c], d["P"][c], d["L"])
         rel, mx = _rel(y[c], ref)
@@ -86,7 +86,7 @@ def test_segments_give_identical_results():
     for seg in (None, 4, 13):
         x = torch.from_numpy(d["x"]).to(dev).requires_grad_(True)
         P = torch.from_numpy(d["P"]).to(dev).requires_grad_(True)
-        y = spectral_tvolap(x, P, plan, segment=seg)
+        y = spectral_tvolap(x, P, plan, segment=seg, fwd_segment=seg)
         (y * torch.from_numpy(d["r"]).to(dev)).sum().backward()
         outs.append((y.detach().cpu().numpy(), x.grad.cpu().numpy(), P.grad.cpu().numpy()))
     for o in outs[1:]:
