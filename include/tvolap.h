@@ -171,6 +171,27 @@ TVOLAP_API int tvolap_process_signal(tvolap_t h, const float *x_dev, int64_t N, 
                           const float *sched_alpha, int64_t sched_stride, float *y_dev,
                           int64_t out_len, int64_t y_stride);
 
+/*
+ * tvolap_process_signal for a batch whose channels differ in length and in
+ * the number of partitions they use (many independent sources of one hop L in
+ * one call; Section 2: c channels side by side). Channel c is input c and
+ * output c (the plan must have identity routing). Per channel, device arrays:
+ *   n_dev        int64 [n_in]   input samples of channel c (<= x_stride)
+ *   out_len_dev  int64 [n_out]  output samples to write (<= max_out_len)
+ *   parts_dev    int32 [n_out]  partitions its filters use (1 .. M): its
+ *                impulse responses have at most 2 * L * parts taps
+ * Grids cover max_out_len; each channel does only its own blocks and
+ * partitions. Values are clamped on the device to the bounds above. Schedules
+ * as in tvolap_process_signal (sched_stride >= blocks of max_out_len); samples
+ * of y_dev past a channel's out_len are not written.
+ */
+TVOLAP_API int tvolap_process_ragged(tvolap_t h, const float *x_dev, int64_t x_stride,
+                                     const int64_t *n_dev, const int64_t *out_len_dev,
+                                     const int32_t *parts_dev, int64_t max_out_len,
+                                     const int32_t *sched_a, const int32_t *sched_b,
+                                     const float *sched_alpha, int64_t sched_stride, float *y_dev,
+                                     int64_t y_stride);
+
 /* Bytes of workspace tvolap_process_signal needs for out_len samples. */
 TVOLAP_API int64_t tvolap_signal_workspace_bytes(tvolap_t h, int64_t out_len);
 

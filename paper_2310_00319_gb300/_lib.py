@@ -36,6 +36,9 @@ SIGNATURES = {
     "tvolap_process_signal": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p,
                                       c_void_p, c_int64, c_void_p, c_int64, c_int64]),
     "tvolap_signal_workspace_bytes": (c_int64, [c_void_p, c_int64]),
+    "tvolap_process_ragged": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p,
+                                      c_int64, c_void_p, c_void_p, c_void_p, c_int64, c_void_p,
+                                      c_int64]),
     "tvolap_forward_spectra": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int, c_void_p]),
     "tvolap_mac": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int64,
                            c_void_p]),

@@ -325,6 +325,30 @@ int tvolap_process_signal(tvolap_t h, const float *x_dev, int64_t N, int64_t x_s
     return cuda_status(e);
 }
 
+int tvolap_process_ragged(tvolap_t h, const float *x_dev, int64_t x_stride, const int64_t *n_dev,
+                          const int64_t *out_len_dev, const int32_t *parts_dev, int64_t max_out_len,
+                          const int32_t *sched_a, const int32_t *sched_b, const float *sched_alpha,
+                          int64_t sched_stride, float *y_dev, int64_t y_stride)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (!h->identity_routing) return TVOLAP_ERR_ARG;
+    if (max_out_len < 0 || x_stride < 0 || y_stride < max_out_len) return TVOLAP_ERR_ARG;
+    if (max_out_len == 0) return TVOLAP_OK;
+    if (!x_dev || !y_dev || !sched_a || !n_dev || !out_len_dev || !parts_dev) return TVOLAP_ERR_ARG;
+    const int64_t nb = blocks_for(h, max_out_len);
+    if (nb > (int64_t)0x7fffffff / 2 || sched_stride < nb) return TVOLAP_ERR_ARG;
+    int st = ensure_workspace(h, (size_t)workspace_bytes(h, nb));
+    if (st != TVOLAP_OK) return st;
+    float2 *X = reinterpret_cast<float2 *>(h->ws);
+    float2 *Y = X + (int64_t)h->n_in * nb * h->P;
+    const Ragged rg{n_dev, out_len_dev, parts_dev};
+    cudaError_t e = launch_block_spectra(h, x_dev, x_stride, x_stride, 0, (int)nb, X, rg);
+    if (e == cudaSuccess)
+        e = launch_mac_signal(h, X, (int)nb, sched_a, sched_b, sched_alpha, sched_stride, Y, rg);
+    if (e == cudaSuccess) e = launch_inverse_ola(h, Y, (int)nb, y_dev, max_out_len, y_stride, rg);
+    return cuda_status(e);
+}
+
 int tvolap_forward_spectra(tvolap_t h, const float *x_dev, int64_t N, int64_t x_stride,
                            int n_blocks, float *X_dev)
 {

@@ -47,12 +47,27 @@ struct tvolap_plan {
 
 namespace tvolap {
 
+// Per-channel sizes of a ragged batch: device arrays, all null for a uniform
+// batch. Channel c is input c and output c (identity routing). Kernels clamp
+// every value to the plan and the launch (0 <= n <= x_stride, 0 <= out_len <=
+// the launch's output length, 1 <= parts <= M).
+struct Ragged {
+    const int64_t *n;          // [n_in]  input samples
+    const int64_t *out_len;    // [n_out] output samples
+    const int32_t *parts;      // [n_out] partitions used
+};
+
+__host__ __device__ inline int64_t blocks_of(int64_t out_len, int L)
+{
+    return out_len <= 0 ? 0 : (out_len - 1) / L + 2;
+}
+
 // kernels_fft.cu
 cudaError_t launch_tables(tvolap_plan *h);
 cudaError_t launch_forward_signal(tvolap_plan *h, const float *x, int64_t N, int64_t x_stride,
                                   int n_blocks, float2 *X);
 cudaError_t launch_block_spectra(tvolap_plan *h, const float *x, int64_t N, int64_t x_stride,
-                                 int64_t t_first, int n_blocks, float2 *X);
+                                 int64_t t_first, int n_blocks, float2 *X, Ragged rg = Ragged{});
 cudaError_t launch_adjoint_output(tvolap_plan *h, const float *g, int64_t g_len, int64_t g_stride,
                                   int64_t t_first, int n_blocks, float2 *G);
 cudaError_t launch_adjoint_input(tvolap_plan *h, const float2 *dX, int64_t q_first, int q_count,
@@ -60,14 +75,14 @@ cudaError_t launch_adjoint_input(tvolap_plan *h, const float2 *dX, int64_t q_fir
 cudaError_t launch_bank(tvolap_plan *h, int first_slot, int count, const float *ir, int ir_len,
                         int64_t ir_stride);
 cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, float *y,
-                               int64_t out_len, int64_t y_stride);
+                               int64_t out_len, int64_t y_stride, Ragged rg = Ragged{});
 cudaError_t launch_forward_stream(tvolap_plan *h, const float *in);
 cudaError_t launch_inverse_stream(tvolap_plan *h, float *out);
 
 // kernels_mac_tma.cu (falls back to the cp.async kernel of kernels_mac.cu)
 cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, const int32_t *sa,
                               const int32_t *sb, const float *sal, int64_t sched_stride,
-                              float2 *Y);
+                              float2 *Y, Ragged rg = Ragged{});
 // api.cu: grow the overflow list of the offline multiply-accumulate
 cudaError_t ensure_overflow(tvolap_plan *h, int64_t entries);
 
@@ -83,7 +98,7 @@ cudaError_t launch_adjoint_mac(tvolap_plan *h, const float2 *G, int64_t g_first,
 // kernels_mac.cu
 cudaError_t launch_mac_signal_lsu(tvolap_plan *h, const float2 *X, int n_blocks,
                                   const int32_t *sa, const int32_t *sb, const float *sal,
-                                  int64_t sched_stride, float2 *Y);
+                                  int64_t sched_stride, float2 *Y, Ragged rg = Ragged{});
 cudaError_t launch_mac_stream(tvolap_plan *h, const int32_t *sa, const int32_t *sb,
                               const float *sal);
 cudaError_t launch_select(tvolap_plan *h, int out_ch, int a, int b, float alpha);

@@ -68,16 +68,22 @@ __global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
 k_forward_signal(const float *__restrict__ x, int64_t N, int64_t x_stride, int L, int n_blocks,
                  int64_t total, const float *__restrict__ win, const float2 *__restrict__ rot,
                  const float2 *__restrict__ post, const float2 *__restrict__ tw,
-                 float2 *__restrict__ X, int64_t t_first)
+                 float2 *__restrict__ X, int64_t t_first, Ragged rg)
 {
     constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F;
     extern __shared__ float2 sm[];
     const int f = threadIdx.x / T, j = threadIdx.x % T;
     float2 *A = sm + f * P, *B = sm + (F + f) * P;
     const int64_t g = (int64_t)blockIdx.x * F + f;     // transform = (channel, block)
-    const bool active = g < total;
+    bool active = g < total;
     const int64_t c = active ? g / n_blocks : 0;
     const int64_t t = active ? g % n_blocks : 0;
+    if (rg.n) {                                        // ragged: this channel's length and blocks
+        int64_t nc = rg.n[c];
+        N = nc < 0 ? 0 : (nc < N ? nc : N);
+        int64_t oc = rg.out_len[c];
+        active = active && (t_first + t < blocks_of(oc, L));
+    }
     const int64_t start = (t_first + t - 1) * (int64_t)L;   // block l = t - 1 starts at l*L
     const float *xc = x + c * x_stride;
     auto src = [&](int n) {
@@ -162,7 +168,7 @@ template <int LG>
 __global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
 k_inverse_ola(const float2 *__restrict__ Y, int n_blocks, int L, int seg, float *__restrict__ y,
               int64_t out_len, int64_t y_stride, const float2 *__restrict__ rot,
-              const float2 *__restrict__ post, const float2 *__restrict__ tw)
+              const float2 *__restrict__ post, const float2 *__restrict__ tw, Ragged rg)
 {
     constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F;
     extern __shared__ float2 sm[];
@@ -173,11 +179,18 @@ k_inverse_ola(const float2 *__restrict__ Y, int n_blocks, int L, int seg, float 
     const int64_t tile0 = (int64_t)blockIdx.x * seg;    // first output hop of the segment
     const int64_t s0 = tile0 * L;
     const int nseg = seg * L;
-    for (int i = threadIdx.x; i < nseg; i += blockDim.x) acc[i] = 0.f;
     const float2 *Yo = Y + (int64_t)o * n_blocks * P;
+    int64_t nb_o = n_blocks;
+    if (rg.out_len) {                                  // ragged: this output's length
+        const int64_t oc = rg.out_len[o];
+        if (oc < out_len) out_len = oc < 0 ? 0 : oc;
+        if (s0 >= out_len) return;                     // whole CTA, before any barrier
+        nb_o = blocks_of(out_len, L);
+    }
+    for (int i = threadIdx.x; i < nseg; i += blockDim.x) acc[i] = 0.f;
     const int64_t t_lo = tile0 - 2 > 0 ? tile0 - 2 : 0;
     int64_t t_hi = tile0 + seg;
-    if (t_hi > n_blocks - 1) t_hi = n_blocks - 1;
+    if (t_hi > nb_o - 1) t_hi = nb_o - 1;
     const float inv_p = 1.0f / (float)P;
     for (int64_t tb = t_lo; tb <= t_hi; tb += F) {
         const int64_t t = tb + f;
@@ -416,7 +429,7 @@ cudaError_t launch_forward_signal(tvolap_plan *h, const float *x, int64_t N, int
 }
 
 cudaError_t launch_block_spectra(tvolap_plan *h, const float *x, int64_t N, int64_t x_stride,
-                                 int64_t t_first, int n_blocks, float2 *X)
+                                 int64_t t_first, int n_blocks, float2 *X, Ragged rg)
 {
     const int64_t total = (int64_t)h->n_in * n_blocks;
     if (total == 0) return cudaSuccess;
@@ -427,7 +440,7 @@ cudaError_t launch_block_spectra(tvolap_plan *h, const float *x, int64_t N, int6
         cudaError_t e = set_smem(k_forward_signal<LG>, sm);
         if (e != cudaSuccess) return e;
         k_forward_signal<LG><<<(unsigned)grid, Geo<P>::THREADS, sm, h->stream>>>(
-            x, N, x_stride, h->L, n_blocks, total, h->win, h->rot, h->post, h->tw, X, t_first);
+            x, N, x_stride, h->L, n_blocks, total, h->win, h->rot, h->post, h->tw, X, t_first, rg);
     });
     return cudaGetLastError();
 }
@@ -451,7 +464,7 @@ cudaError_t launch_bank(tvolap_plan *h, int first_slot, int count, const float *
 }
 
 cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, float *y,
-                               int64_t out_len, int64_t y_stride)
+                               int64_t out_len, int64_t y_stride, Ragged rg)
 {
     if (out_len <= 0) return cudaSuccess;
     const int seg = inverse_seg(h->L);
@@ -463,7 +476,7 @@ cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, fl
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)n_seg, (unsigned)h->n_out);
         k_inverse_ola<LG><<<grid, Geo<P>::THREADS, sm, h->stream>>>(
-            Y, n_blocks, h->L, seg, y, out_len, y_stride, h->rot, h->post, h->tw);
+            Y, n_blocks, h->L, seg, y, out_len, y_stride, h->rot, h->post, h->tw, rg);
     });
     return cudaGetLastError();
 }

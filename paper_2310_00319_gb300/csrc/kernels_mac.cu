@@ -52,7 +52,8 @@ struct LsuArgs {
     float2 *Yo;                // Y of this output, offset to the lane's bin
     const int32_t *ao, *bo;    // schedule rows of this output (bo may be null)
     const float *alo;          // may be null
-    int M, P, n_blocks, n_slots_total, null_slot;
+    int M, P, n_blocks, n_slots_total, null_slot;   // M: slot stride; n_blocks: this output's
+    int Mo;                    // partitions this output uses (loop bound, <= M)
     unsigned *err;
     float2 *ring;              // this thread's ring base
     int ring_stride;
@@ -124,7 +125,7 @@ __device__ __forceinline__ void lsu_process_run(const LsuArgs &g, int tf)
         }
     }
     int m_end = (tf + 2 * (R - 1)) / 2 + 1;     // partitions with t - 2m >= 0 for some block
-    if (m_end > g.M) m_end = g.M;
+    if (m_end > g.Mo) m_end = g.Mo;
     float2 acc[R];
     if (rs.ns == 1) {
         lsu_run<R, D, 1>(g, tf, m_end, rs, acc);
@@ -148,14 +149,21 @@ k_mac_signal_lsu(const float2 *__restrict__ X, int n_blocks, int M, int P,
                  const float2 *__restrict__ bank, int n_slots_total, int null_slot,
                  const int32_t *__restrict__ out_to_in, const int32_t *__restrict__ sa,
                  const int32_t *__restrict__ sb, const float *__restrict__ sal,
-                 int64_t sched_stride, float2 *__restrict__ Y, unsigned *err)
+                 int64_t sched_stride, float2 *__restrict__ Y, unsigned *err, Ragged rg)
 {
     __shared__ float2 ring_all[D * (MAX_NS + 1) * 32 * LSU_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int k = blockIdx.y * 32 + lane;
     const int o = blockIdx.z;
     const int tf = blockIdx.x * (4 * R) + (w >> 1) * (2 * R) + (w & 1);
-    if (tf >= n_blocks) return;                       // whole warp; no barriers below
+    int nb_o = n_blocks, Mo = M;
+    if (rg.out_len) {                                 // ragged: this output's blocks, partitions
+        const int64_t b = blocks_of(rg.out_len[o], P / 2);
+        nb_o = b < n_blocks ? (int)b : n_blocks;
+        const int po = rg.parts[o];
+        Mo = po < 1 ? 1 : (po < M ? po : M);
+    }
+    if (tf >= nb_o) return;                           // whole warp; no barriers below
     LsuArgs g;
     g.Xc = X + (int64_t)out_to_in[o] * n_blocks * P + k;
     g.bk = bank + k;
@@ -164,8 +172,9 @@ k_mac_signal_lsu(const float2 *__restrict__ X, int n_blocks, int M, int P,
     g.bo = sb ? sb + (int64_t)o * sched_stride : nullptr;
     g.alo = sal ? sal + (int64_t)o * sched_stride : nullptr;
     g.M = M;
+    g.Mo = Mo;
     g.P = P;
-    g.n_blocks = n_blocks;
+    g.n_blocks = nb_o;
     g.n_slots_total = n_slots_total;
     g.null_slot = null_slot;
     g.err = err;
@@ -258,7 +267,7 @@ __global__ void k_select(int32_t *cur_a, int32_t *cur_b, float *cur_al, int o, i
 
 cudaError_t launch_mac_signal_lsu(tvolap_plan *h, const float2 *X, int n_blocks,
                                   const int32_t *sa, const int32_t *sb, const float *sal,
-                                  int64_t sched_stride, float2 *Y)
+                                  int64_t sched_stride, float2 *Y, Ragged rg)
 {
     if (n_blocks <= 0) return cudaSuccess;
     constexpr int R = LSU_R;
@@ -266,7 +275,7 @@ cudaError_t launch_mac_signal_lsu(tvolap_plan *h, const float2 *X, int n_blocks,
               (unsigned)h->n_out);
     k_mac_signal_lsu<R, LSU_D><<<grid, 32 * LSU_WARPS, 0, h->stream>>>(
         X, n_blocks, h->M, h->P, h->bank, h->n_slots_total, h->null_slot, h->out_to_in, sa, sb,
-        sal, sched_stride, Y, h->err);
+        sal, sched_stride, Y, h->err, rg);
     return cudaGetLastError();
 }
 

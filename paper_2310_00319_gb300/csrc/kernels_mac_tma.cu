@@ -254,7 +254,7 @@ k_mac_overflow_tma(const __grid_constant__ CUtensorMap xmap, const __grid_consta
                    const int32_t *__restrict__ out_to_in, const int32_t *__restrict__ sa,
                    const int32_t *__restrict__ sb, const float *__restrict__ sal,
                    int64_t sched_stride, float2 *__restrict__ Y, unsigned *err,
-                   const int4 *__restrict__ list, const int *__restrict__ count)
+                   const int4 *__restrict__ list, const int *__restrict__ count, Ragged rg)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -267,9 +267,7 @@ k_mac_overflow_tma(const __grid_constant__ CUtensorMap xmap, const __grid_consta
     g.xmap = &xmap;
     g.hmap = &hmap;
     g.lane = lane;
-    g.M = M;
     g.P = P;
-    g.n_blocks = n_blocks;
     g.n_slots_total = n_slots_total;
     g.null_slot = null_slot;
     g.err = err;
@@ -286,9 +284,18 @@ k_mac_overflow_tma(const __grid_constant__ CUtensorMap xmap, const __grid_consta
         const int4 ent = list[e];                      // (output, bin tile, parity, group)
         int T0;
         group_origin(ent.z, ent.w, T0);
-        const int tf = T0 + 2 * R * w;
-        if (tf >= n_blocks) continue;
         const int o = ent.x;
+        int nb_o = n_blocks, Mo = M;
+        if (rg.out_len) {
+            const int64_t b = blocks_of(rg.out_len[o], P / 2);
+            nb_o = b < n_blocks ? (int)b : n_blocks;
+            const int po = rg.parts[o];
+            Mo = po < 1 ? 1 : (po < M ? po : M);
+        }
+        const int tf = T0 + 2 * R * w;
+        if (tf >= nb_o) continue;
+        g.n_blocks = nb_o;                             // bounds; rows keep the launch stride
+        g.M = Mo;                                      // loop bound (bank rows are addressed by the map)
         g.k0 = ent.y * 32;
         g.cin = out_to_in[o];
         g.Yo = Y + (int64_t)o * n_blocks * P + g.k0 + lane;
@@ -396,12 +403,19 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
                    const int32_t *__restrict__ out_to_in, const int32_t *__restrict__ sa,
                    const int32_t *__restrict__ sb, const float *__restrict__ sal,
                    int64_t sched_stride, float2 *__restrict__ Y, unsigned *err,
-                   int4 *__restrict__ list, int *__restrict__ count)
+                   int4 *__restrict__ list, int *__restrict__ count, Ragged rg)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int R = TMA_R, D = TMA_D;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int p = blockIdx.x & 1, grp = blockIdx.x >> 1;
+    const int64_t y_rows = n_blocks;                   // row stride of Y for every output
+    if (rg.out_len) {                                  // ragged: this output's blocks, partitions
+        const int64_t b = blocks_of(rg.out_len[blockIdx.z], P / 2);
+        if (b < n_blocks) n_blocks = (int)b;
+        const int po = rg.parts[blockIdx.z];
+        M = po < 1 ? 1 : (po < M ? po : M);
+    }
     int T0;
     group_origin(p, grp, T0);
     if (T0 >= n_blocks) return;                        // whole CTA
@@ -531,7 +545,7 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
         if (lane == 0) atomicOr(err, ERR_TIMEOUT);
         return;
     }
-    float2 *Yo = Y + (int64_t)o * n_blocks * P + k0 + lane;
+    float2 *Yo = Y + (int64_t)o * y_rows * P + k0 + lane;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int t = tf + 2 * r;
@@ -580,14 +594,14 @@ bool encode_spectra(CUtensorMap *map, const void *base, int P, int64_t dim1, int
 
 cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, const int32_t *sa,
                               const int32_t *sb, const float *sal, int64_t sched_stride,
-                              float2 *Y)
+                              float2 *Y, Ragged rg)
 {
     if (n_blocks <= 0) return cudaSuccess;
     CUtensorMap xrun, hmap;
     const bool tma = h->mac_variant != 1 &&
                      encode_spectra(&xrun, X, h->P, n_blocks, h->n_in, TMA_D, 2) &&
                      encode_spectra(&hmap, h->bank, h->P, h->M, h->n_slots_total + 1, TMA_D, 1);
-    if (!tma) return launch_mac_signal_lsu(h, X, n_blocks, sa, sb, sal, sched_stride, Y);
+    if (!tma) return launch_mac_signal_lsu(h, X, n_blocks, sa, sb, sal, sched_stride, Y, rg);
     const int tiles = h->P / 32;
     const int groups = ((n_blocks + 1) / 2 + GROUP_ROWS - 1) / GROUP_ROWS;
     const int64_t max_entries = (int64_t)2 * groups * tiles * h->n_out;
@@ -604,7 +618,7 @@ cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, con
     dim3 grid((unsigned)(2 * groups), (unsigned)tiles, (unsigned)h->n_out);
     k_mac_signal_group<<<grid, 32 * (GW + 1), gsmem, h->stream>>>(
         xrun, hmap, n_blocks, h->M, h->P, h->n_slots_total, h->null_slot, h->out_to_in, sa, sb,
-        sal, sched_stride, Y, h->err, h->ovf_list, h->ovf_count);
+        sal, sched_stride, Y, h->err, h->ovf_list, h->ovf_count, rg);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t wsmem = (size_t)TMA_WARPS * WARP_BYTES;
@@ -618,7 +632,7 @@ cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, con
     const int64_t ogrid = max_entries < 2LL * sms ? max_entries : 2LL * sms;
     k_mac_overflow_tma<<<(unsigned)ogrid, 32 * TMA_WARPS, wsmem, h->stream>>>(
         xrun, hmap, n_blocks, h->M, h->P, h->n_slots_total, h->null_slot, h->out_to_in, sa, sb, sal,
-        sched_stride, Y, h->err, h->ovf_list, h->ovf_count);
+        sched_stride, Y, h->err, h->ovf_list, h->ovf_count, rg);
     return cudaGetLastError();
 }
 

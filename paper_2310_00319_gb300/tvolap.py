@@ -183,6 +183,27 @@ class Plan:
                    stride, _ptr(out), out_len, out.shape[1])
         return out
 
+    def process_ragged(self, x: torch.Tensor, n: torch.Tensor, out_len: torch.Tensor,
+                       parts: torch.Tensor, max_out_len: int, sched_a, sched_b=None,
+                       sched_alpha=None, out: torch.Tensor | None = None):
+        """Channels of different lengths and partition counts in one call:
+        x [C, x_stride] (channel c holds n[c] samples), n/out_len int64 [C],
+        parts int32 [C]; returns y [C, max_out_len] (channel c valid up to
+        out_len[c])."""
+        x = _need(x, torch.float32, self.device, "x", 2)
+        _need(n, torch.int64, self.device, "n", 1)
+        _need(out_len, torch.int64, self.device, "out_len", 1)
+        _need(parts, torch.int32, self.device, "parts", 1)
+        nb = n_blocks_for(max_out_len, self.L)
+        sa, sb, sal, stride = self._sched(sched_a, sched_b, sched_alpha, nb)
+        if out is None:
+            out = torch.empty((self.n_out, max_out_len), dtype=torch.float32, device=self.device)
+        _need(out, torch.float32, self.device, "out", 2)
+        self._call("tvolap_process_ragged", _ptr(x), x.shape[1], _ptr(n), _ptr(out_len),
+                   _ptr(parts), int(max_out_len), _ptr(sa), _ptr(sb), _ptr(sal), stride,
+                   _ptr(out), out.shape[1])
+        return out
+
     def workspace_bytes(self, out_len: int) -> int:
         return self._call("tvolap_signal_workspace_bytes", int(out_len))
 

@@ -199,3 +199,42 @@ def differentiable(seed=4, n_ch=16, N=240000, L=256, ir_len=24000, scale=None, w
         out["target_irs"] = _f32(irs)
         out["target_sched"] = _i32(np.tile(cyclic_schedule(nb, 4, 32)[None, :], (n_ch, 1)))
     return out
+
+
+@dataclass
+class Source:
+    """One independent source of a batched workload: hop L, input x [N],
+    stored responses irs [n_ir, ir_len], per-block filter index sched [n_blocks]
+    (into irs), output length out_len."""
+    L: int
+    x: np.ndarray
+    irs: np.ndarray
+    sched: np.ndarray
+    out_len: int
+
+    @property
+    def M(self):
+        return max(1, -(-self.irs.shape[1] // (2 * self.L)))
+
+
+def batched_uneven(seed=3, n_src=512, hops=(64, 128, 256, 512), ir_min=4800, ir_max=96000,
+                   sec_min=1.0, sec_max=20.0, n_ir=4, switch_max=8, fs=FS):
+    """Batched uneven sources: hop L uniform over `hops`, impulse-response
+    length log-uniform in [ir_min, ir_max] (decaying Gaussian, T60 = length / 3
+    samples-to-seconds), signal length uniform in [sec_min, sec_max] s of white
+    noise (sigma 0.1), n_ir stored responses per source and a switch to the next
+    one every k ~ U{1..switch_max} blocks."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_src):
+        L = int(rng.choice(hops))
+        ir_len = int(round(np.exp(rng.uniform(np.log(ir_min), np.log(ir_max)))))
+        N = int(round(rng.uniform(sec_min, sec_max) * fs))
+        t60 = ir_len / (3.0 * fs)
+        irs = np.stack([decaying_ir(rng, ir_len, t60, fs) for _ in range(n_ir)])
+        x = white(rng, N)
+        nb = blocks_for(N, L)
+        k = int(rng.integers(1, switch_max + 1))
+        sched = cyclic_schedule(nb, n_ir, k)
+        out.append(Source(L, _f32(x), _f32(irs), _i32(sched), N))
+    return out
