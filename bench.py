@@ -562,6 +562,168 @@ def run_batched(args):
             "gpu_launches": launches * args.steps, "clocks": clocks}
 
 
+# --------------------------------------------------------------------------- serving
+def run_serve(args, lat_ticks=4000, thr_ticks=3000, timed_ticks=300, warm=200):
+    """Streaming server: 1000 streams present at the start, Poisson arrivals
+    at 50/s with lifetimes of 2..30 s, hop 64/128/256, binaural banks of 36
+    pairs of 12000..144000 taps, a head-orientation walk choosing the pair of
+    every block. Base tick 64 samples (1.333 ms at 48 kHz). Three measurements
+    over consecutive ticks: latency (one tick at a time: host-to-host time from
+    the tick call to its outputs in host memory, and device time), throughput
+    (ticks pipelined two deep, device time), and the multiply-accumulate
+    kernel alone (direct launches between CUDA events)."""
+    import torch
+    from paper_2310_00319_gb300._lib import TvolapError
+    from paper_2310_00319_gb300.server import OPT_TIMING, Server
+    from synth import workloads as W
+    dev = torch.device("cuda", 0)
+    fs, base, top, cap, n_pairs = 48000, 64, 256, 1024, 36
+    rng = np.random.default_rng(5)
+    # response banks: K distinct banks (lengths uniform 12000..144000), each
+    # stream takes one at random and transforms it into its own arena piece
+    K = 16
+    lens = rng.integers(12000, 144001, K)
+    banks = [torch.from_numpy(W.serving_bank(rng, int(n), n_pairs)).to(dev) for n in lens]
+    hops = np.array([64, 128, 256])
+    total_ticks = warm + lat_ticks + thr_ticks + timed_ticks
+    ev = W.serving_arrivals(seed=5, duration_s=total_ticks * base / fs, prefill=1000,
+                            base_hop=base, fs=fs)
+    n_ev = ev.shape[0]
+    L_of = hops[rng.integers(0, 3, n_ev)]
+    bank_of = rng.integers(0, K, n_ev)
+    stream = torch.cuda.Stream(dev)
+    free_b = torch.cuda.mem_get_info(dev)[0]
+    arena = int(min(0.6 * free_b, 140e9))
+    srv = Server(base, top, cap, max_out=2, arena_bytes=arena, device=dev, stream=stream)
+    live = {}                 # stream id -> event index
+    leave_at = {}
+    rejected = 0
+    nxt = 0
+
+    def arrivals(tick):
+        nonlocal nxt, rejected
+        while nxt < n_ev and ev[nxt, 0] <= tick:
+            L = int(L_of[nxt])
+            try:
+                i = srv.admit(L, banks[bank_of[nxt]])
+                live[i] = nxt
+                leave_at[i] = int(ev[nxt, 1])
+                srv.sel[i] = int(rng.integers(0, n_pairs))
+            except TvolapError as err:
+                if err.status != -5:             # only TVOLAP_ERR_CAPACITY is a refusal
+                    raise
+                rejected += 1
+            nxt += 1
+        for i in [i for i, t in leave_at.items() if t <= tick]:
+            srv.retire(i)
+            del live[i], leave_at[i]
+
+    pool = (0.1 * rng.standard_normal((4096, top))).astype(np.float32)
+    steps = np.array([-1, 0, 1], np.int32)
+
+    def stage(ids, tick):
+        srv.inp[ids] = pool[(ids * 7 + tick) % 4096]
+        srv.sel[ids] = (srv.sel[ids] + steps[rng.integers(0, 3, ids.shape[0])]) % n_pairs
+
+    tick = 0
+    arrivals(0)
+    srv.wait()
+    for _ in range(warm):
+        arrivals(tick)
+        ids = srv.due()
+        stage(ids, tick)
+        srv.tick()
+        tick += 1
+    srv.wait()
+    # latency: one tick at a time
+    h2h, gpu = [], []
+    e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+         for _ in range(lat_ticks)]
+    s0 = srv.stats()
+    with ClockSampler(0) as clk:
+        for k in range(lat_ticks):
+            arrivals(tick)
+            ids = srv.due()
+            stage(ids, tick)
+            t0 = time.perf_counter()
+            e[k][0].record(stream)
+            srv.tick()
+            e[k][1].record(stream)
+            srv.wait()
+            h2h.append(time.perf_counter() - t0)
+            tick += 1
+        torch.cuda.synchronize(dev)
+        gpu = [a.elapsed_time(b) for a, b in e]
+        s1 = srv.stats()
+        # throughput: pipelined, device time over the whole run
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_host = time.perf_counter()
+        a.record(stream)
+        for k in range(thr_ticks):
+            arrivals(tick)
+            ids = srv.due()
+            stage(ids, tick)
+            srv.tick()
+            tick += 1
+        b.record(stream)
+        srv.wait()
+        t_host = time.perf_counter() - t_host
+        s2 = srv.stats()
+    thr_ms = a.elapsed_time(b)
+    # the multiply-accumulate kernel alone: direct launches with stage events
+    srv.set_option(OPT_TIMING, 1)
+    s3 = srv.stats()
+    for k in range(timed_ticks):
+        arrivals(tick)
+        ids = srv.due()
+        stage(ids, tick)
+        srv.tick()
+        tick += 1
+    srv.wait()
+    s4 = srv.stats()
+    srv.set_option(OPT_TIMING, 0)
+    st = s4
+    srv.close()
+    stage_ms = [s4["stage_ms"][i] - s3["stage_ms"][i] for i in range(3)]
+    mac_bytes = s4["mac_bytes"] - s3["mac_bytes"]
+    mac_gbs = mac_bytes / (stage_ms[1] * 1e-3) / 1e9
+    peaks, kind = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    samples = s2["channel_samples"] - s1["channel_samples"]
+    deadline = base / fs * 1e3
+    h2h_ms = np.array(h2h) * 1e3
+    gpu = np.array(gpu)
+    return {"metric": "channel-samples/s (streaming, 1000 binaural streams)",
+            "value": round(samples / (thr_ms * 1e-3), 1), "unit": "channel-samples/s",
+            "n_gpus": 1, "steps": thr_ticks, "warmup": warm,
+            "ms_per_step": round(thr_ms / thr_ticks, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving_1000_streams", "base_tick_samples": base,
+                       "hops": [64, 128, 256], "pairs_per_stream": n_pairs,
+                       "ir_len": "uniform 12000..144000 (16 banks)", "capacity": cap,
+                       "arena_gb": round(arena / 1e9, 1),
+                       "l2": "banks and delay lines (tens of GB) far larger than L2"},
+            "latency": {"ticks": lat_ticks, "deadline_ms": round(deadline, 4),
+                        "host_to_host_ms_p50": round(float(np.percentile(h2h_ms, 50)), 4),
+                        "host_to_host_ms_p99": round(float(np.percentile(h2h_ms, 99)), 4),
+                        "gpu_ms_p50": round(float(np.percentile(gpu, 50)), 4),
+                        "gpu_ms_p99": round(float(np.percentile(gpu, 99)), 4),
+                        "missed_deadline": int((h2h_ms > deadline).sum())},
+            "streams": {"live_end": st["live"], "rejected": rejected,
+                        "admitted_total": nxt - rejected,
+                        "mean_due_per_tick": round((s2["stream_blocks"] - s1["stream_blocks"]) /
+                                                   thr_ticks, 1)},
+            "throughput_host_s": round(t_host, 3),
+            "roofline": {"bound": "hbm", "achieved": round(mac_gbs, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(mac_gbs / hbm, 4), "traffic": None,
+                         "kernel": "k_srv_mac (delay line + 2 bank spectra read, Y written)"},
+            "stages_ms_per_tick": {"forward": round(stage_ms[0] / timed_ticks, 4),
+                                   "mac": round(stage_ms[1] / timed_ticks, 4),
+                                   "inverse": round(stage_ms[2] / timed_ticks, 4)},
+            "gpu_launches": 7 * thr_ticks,
+            "peaks": kind, "clocks": clk.summary()}
+
+
 # --------------------------------------------------------------------------- oracle
 _F64 = {}
 
@@ -636,7 +798,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain_at_scale",
-                    choices=["plain_at_scale", "adjoint", "batched"])
+                    choices=["plain_at_scale", "adjoint", "batched", "serve"])
     ap.add_argument("--channels", type=int, default=64)
     ap.add_argument("--samples", type=int, default=480000)
     ap.add_argument("--traffic", type=float, default=None,
@@ -654,6 +816,8 @@ def main():
         out = run_adjoint(args)
     elif args.workload == "batched":
         out = run_batched(args)
+    elif args.workload == "serve":
+        out = run_serve(args)
     else:
         out = run_ours(args)
     if out is not None:

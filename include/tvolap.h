@@ -344,6 +344,208 @@ TVOLAP_API int tvolap_set_option(tvolap_t h, int option, int value);
  */
 TVOLAP_API int tvolap_check(tvolap_t h);
 
+/* ========================================================================
+ * Streaming server: many independent streams, each with its own hop L,
+ * partition count M, outputs (1 or 2, e.g. a binaural pair fed by one input)
+ * and a bank of stored filters, processed block by block as in
+ * tvolap_process_block (Section 2: all partitions switch at once, output
+ * delayed by L), admitted and retired while the server runs.
+ *
+ * Time advances in base ticks of base_hop samples. A stream of hop L =
+ * r * base_hop is due once every r base ticks, at ticks T with T mod r equal
+ * to its phase; the phase is picked at admission to even out the bytes read
+ * per tick. One tick processes every due stream: forward transforms into each
+ * stream's delay line, the Eq. 7 multiply-accumulate against the filter
+ * selected for that block, inverse transforms and overlap-add. A tick is one
+ * CUDA-graph replay (or the same launches issued directly).
+ *
+ * Device memory: one arena of arena_bytes, allocated at creation, holds every
+ * stream's filter bank, delay line and overlap state; admission takes a
+ * contiguous piece (first fit, 256-byte aligned) and fails with
+ * TVOLAP_ERR_CAPACITY when no free slot or no piece of the stream's footprint
+ * is left. Retiring returns the piece at once; the server orders any later
+ * writes into it after the ticks already enqueued.
+ *
+ * Input and output blocks pass through two sets of pinned host staging arrays
+ * that the kernels read and write directly (mapped host memory); tick k
+ * (k = 1, 2, ...) uses set (k - 1) mod 2, so the caller can fill one set
+ * while the previous tick runs on the other. tvolap_server_due names the set
+ * of the next tick after waiting for the tick that used it before: write, for
+ * every stream it lists, the L new samples into in[id][0..L) of that set and
+ * the filter index of the block into sel[id]; once that tick has finished
+ * (the next tvolap_server_due naming the same set, or tvolap_server_wait) the
+ * output block of output o is in out[id][o][0..L) of the set.
+ *
+ * A server is not thread-safe, except tvolap_server_post (any thread).
+ * ======================================================================== */
+typedef struct tvolap_server *tvolap_server_t;
+
+/*
+ * Create a server.
+ *   base_hop     smallest hop; a power of two in [16, 1024]
+ *   max_hop      largest hop; a power of two in [base_hop, 1024], at most
+ *                8 * base_hop (hops base_hop, 2 base_hop, ... max_hop)
+ *   capacity     maximum number of streams admitted at once, 1 .. 65536
+ *   max_out      outputs per stream, 1 or 2
+ *   arena_bytes  device memory for the streams' state and banks
+ *   stream       cudaStream_t of the ticks (NULL = legacy default stream)
+ * Allocates the arena, the per-slot tables, the host staging (pinned) and a
+ * second stream for admissions. Returns TVOLAP_ERR_OOM when an allocation
+ * fails.
+ */
+TVOLAP_API int tvolap_server_create(tvolap_server_t *out, int base_hop, int max_hop, int capacity,
+                                    int max_out, int64_t arena_bytes, void *stream);
+
+/* Wait for outstanding work and release everything. NULL is accepted. */
+TVOLAP_API int tvolap_server_destroy(tvolap_server_t s);
+
+/*
+ * Device bytes a stream of hop L, M partitions, n_out outputs and n_filters
+ * stored filters takes from the arena: its bank (n_filters * n_out * M spectra),
+ * its delay line (2M spectra), its overlap state (3L floats per output) and
+ * its input history (L floats), each rounded up to 256 bytes.
+ */
+TVOLAP_API int tvolap_server_footprint(tvolap_server_t s, int L, int M, int n_out, int n_filters,
+                                       int64_t *bytes);
+
+/*
+ * Admit a stream.
+ *   L          hop: base_hop * 2^k <= max_hop
+ *   M          partitions (responses of up to 2*L*M taps), >= 1
+ *   n_out      1 .. max_out outputs, all fed by the stream's one input
+ *   n_filters  stored filters, >= 1; filter f has one response per output
+ *   ir_dev     device float [n_filters * n_out][ir_stride]: response of
+ *              output o of filter f in row f * n_out + o, ir_len taps
+ *              (<= 2*L*M, zero beyond); kept valid by the caller until the
+ *              stream is live (tvolap_server_state) or the server is waited on
+ *   id         receives the stream id, in [0, capacity)
+ * The bank transform (Eqs. 2, 4, 6) and the zeroing of the stream's state run
+ * on the admission stream, overlapping ticks in flight; the stream becomes
+ * live, and starts to be listed as due, at the first tick planned after that
+ * work has finished. Returns TVOLAP_ERR_CAPACITY (nothing changed) when no
+ * slot or no arena piece is free.
+ */
+TVOLAP_API int tvolap_server_admit(tvolap_server_t s, int L, int M, int n_out, int n_filters,
+                                   const float *ir_dev, int ir_len, int64_t ir_stride, int *id);
+
+/* Retire a stream: it is never due again and its slot and memory are free. */
+TVOLAP_API int tvolap_server_retire(tvolap_server_t s, int id);
+
+/*
+ * State of stream id: 0 free, 1 admitted (bank transform pending), 2 live.
+ * blocks (may be NULL) receives the number of blocks the stream has been
+ * given so far, phase (may be NULL) its phase in base ticks.
+ */
+TVOLAP_API int tvolap_server_state(tvolap_server_t s, int id, int *state, int64_t *blocks,
+                                   int *phase);
+
+/*
+ * Host staging arrays of set `buffer` (0 or 1; pinned, valid for the
+ * server's life):
+ *   in   float [capacity][in_stride]          in_stride = max_hop
+ *   sel  int32 [capacity]                     (one array, read by tick)
+ *   out  float [capacity][max_out][out_stride] out_stride = max_hop
+ * Any pointer argument may be NULL.
+ */
+TVOLAP_API int tvolap_server_staging(tvolap_server_t s, int buffer, float **in,
+                                     int64_t *in_stride, int32_t **sel, float **out,
+                                     int64_t *out_stride);
+
+/*
+ * Streams due at the next tick, in increasing id order (live streams whose
+ * phase matches; streams whose admission work has finished turn live here).
+ * First waits for the tick that last used the next tick's staging set, whose
+ * index goes to *buffer (may be NULL). Writes up to cap ids to ids_host and
+ * the total to count.
+ */
+TVOLAP_API int tvolap_server_due(tvolap_server_t s, int32_t *ids_host, int cap, int *count,
+                                 int *buffer);
+
+/*
+ * Run the next tick on the due streams (the list tvolap_server_due returned,
+ * or would return). Reads sel[id] now and in[id] of its staging set when the
+ * tick executes. Returns TVOLAP_ERR_ARG, with nothing enqueued, when a due
+ * stream's sel is outside [0, n_filters). Returns without waiting; at most two
+ * ticks are in flight (a third waits for the first).
+ */
+TVOLAP_API int tvolap_server_tick(tvolap_server_t s);
+
+/*
+ * Wait until every enqueued tick and admission has finished; afterwards the
+ * out arrays of both staging sets hold the outputs of their last ticks. Returns TVOLAP_ERR_TIMEOUT when the input
+ * wait of TVOLAP_SERVER_OPT_WAIT_US ran out for a tick: that tick processed
+ * nothing, the due streams' block counts are rolled back (the same blocks
+ * are due again), and the server stays usable. TVOLAP_ERR_CUDA on a CUDA
+ * error.
+ */
+TVOLAP_API int tvolap_server_wait(tvolap_server_t s);
+
+/*
+ * Producer hand-off for TVOLAP_SERVER_OPT_WAIT_US: declare that the staging
+ * for tick number seq (1 for the first tick, then 2, 3, ...) is written. Any
+ * thread may call it.
+ */
+TVOLAP_API int tvolap_server_post(tvolap_server_t s, uint64_t seq);
+
+/* Options of tvolap_server_set_option. */
+typedef enum tvolap_server_option {
+    /* 1 (default): each tick is a CUDA-graph replay; 0: direct launches. */
+    TVOLAP_SERVER_OPT_GRAPH = 1,
+    /* 0 (default): ticks start at once. > 0: each tick first waits on the GPU,
+       for at most this many microseconds (<= 2000000), until
+       tvolap_server_post has declared its staging written; one tick is in
+       flight at a time. */
+    TVOLAP_SERVER_OPT_WAIT_US = 2,
+    /* 1: direct launches with CUDA events around the three stages; their
+       times accumulate into tvolap_server_stats. 0 (default): off. */
+    TVOLAP_SERVER_OPT_TIMING = 3
+} tvolap_server_option;
+
+TVOLAP_API int tvolap_server_set_option(tvolap_server_t s, int option, int64_t value);
+
+/* Counters of a server. */
+typedef struct tvolap_server_stats {
+    int64_t ticks;             /* ticks enqueued */
+    int64_t stream_blocks;     /* (stream, block) pairs processed */
+    int64_t channel_samples;   /* output samples produced, all outputs */
+    int64_t mac_bytes;         /* algorithmic bytes of Eq. 7: spectra read + written */
+    int32_t live, pending;     /* streams live / admitted but not yet live */
+    int32_t last_due, last_items;
+    int64_t arena_bytes, arena_used;
+    double stage_ms[3];        /* forward, multiply-accumulate, inverse (timing option) */
+    int64_t timed_ticks;       /* ticks that stage_ms covers */
+} tvolap_server_stats;
+
+TVOLAP_API int tvolap_server_stats_get(tvolap_server_t s, tvolap_server_stats *st);
+
+/* ------------------------------------------------------------------------
+ * The server's host-side scheduler on its own (no device memory, no GPU):
+ * slot allocation, arena placement, phase choice and due lists, exactly as
+ * the server uses them. Offsets are byte offsets into an arena of
+ * arena_bytes. Arguments and errors are those of the server calls above.
+ * ------------------------------------------------------------------------ */
+typedef struct tvolap_sched *tvolap_sched_t;
+
+TVOLAP_API int tvolap_sched_create(tvolap_sched_t *out, int base_hop, int max_hop, int capacity,
+                                   int max_out, int64_t arena_bytes);
+TVOLAP_API int tvolap_sched_destroy(tvolap_sched_t s);
+/* Footprint of a stream (as tvolap_server_footprint). */
+TVOLAP_API int tvolap_sched_footprint(int L, int M, int n_out, int n_filters, int64_t *bytes);
+/* Admit: receives the id, the arena offset and the phase. */
+TVOLAP_API int tvolap_sched_admit(tvolap_sched_t s, int L, int M, int n_out, int n_filters,
+                                  int *id, int64_t *offset, int *phase);
+TVOLAP_API int tvolap_sched_activate(tvolap_sched_t s, int id);
+TVOLAP_API int tvolap_sched_retire(tvolap_sched_t s, int id);
+/* Due ids at the next tick (live streams only), as tvolap_server_due. */
+TVOLAP_API int tvolap_sched_due(tvolap_sched_t s, int32_t *ids_host, int cap, int *count);
+/* Advance one tick: the due streams' block counts grow by one. */
+TVOLAP_API int tvolap_sched_advance(tvolap_sched_t s);
+/* Bytes of Eq. 7 read per base tick by the streams due at each phase
+   (loads[q] for q in [0, max_hop / base_hop)); *n receives that count. */
+TVOLAP_API int tvolap_sched_phase_loads(tvolap_sched_t s, int64_t *loads, int cap, int *n);
+/* Arena bytes in use, and the largest free piece. */
+TVOLAP_API int tvolap_sched_arena(tvolap_sched_t s, int64_t *used, int64_t *largest_free);
+
 #ifdef __cplusplus
 }
 #endif

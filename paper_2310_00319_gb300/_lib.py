@@ -18,6 +18,7 @@ _lib = None
 c_int, c_int64, c_float, c_void_p = ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p
 P_int32 = ctypes.POINTER(ctypes.c_int32)
 P_int = ctypes.POINTER(ctypes.c_int)
+P_int64 = ctypes.POINTER(ctypes.c_int64)
 
 # name -> (restype, argtypes); mirrors include/tvolap.h
 SIGNATURES = {
@@ -60,6 +61,34 @@ SIGNATURES = {
     "tvolap_process_signal_static": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p,
                                              c_void_p, c_void_p, c_int64, c_void_p, c_int64,
                                              c_int64]),
+    # streaming server
+    "tvolap_server_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int, c_int64,
+                                     c_void_p]),
+    "tvolap_server_destroy": (c_int, [c_void_p]),
+    "tvolap_server_footprint": (c_int, [c_void_p, c_int, c_int, c_int, c_int, P_int64]),
+    "tvolap_server_admit": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_int64,
+                                    P_int]),
+    "tvolap_server_retire": (c_int, [c_void_p, c_int]),
+    "tvolap_server_state": (c_int, [c_void_p, c_int, P_int, P_int64, P_int]),
+    "tvolap_server_staging": (c_int, [c_void_p, c_int, ctypes.POINTER(c_void_p), P_int64,
+                                      ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), P_int64]),
+    "tvolap_server_due": (c_int, [c_void_p, P_int32, c_int, P_int, P_int]),
+    "tvolap_server_tick": (c_int, [c_void_p]),
+    "tvolap_server_wait": (c_int, [c_void_p]),
+    "tvolap_server_post": (c_int, [c_void_p, ctypes.c_uint64]),
+    "tvolap_server_set_option": (c_int, [c_void_p, c_int, c_int64]),
+    "tvolap_server_stats_get": (c_int, [c_void_p, c_void_p]),
+    # host scheduler alone
+    "tvolap_sched_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int, c_int64]),
+    "tvolap_sched_destroy": (c_int, [c_void_p]),
+    "tvolap_sched_footprint": (c_int, [c_int, c_int, c_int, c_int, P_int64]),
+    "tvolap_sched_admit": (c_int, [c_void_p, c_int, c_int, c_int, c_int, P_int, P_int64, P_int]),
+    "tvolap_sched_activate": (c_int, [c_void_p, c_int]),
+    "tvolap_sched_retire": (c_int, [c_void_p, c_int]),
+    "tvolap_sched_due": (c_int, [c_void_p, P_int32, c_int, P_int]),
+    "tvolap_sched_advance": (c_int, [c_void_p]),
+    "tvolap_sched_phase_loads": (c_int, [c_void_p, P_int64, c_int, P_int]),
+    "tvolap_sched_arena": (c_int, [c_void_p, P_int64, P_int64]),
 }
 
 STATUS = {0: "TVOLAP_OK", -1: "TVOLAP_ERR_ARG", -2: "TVOLAP_ERR_OOM", -3: "TVOLAP_ERR_CUDA",

@@ -87,9 +87,11 @@ class BatchedTvolap:
         return self.graph
 
     def replay(self):
+        """Replay the captured batch on the batch's stream."""
         if self.graph is None:
             self.capture()
-        self.graph.replay()
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
 
     def output(self, i):
         """Output of source i (a view into its group's buffer)."""

@@ -33,7 +33,7 @@ def nvcc() -> str:
 
 
 def sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
 def _deps():
@@ -62,7 +62,7 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
 
 
 def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    """Compile every .cu under csrc/ and link lib/libtvolap.so; returns its path."""
+    """Compile every .cu and .cpp under csrc/ and link lib/libtvolap.so; returns its path."""
     if not force and not verbose_ptxas and up_to_date():
         return LIB_PATH
     os.makedirs(OBJ_DIR, exist_ok=True)

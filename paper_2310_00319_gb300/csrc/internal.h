@@ -78,6 +78,12 @@ cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, fl
                                int64_t out_len, int64_t y_stride, Ragged rg = Ragged{});
 cudaError_t launch_forward_stream(tvolap_plan *h, const float *in);
 cudaError_t launch_inverse_stream(tvolap_plan *h, float *out);
+// tables and bank transform for a hop L (P = 2L = 1 << lgP) outside a plan
+cudaError_t launch_tables_raw(float2 *tw, float2 *rot, float2 *post, float *win, int L,
+                              cudaStream_t st);
+cudaError_t launch_bank_raw(int lgP, int L, int M, int64_t count, const float *ir, int ir_len,
+                            int64_t ir_stride, const float2 *rot, const float2 *post,
+                            const float2 *tw, float2 *dst, cudaStream_t st);
 
 // kernels_mac_tma.cu (falls back to the cp.async kernel of kernels_mac.cu)
 cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, const int32_t *sa,

@@ -7,19 +7,12 @@
 //   k_inverse_stream    one block per output, overlap-add against the state
 // Every transform is P = 2L complex points (see fft_core.cuh); T = P/8 threads
 // run one transform, F = max(1, 256/T) transforms share a 256-thread CTA.
-#include "fft_core.cuh"
+#include "fft_block.cuh"
 #include "internal.h"
 
 namespace tvolap {
 
 namespace {
-
-template <int P>
-struct Geo {
-    static constexpr int T = P / 8;                    // threads per transform
-    static constexpr int F = (256 / T) > 0 ? 256 / T : 1;   // transforms per CTA
-    static constexpr int THREADS = T * F;
-};
 
 __global__ void k_tables(float2 *tw, float2 *rot, float2 *post, float *win, int L)
 {
@@ -37,30 +30,6 @@ __global__ void k_tables(float2 *tw, float2 *rot, float2 *post, float *win, int 
         // periodic Hann of length 2L with amplitude 1/2 (hop-L windows sum to 1)
         win[i] = (float)(0.5 * (1.0 - cospi((double)i / (double)L)));
     }
-}
-
-// Forward real transform of one zero-padded block whose first 2L samples are
-// given by src(n) (n < 2L): fills A, runs the FFT, splits into X via st.
-template <int P, bool FULL = false, class Src, class Store>
-__device__ __forceinline__ void forward_block(float2 *A, float2 *B, int j, bool active, Src src,
-                                              const float2 *__restrict__ rot,
-                                              const float2 *__restrict__ post,
-                                              const float2 *__restrict__ tw, Store st)
-{
-    constexpr int T = P / 8;
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        const int r = j + s * T;
-        float2 z = make_float2(0.f, 0.f);
-        // r < P/2 = L unless FULL: the upper half is the zero padding of Eqs. 3-4
-        if ((FULL || s < 4) && active) {
-            z = cmul(src(2 * r), __ldg(rot + r));
-        }
-        A[r] = z;
-    }
-    __syncthreads();
-    float2 *Z = fft_complex<P, false>(A, B, j, tw);
-    split_forward<P>(Z, j, post, st);
 }
 
 template <int LG>
@@ -346,43 +315,9 @@ k_inverse_stream(const float2 *__restrict__ Ys, float *__restrict__ ola, float *
     const int o = blockIdx.x * F + f;
     const bool active = o < n_out;
     const float2 *Yo = Ys + (int64_t)(active ? o : 0) * P;
-    merge_inverse<P>(A, j, post, [&](int k) { return active ? Yo[k] : make_float2(0.f, 0.f); });
-    __syncthreads();
-    float2 *Z = fft_complex<P, true>(A, B, j, tw);
-    const float inv_p = 1.0f / (float)P;
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        const int r = j + s * T;
-        Z[r] = cscale(cmulc(Z[r], __ldg(rot + r)), inv_p);
-    }
-    __syncthreads();
-    const float *yb = reinterpret_cast<const float *>(Z);
     float *st = ola + (int64_t)(active ? o : 0) * 3 * L;
     float *ou = out + (int64_t)(active ? o : 0) * L;
-    // read every pending sum this thread rewrites before any thread writes;
-    // T = L/4 threads cover the 3L pending sums in exactly 12 steps
-    float keep[12];
-#pragma unroll
-    for (int u = 0; u < 12; ++u) {
-        const int i = j + u * T;
-        float v = yb[i + L];
-        if (i < 2 * L) v += st[i + L];
-        keep[u] = v;
-    }
-    if (active)
-        for (int i = j; i < L; i += T) ou[i] = st[i] + yb[i];
-    __syncthreads();
-    if (active) {
-#pragma unroll
-        for (int u = 0; u < 12; ++u) st[j + u * T] = keep[u];
-    }
-}
-
-template <int LG>
-size_t smem_fft()
-{
-    constexpr int P = 1 << LG;
-    return (size_t)2 * Geo<P>::F * P * sizeof(float2);
+    inverse_stream_block<P>(A, B, j, active, [&](int k) { return Yo[k]; }, st, ou, rot, post, tw);
 }
 
 // Segment length (output hops per CTA) of the offline inverse.
@@ -402,25 +337,6 @@ cudaError_t launch_tables(tvolap_plan *h)
     return cudaGetLastError();
 }
 
-#define TVOLAP_DISPATCH(LGV, ...)             \
-    switch (LGV) {                            \
-    case 5: { constexpr int LG = 5; __VA_ARGS__; } break;   \
-    case 6: { constexpr int LG = 6; __VA_ARGS__; } break;   \
-    case 7: { constexpr int LG = 7; __VA_ARGS__; } break;   \
-    case 8: { constexpr int LG = 8; __VA_ARGS__; } break;   \
-    case 9: { constexpr int LG = 9; __VA_ARGS__; } break;   \
-    case 10: { constexpr int LG = 10; __VA_ARGS__; } break; \
-    case 11: { constexpr int LG = 11; __VA_ARGS__; } break; \
-    default: return cudaErrorInvalidValue;    \
-    }
-
-template <class Kern>
-static cudaError_t set_smem(Kern k, size_t bytes)
-{
-    if (bytes > 48 * 1024)
-        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    return cudaSuccess;
-}
 
 cudaError_t launch_forward_signal(tvolap_plan *h, const float *x, int64_t N, int64_t x_stride,
                                   int n_blocks, float2 *X)
@@ -459,6 +375,31 @@ cudaError_t launch_bank(tvolap_plan *h, int first_slot, int count, const float *
         if (e != cudaSuccess) return e;
         k_bank<LG><<<(unsigned)grid, Geo<P>::THREADS, sm, h->stream>>>(
             ir, ir_len, ir_stride, h->M, h->L, total, h->rot, h->post, h->tw, dst);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tables_raw(float2 *tw, float2 *rot, float2 *post, float *win, int L,
+                              cudaStream_t st)
+{
+    k_tables<<<(2 * L + 255) / 256, 256, 0, st>>>(tw, rot, post, win, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bank_raw(int lgP, int L, int M, int64_t count, const float *ir, int ir_len,
+                            int64_t ir_stride, const float2 *rot, const float2 *post,
+                            const float2 *tw, float2 *dst, cudaStream_t st)
+{
+    const int64_t total = count * M;
+    if (total == 0) return cudaSuccess;
+    TVOLAP_DISPATCH(lgP, {
+        constexpr int P = 1 << LG;
+        const int64_t grid = (total + Geo<P>::F - 1) / Geo<P>::F;
+        const size_t sm = smem_fft<LG>();
+        cudaError_t e = set_smem(k_bank<LG>, sm);
+        if (e != cudaSuccess) return e;
+        k_bank<LG><<<(unsigned)grid, Geo<P>::THREADS, sm, st>>>(ir, ir_len, ir_stride, M, L, total,
+                                                              rot, post, tw, dst);
     });
     return cudaGetLastError();
 }

@@ -238,3 +238,78 @@ def batched_uneven(seed=3, n_src=512, hops=(64, 128, 256, 512), ir_min=4800, ir_
         sched = cyclic_schedule(nb, n_ir, k)
         out.append(Source(L, _f32(x), _f32(irs), _i32(sched), N))
     return out
+
+
+# ----------------------------------------------------------------------------- serving
+def binaural_pair(rng, n: int, t60: float, rho: float = 0.5, fs: int = FS) -> np.ndarray:
+    """[2, n]: left = Gaussian noise g_l, right = rho g_l + sqrt(1 - rho^2) g_r
+    (correlation rho), both times the same 60 dB-per-T60 decay, each scaled to
+    unit energy."""
+    k = np.arange(n, dtype=np.float64)
+    env = 10.0 ** (-3.0 * k / (fs * t60))
+    gl = rng.standard_normal(n)
+    gr = rho * gl + np.sqrt(1.0 - rho * rho) * rng.standard_normal(n)
+    out = np.stack([gl * env, gr * env])
+    return out / np.sqrt(np.sum(out * out, axis=1, keepdims=True))
+
+
+def serving_bank(rng, ir_len: int, n_pairs: int = 36, fs: int = FS) -> np.ndarray:
+    """[n_pairs, 2, ir_len] float32 binaural pairs, T60 = ir_len / 3 samples
+    expressed in seconds (as for the batched sources)."""
+    t60 = ir_len / (3.0 * fs)
+    return _f32(np.stack([binaural_pair(rng, ir_len, t60, fs=fs) for _ in range(n_pairs)]))
+
+
+def head_walk(rng, n_blocks: int, n_pairs: int = 36) -> np.ndarray:
+    """Pair index per block: a start uniform over the pairs, then steps of -1, 0
+    or +1 (equally likely) modulo n_pairs."""
+    p0 = int(rng.integers(0, n_pairs))
+    steps = rng.integers(-1, 2, size=n_blocks)
+    steps[0] = 0
+    return _i32(np.mod(p0 + np.cumsum(steps), n_pairs))
+
+
+@dataclass
+class ServeStream:
+    """One stream of the serving workload: hop L, binaural bank irs
+    [n_pairs, 2, ir_len], input x [n_blocks * L] and pair index per block."""
+    L: int
+    irs: np.ndarray
+    x: np.ndarray
+    sel: np.ndarray
+
+    @property
+    def n_blocks(self):
+        return self.sel.shape[0]
+
+
+def serving_streams(seed: int, n: int, hops=(16, 32, 64), ir_min=200, ir_max=1500,
+                    n_pairs=6, blocks=(20, 60)) -> list:
+    """Small streams for parity checks: hop uniform over `hops`, response length
+    uniform in [ir_min, ir_max], white input (sigma 0.1) of a block count
+    uniform in `blocks`, head walk over n_pairs pairs."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        L = int(rng.choice(hops))
+        ir_len = int(rng.integers(ir_min, ir_max + 1))
+        nb = int(rng.integers(blocks[0], blocks[1] + 1))
+        irs = serving_bank(rng, ir_len, n_pairs)
+        out.append(ServeStream(L, irs, _f32(white(rng, nb * L)), head_walk(rng, nb, n_pairs)))
+    return out
+
+
+def serving_arrivals(seed=5, duration_s=13.0, rate=50.0, life_min=2.0, life_max=30.0,
+                     prefill=1000, base_hop=64, fs=FS):
+    """Arrival and departure times, in base ticks of base_hop samples, of the
+    serving workload: `prefill` streams present at tick 0, then Poisson arrivals
+    at `rate` per second; every lifetime uniform in [life_min, life_max] s.
+    Returns an int64 array [n, 2] of (arrive, leave) sorted by arrival."""
+    rng = np.random.default_rng(seed)
+    tick_s = base_hop / fs
+    n_new = int(rng.poisson(rate * duration_s))
+    t_new = np.sort(rng.uniform(0.0, duration_s, n_new))
+    arrive = np.concatenate([np.zeros(prefill), t_new])
+    life = rng.uniform(life_min, life_max, arrive.shape[0])
+    ev = np.stack([np.floor(arrive / tick_s), np.floor((arrive + life) / tick_s)], axis=1)
+    return ev.astype(np.int64)

@@ -1,0 +1,232 @@
+"""GPU tests of the streaming server (tvolap_server_*): every stream against the
+FP64 oracle (output delayed by L), one stream alone and in a mix of streams
+arriving and leaving (bit-identical), graph replay against direct launches,
+admission by device footprint, a bad filter index, and the bounded input wait
+running out (a flag nothing sets) with the server staying usable.
+
+Tolerance against the oracle: rel-L2 <= 1e-5 and max-abs <= 1e-4 x peak.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TIMEOUT_STATUS = -6
+CAPACITY_STATUS = -5
+ARG_STATUS = -1
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _server(dev, base=16, top=64, cap=16, arena=256 << 20, **kw):
+    from paper_2310_00319_gb300.server import Server
+    return Server(base, top, cap, max_out=2, arena_bytes=arena, device=dev, **kw)
+
+
+def _irs(s, n_out, dev):
+    return torch.from_numpy(np.ascontiguousarray(s.irs[:, :n_out])).to(dev)
+
+
+def drive(srv, streams, starts, dev, n_outs=None, max_ticks=100000):
+    """Admit stream i at tick starts[i], feed one block per due tick, retire
+    it after its last block. Returns each stream's output blocks [n_out, nb, L]."""
+    n_outs = n_outs or [2] * len(streams)
+    outs = [np.zeros((n_outs[i], s.n_blocks, s.L), np.float32) for i, s in enumerate(streams)]
+    ids = [None] * len(streams)
+    given = [0] * len(streams)
+    done = 0
+    owner = {}
+    tick = 0
+    while done < len(streams) and tick < max_ticks:
+        for i, s in enumerate(streams):
+            if ids[i] is None and starts[i] == tick:
+                ids[i] = srv.admit(s.L, _irs(s, n_outs[i], dev))
+                owner[ids[i]] = i
+        due = srv.due()
+        for sid in due:
+            i = owner[int(sid)]
+            s, b = streams[i], given[i]
+            assert srv.state(int(sid))[1] == b
+            srv.inp[sid, :s.L] = s.x[b * s.L:(b + 1) * s.L]
+            srv.sel[sid] = s.sel[b]
+        srv.tick()
+        srv.wait()
+        for sid in due:
+            i = owner[int(sid)]
+            s, b = streams[i], given[i]
+            outs[i][:, b, :] = srv.out[sid, :n_outs[i], :s.L]
+            given[i] += 1
+            if given[i] == s.n_blocks:
+                srv.retire(int(sid))
+                del owner[int(sid)]
+                done += 1
+        tick += 1
+    assert done == len(streams), "streams did not finish"
+    return outs
+
+
+def _oracle_stream(s, n_out):
+    nb, L = s.n_blocks, s.L
+    F, _, ir_len = s.irs.shape
+    irs = s.irs[:, :n_out].reshape(F * n_out, ir_len)
+    sched = np.stack([s.sel * n_out + o for o in range(n_out)]).astype(np.int32)
+    return oracle.tvolap_direct(s.x[None, :], irs, L, sched, out_len=(nb - 1) * L,
+                                out_to_in=[0] * n_out)
+
+
+def _assert_close(y, ref, what):
+    rel = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    mx = np.max(np.abs(y - ref)) / np.max(np.abs(ref))
+    assert rel <= 1e-5 and mx <= 1e-4, (what, rel, mx)
+
+
+def test_streams_match_oracle():
+    dev = _dev()
+    S = W.serving_streams(41, 7)
+    n_outs = [2, 1, 2, 2, 1, 2, 2]
+    starts = [0, 0, 3, 5, 9, 14, 20]
+    srv = _server(dev)
+    outs = drive(srv, S, starts, dev, n_outs)
+    for i, s in enumerate(S):
+        ref = _oracle_stream(s, n_outs[i])
+        y = outs[i].reshape(n_outs[i], -1).astype(np.float64)
+        # block 0 emits samples [-L, 0): silence up to FP32 rounding
+        assert np.max(np.abs(y[:, :s.L])) <= 1e-5 * np.max(np.abs(ref)), i
+        _assert_close(y[:, s.L:], ref, (i, s.L))
+    st = srv.stats()
+    assert st["live"] == 0 and st["pending"] == 0 and st["arena_used"] == 0
+    srv.close()
+
+
+def test_alone_equals_mix_bitwise():
+    """Continuous batching: the result of a stream does not depend on the other
+    streams admitted, running or retired around it."""
+    dev = _dev()
+    A = W.serving_streams(42, 1, hops=(32,), blocks=(70, 70))[0]
+    others = W.serving_streams(43, 9, blocks=(10, 40))
+    srv = _server(dev)
+    alone = drive(srv, [A], [0], dev)[0]
+    srv.close()
+    srv = _server(dev)
+    starts = [5] + [int(v) for v in np.random.default_rng(1).integers(0, 60, len(others))]
+    mix = drive(srv, [A] + others, starts, dev)[0]
+    srv.close()
+    np.testing.assert_array_equal(alone, mix)
+
+
+def test_graph_equals_direct_launches_and_timing():
+    dev = _dev()
+    from paper_2310_00319_gb300.server import OPT_GRAPH, OPT_TIMING
+    S = W.serving_streams(44, 5)
+    starts = [0, 1, 2, 3, 4]
+    runs = []
+    for opt in ((OPT_GRAPH, 1), (OPT_GRAPH, 0), (OPT_TIMING, 1)):
+        srv = _server(dev)
+        srv.set_option(*opt)
+        runs.append(drive(srv, S, starts, dev))
+        st = srv.stats()
+        if opt[0] == OPT_TIMING:
+            assert st["timed_ticks"] == st["ticks"] > 0
+            assert all(v > 0 for v in st["stage_ms"])
+        srv.close()
+    for r in runs[1:]:
+        for a, b in zip(runs[0], r):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_admission_by_footprint():
+    dev = _dev()
+    from paper_2310_00319_gb300._lib import TvolapError
+    S = W.serving_streams(45, 3, hops=(64,), ir_min=1000, ir_max=1000)
+    probe = _server(dev)
+    fp = probe.footprint(64, -(-1000 // 128), 2, S[0].irs.shape[0])
+    probe.close()
+    srv = _server(dev, cap=8, arena=2 * fp)
+    a = srv.admit(64, _irs(S[0], 2, dev))
+    b = srv.admit(64, _irs(S[1], 2, dev))
+    with pytest.raises(TvolapError) as ei:
+        srv.admit(64, _irs(S[2], 2, dev))
+    assert ei.value.status == CAPACITY_STATUS
+    assert srv.stats()["arena_used"] == 2 * fp
+    srv.retire(a)
+    c = srv.admit(64, _irs(S[2], 2, dev))
+    assert c == a and srv.stats()["arena_used"] == 2 * fp
+    srv.retire(b)
+    srv.retire(c)
+    srv.wait()
+    srv.close()
+    # slot limit: two slots, arena to spare
+    srv = _server(dev, cap=2, arena=16 * fp)
+    srv.admit(64, _irs(S[0], 2, dev))
+    srv.admit(64, _irs(S[1], 2, dev))
+    with pytest.raises(TvolapError) as ei:
+        srv.admit(64, _irs(S[2], 2, dev))
+    assert ei.value.status == CAPACITY_STATUS
+    srv.wait()
+    srv.close()
+
+
+def test_bad_filter_index_is_rejected():
+    dev = _dev()
+    from paper_2310_00319_gb300._lib import TvolapError
+    s = W.serving_streams(46, 1)[0]
+    srv = _server(dev)
+    i = srv.admit(s.L, _irs(s, 2, dev))
+    srv.wait()
+    while len(srv.due()) == 0:
+        srv.tick()
+        srv.wait()
+    srv.sel[i] = s.irs.shape[0]           # one past the last filter
+    with pytest.raises(TvolapError) as ei:
+        srv.tick()
+    assert ei.value.status == ARG_STATUS
+    assert srv.state(i)[1] == 0 and srv.stats()["ticks"] >= 0
+    srv.close()
+
+
+def test_input_wait_times_out_and_server_recovers():
+    """With the input wait on, a tick whose staging is never declared written
+    gives up after the limit (no fault, no hang), processes nothing and is
+    rolled back; the same blocks then run normally and the outputs equal those
+    of a run that never timed out."""
+    dev = _dev()
+    from paper_2310_00319_gb300._lib import TvolapError
+    from paper_2310_00319_gb300.server import OPT_WAIT_US
+    s = W.serving_streams(47, 1, hops=(16,), blocks=(30, 30))[0]
+    srv = _server(dev)
+    ref = drive(srv, [s], [0], dev)[0]
+    srv.close()
+
+    srv = _server(dev)
+    srv.set_option(OPT_WAIT_US, 20000)                   # 20 ms
+    i = srv.admit(s.L, _irs(s, 2, dev))
+    srv.wait()
+    due = srv.due()
+    assert list(due) == [i]
+    srv.inp[i, :s.L] = s.x[:s.L]
+    srv.sel[i] = s.sel[0]
+    srv.tick()                                           # nothing posts tick 1
+    with pytest.raises(TvolapError) as ei:
+        srv.wait()
+    assert ei.value.status == TIMEOUT_STATUS
+    assert srv.state(i)[1] == 0 and srv.stats()["ticks"] == 0
+    # the same tick again, now posted: runs normally from here on
+    out = np.zeros_like(ref)
+    for b in range(s.n_blocks):
+        assert list(srv.due()) == [i]
+        srv.inp[i, :s.L] = s.x[b * s.L:(b + 1) * s.L]
+        srv.sel[i] = s.sel[b]
+        srv.post(srv.stats()["ticks"] + 1)              # the next tick's number
+        srv.tick()
+        srv.wait()
+        out[:, b, :] = srv.out[i, :2, :s.L]
+    np.testing.assert_array_equal(out, ref)
+    srv.close()
