@@ -508,7 +508,9 @@ def run_batched(args):
     ms = t0e.elapsed_time(t1e) / args.steps
     launches = 4 * len(B.groups)    # per hop group: forward, MAC group + overflow, inverse
 
-    # plain per-source form
+    # plain per-source form: one single-channel process_signal per source in a
+    # loop, with the staging the autotuner chose for the source's hop (same
+    # kernels), and again with the default staging
     stream = torch.cuda.current_stream(dev)
     per = []
     for s in S:
@@ -516,21 +518,28 @@ def run_batched(args):
         p.load_bank(0, torch.from_numpy(s.irs).to(dev))
         per.append((p, torch.from_numpy(s.x[None, :]).to(dev),
                     torch.from_numpy(s.sched[None, :]).to(dev),
-                    torch.empty((1, s.out_len), dtype=torch.float32, device=dev), s.out_len))
+                    torch.empty((1, s.out_len), dtype=torch.float32, device=dev), s.out_len, s.L))
 
     def loop():
-        for p, x, sc, y, ol in per:
+        for p, x, sc, y, ol, _ in per:
             p.process_signal(x, sc, out_len=ol, out=y)
-    loop()
-    torch.cuda.synchronize(dev)
-    reps = max(1, min(3, args.steps))
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(reps):
+
+    def time_loop():
         loop()
-    b.record(stream)
-    torch.cuda.synchronize(dev)
-    per_ms = a.elapsed_time(b) / reps
+        torch.cuda.synchronize(dev)
+        reps = max(1, min(3, args.steps))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            loop()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    default_ms = time_loop()
+    for p, *_, L in per:
+        p.set_option(1, tuned[L][0])
+    per_ms = time_loop()
     for p, *_ in per:
         p.check()
         p.close()
@@ -553,7 +562,9 @@ def run_batched(args):
                        "l2": "inputs larger than L2 (about 1 GB of input, 10 GB of spectra)"},
             "vs_per_source": {"per_source_ms_per_step": round(per_ms, 4),
                               "batched_ms_per_step": round(ms, 4),
-                              "ratio": round(per_ms / ms, 3)},
+                              "ratio": round(per_ms / ms, 3),
+                              "per_source_default_staging_ms": round(default_ms, 4),
+                              "note": "per-source loop with the staging chosen for its hop"},
             "roofline": {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1),
                          "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
                          "kernel": "whole step: Eq. 7 flops / replay time (lower bound on "

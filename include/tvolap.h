@@ -328,7 +328,11 @@ TVOLAP_API int tvolap_process_signal_static(tvolap_t h, const float *x_dev, int6
 typedef enum tvolap_option {
     /* Staging of the offline multiply-accumulate: 0 = tiled bulk tensor copies
        (TMA) when the buffers allow it, else cp.async (default); 1 = always
-       cp.async. Both give identical results. */
+       cp.async; 2 = as 0, with up to four distinct filters staged per group of
+       64 consecutive blocks instead of three (for schedules that cycle four
+       filters; fewer resident groups per SM). 0 and 1 give identical results;
+       2 differs from them only in the rounding of blocks whose group holds
+       four filters. */
     TVOLAP_OPT_MAC_STAGING = 1
 } tvolap_option;
 

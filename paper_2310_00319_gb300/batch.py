@@ -6,7 +6,7 @@ whose channels are the group's sources, processed with
 tvolap_process_ragged (per-channel lengths and partition counts). All plans
 share one CUDA stream, so the whole batch can be captured once as a CUDA graph
 and replayed. ``autotune`` picks the multiply-accumulate staging per group by
-timing both variants on the batch itself.
+timing the variants on the batch itself.
 """
 from __future__ import annotations
 
@@ -102,12 +102,13 @@ class BatchedTvolap:
         raise IndexError(i)
 
     def autotune(self, reps=3):
-        """Per group, time both multiply-accumulate stagings on this batch and
-        keep the faster one. Returns {L: (chosen option, ms per variant)}."""
+        """Per group, time the multiply-accumulate stagings on this batch (TMA
+        groups of up to 3 or 4 filters, cp.async) and keep the fastest.
+        Returns {L: (chosen option, ms per option)}."""
         chosen = {}
         for g in self.groups:
             times = []
-            for opt in (0, 1):
+            for opt in (0, 1, 2):
                 g.plan.set_option(1, opt)
                 g.run()
                 torch.cuda.synchronize(self.device)

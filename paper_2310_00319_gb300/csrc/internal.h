@@ -35,7 +35,8 @@ struct tvolap_plan {
     float2 *Ystream;              // [n_out][P] this tick's output spectra
     int64_t tick;
 
-    int mac_variant;              // 0: TMA staging when possible, 1: cp.async staging
+    int mac_variant;              // 0: TMA staging (groups of <= 3 slots) when possible,
+                                  // 1: cp.async staging, 2: TMA staging, groups of <= 4 slots
     int4 *ovf_list;               // groups the group kernel hands to the per-warp kernel
     int *ovf_count;
     int64_t ovf_cap;

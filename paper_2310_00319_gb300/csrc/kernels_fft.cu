@@ -52,6 +52,9 @@ k_forward_signal(const float *__restrict__ x, int64_t N, int64_t x_stride, int L
         N = nc < 0 ? 0 : (nc < N ? nc : N);
         int64_t oc = rg.out_len[c];
         active = active && (t_first + t < blocks_of(oc, L));
+        // past every channel's last block: the whole CTA leaves (uniform vote,
+        // before the transform's barriers)
+        if (!__syncthreads_or(active)) return;
     }
     const int64_t start = (t_first + t - 1) * (int64_t)L;   // block l = t - 1 starts at l*L
     const float *xc = x + c * x_stride;

@@ -330,25 +330,33 @@ k_mac_overflow_tma(const __grid_constant__ CUtensorMap xmap, const __grid_consta
 // products are exact zeros.
 constexpr int NSTAGE = 3;
 constexpr int XRING = 64;                             // rows; chunk c writes slots [-8c, -8c+8) mod 64
-constexpr int HSTAGE_ROWS = MAX_NS * TMA_D;
-constexpr int GROUP_BYTES = 256 + XRING * ROW_BYTES + NSTAGE * HSTAGE_ROWS * ROW_BYTES;
+// NSM: most distinct slots a group may stage (3, or 4 for schedules cycling
+// four filters); groups with more go to the overflow list.
+template <int NSM>
+struct GroupGeo {
+    static constexpr int HSTAGE_ROWS = NSM * TMA_D;
+    static constexpr int BYTES = 256 + XRING * ROW_BYTES + NSTAGE * HSTAGE_ROWS * ROW_BYTES;
+    static constexpr int MIN_CTAS = NSM <= 3 ? 4 : 3;  // CTAs per SM the registers must allow
+};
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+template <int NSM>
 struct GroupSmem {
     uint64_t bar[1 + 2 * NSTAGE];     // 0 window, 1.. full, 1+NSTAGE.. empty
     int U, overflow, n_active;
-    int slot[MAX_NS];
+    int slot[NSM];
 };
+static_assert(sizeof(GroupSmem<4>) <= 256, "group header must fit its 256 bytes");
 
 __device__ __forceinline__ int ring_slot(int j) { return j & (XRING - 1); }
 
-template <int NS>
-__device__ __forceinline__ void group_chunk(const float2 *xs, const float2 *const (&hb)[MAX_NS],
-                                            int c, const RunSlots<TMA_R> &rs,
+template <int NS, int NSM>
+__device__ __forceinline__ void group_chunk(const float2 *xs, const float2 *const (&hb)[NSM],
+                                            int c, const RunSlots<TMA_R, NSM> &rs,
                                             float2 (&xw)[TMA_R], float2 (&acc)[TMA_R])
 {
     constexpr int D = TMA_D, R = TMA_R;
@@ -358,15 +366,15 @@ __device__ __forceinline__ void group_chunk(const float2 *xs, const float2 *cons
         float2 hs[NS > 1 ? NS - 1 : 1];
 #pragma unroll
         for (int j = 1; j < NS; ++j) hs[j - 1] = hb[j][u * 32];
-        run_step<R, NS>(acc, xw, hb[0][u * 32], hs, rs.w, u);
+        run_step<R, NS, NSM>(acc, xw, hb[0][u * 32], hs, rs.w, u);
     }
 }
 
-template <int NS>
-__device__ __forceinline__ bool group_consume(GroupSmem *gs, const float2 *xring, const float2 *hst,
-                                              int w, int lane, int nchunks, int m_end,
-                                              const RunSlots<TMA_R> &rs, const int (&idx)[MAX_NS],
-                                              float2 (&acc)[TMA_R])
+template <int NS, int NSM>
+__device__ __forceinline__ bool group_consume(GroupSmem<NSM> *gs, const float2 *xring,
+                                              const float2 *hst, int w, int lane, int nchunks,
+                                              int m_end, const RunSlots<TMA_R, NSM> &rs,
+                                              const int (&idx)[NSM], float2 (&acc)[TMA_R])
 {
     constexpr int D = TMA_D, R = TMA_R;
     float2 xw[R];
@@ -383,11 +391,11 @@ __device__ __forceinline__ bool group_consume(GroupSmem *gs, const float2 *xring
         if (c * D < m_end) {
             // rows i = 8w - 8c - u, u < 8: ring slots 8(w - c) .. 8(w - c) + 7, row 7 - u
             const float2 *xs = xring + ring_slot(D * (w - c)) * 32 + lane;
-            const float2 *st = hst + q * HSTAGE_ROWS * 32 + lane;
-            const float2 *hb[MAX_NS];
+            const float2 *st = hst + q * GroupGeo<NSM>::HSTAGE_ROWS * 32 + lane;
+            const float2 *hb[NSM];
 #pragma unroll
-            for (int j = 0; j < MAX_NS; ++j) hb[j] = st + idx[j] * D * 32;
-            group_chunk<NS>(xs, hb, c, rs, xw, acc);
+            for (int j = 0; j < NSM; ++j) hb[j] = st + idx[j] * D * 32;
+            group_chunk<NS, NSM>(xs, hb, c, rs, xw, acc);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(gs->bar + 1 + NSTAGE + q);
@@ -397,7 +405,8 @@ __device__ __forceinline__ bool group_consume(GroupSmem *gs, const float2 *xring
 
 // grid: x = (group, parity) pairs, y = 32-bin tiles, z = output channels;
 // 4 consumer warps + 1 loader warp.
-__global__ void __launch_bounds__(32 * (GW + 1), 4)
+template <int NSM>
+__global__ void __launch_bounds__(32 * (GW + 1), GroupGeo<NSM>::MIN_CTAS)
 k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap hmap,
                    int n_blocks, int M, int P, int n_slots_total, int null_slot,
                    const int32_t *__restrict__ out_to_in, const int32_t *__restrict__ sa,
@@ -420,7 +429,7 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
     group_origin(p, grp, T0);
     if (T0 >= n_blocks) return;                        // whole CTA
     if (*(volatile unsigned *)err & ERR_TIMEOUT) return;
-    GroupSmem *gs = reinterpret_cast<GroupSmem *>(smem_raw);
+    GroupSmem<NSM> *gs = reinterpret_cast<GroupSmem<NSM> *>(smem_raw);
     float2 *xring = reinterpret_cast<float2 *>(smem_raw + 256);
     float2 *hst = reinterpret_cast<float2 *>(smem_raw + 256 + XRING * ROW_BYTES);
     const int o = blockIdx.z, k0 = blockIdx.y * 32;
@@ -441,12 +450,12 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
             vb = (al != 0.f) && (b != a);
         }
         int U = 0, ovf = 0;
-        for (int it = 0; it <= MAX_NS; ++it) {
+        for (int it = 0; it <= NSM; ++it) {
             const unsigned ma = __ballot_sync(0xffffffffu, va), mb = __ballot_sync(0xffffffffu, vb);
             if (!ma && !mb) break;
             const int v = ma ? __shfl_sync(0xffffffffu, a, __ffs(ma) - 1)
                              : __shfl_sync(0xffffffffu, b, __ffs(mb) - 1);
-            if (U == MAX_NS) {
+            if (U == NSM) {
                 ovf = 1;
                 break;
             }
@@ -509,7 +518,8 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
                 tma_load_3d(xring + ring_slot(-D * c) * 32, &xmap, k0, T0 - 2 * D * c - 2 * (D - 1),
                             cin, bar);
                 for (int j = 0; j < U; ++j)
-                    tma_load_3d(hst + (q * HSTAGE_ROWS + j * D) * 32, &hmap, k0, c * D, gs->slot[j], bar);
+                    tma_load_3d(hst + (q * GroupGeo<NSM>::HSTAGE_ROWS + j * D) * 32, &hmap, k0, c * D,
+                                gs->slot[j], bar);
             }
         }
         if (!ok) {
@@ -524,23 +534,27 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
     }
     if (w >= n_active) return;                        // ---- consumers (no CTA barriers below)
     const int tf = T0 + 2 * R * w;
-    RunSlots<R> rs;
-    run_slots<R>(ao, bo, alo, tf, n_blocks, n_slots_total, null_slot, err, rs);
-    int idx[MAX_NS] = {0, 0, 0};
+    RunSlots<R, NSM> rs;
+    run_slots<R, NSM>(ao, bo, alo, tf, n_blocks, n_slots_total, null_slot, err, rs);
+    int idx[NSM];
 #pragma unroll
-    for (int j = 0; j < MAX_NS; ++j)
+    for (int j = 0; j < NSM; ++j) {
+        idx[j] = 0;
         for (int q = 0; q < U; ++q)
             if (j < rs.ns && gs->slot[q] == rs.sl[j]) idx[j] = q;
+    }
     int m_end = (tf + 2 * (R - 1)) / 2 + 1;
     if (m_end > M) m_end = M;
     float2 acc[R];
     bool ok;
     if (rs.ns == 1)
-        ok = group_consume<1>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
+        ok = group_consume<1, NSM>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
     else if (rs.ns == 2)
-        ok = group_consume<2>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
+        ok = group_consume<2, NSM>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
+    else if (NSM == 3 || rs.ns == 3)
+        ok = group_consume<3, NSM>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
     else
-        ok = group_consume<3>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
+        ok = group_consume<NSM, NSM>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
     if (!ok) {
         if (lane == 0) atomicOr(err, ERR_TIMEOUT);
         return;
@@ -590,6 +604,23 @@ bool encode_spectra(CUtensorMap *map, const void *base, int P, int64_t dim1, int
     return r == CUDA_SUCCESS;
 }
 
+template <int NSM>
+cudaError_t launch_group(dim3 grid, const CUtensorMap &xrun, const CUtensorMap &hmap,
+                         tvolap_plan *h, int n_blocks, const int32_t *sa, const int32_t *sb,
+                         const float *sal, int64_t sched_stride, float2 *Y, Ragged rg)
+{
+    const size_t gsmem = GroupGeo<NSM>::BYTES;
+    if (gsmem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_mac_signal_group<NSM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
+        if (e != cudaSuccess) return e;
+    }
+    k_mac_signal_group<NSM><<<grid, 32 * (GW + 1), gsmem, h->stream>>>(
+        xrun, hmap, n_blocks, h->M, h->P, h->n_slots_total, h->null_slot, h->out_to_in, sa, sb,
+        sal, sched_stride, Y, h->err, h->ovf_list, h->ovf_count, rg);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, const int32_t *sa,
@@ -609,17 +640,10 @@ cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, con
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(h->ovf_count, 0, sizeof(int), h->stream);
     if (e != cudaSuccess) return e;
-    const size_t gsmem = GROUP_BYTES;
-    if (gsmem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_mac_signal_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)gsmem);
-        if (e != cudaSuccess) return e;
-    }
     dim3 grid((unsigned)(2 * groups), (unsigned)tiles, (unsigned)h->n_out);
-    k_mac_signal_group<<<grid, 32 * (GW + 1), gsmem, h->stream>>>(
-        xrun, hmap, n_blocks, h->M, h->P, h->n_slots_total, h->null_slot, h->out_to_in, sa, sb,
-        sal, sched_stride, Y, h->err, h->ovf_list, h->ovf_count, rg);
-    e = cudaGetLastError();
+    e = h->mac_variant == 2
+            ? launch_group<4>(grid, xrun, hmap, h, n_blocks, sa, sb, sal, sched_stride, Y, rg)
+            : launch_group<3>(grid, xrun, hmap, h, n_blocks, sa, sb, sal, sched_stride, Y, rg);
     if (e != cudaSuccess) return e;
     const size_t wsmem = (size_t)TMA_WARPS * WARP_BYTES;
     if (wsmem > 48 * 1024) {

@@ -29,24 +29,25 @@ __device__ __forceinline__ void cmac(float2 &acc, float2 h, float2 x)
 
 // Within a run of R blocks the filter of block r is a mix of the run's
 // distinct slots s_0 .. s_{ns-1}: H_r = sum_j w_rj H_{s_j} with sum_j w_rj = 1,
-// so H_r = H_{s_0} + sum_{j>=1} w_rj (H_{s_j} - H_{s_0}).
+// so H_r = H_{s_0} + sum_{j>=1} w_rj (H_{s_j} - H_{s_0}). NSM is the most
+// distinct slots a run may hold (MAX_NS unless a kernel is built for more).
 constexpr int MAX_NS = 3;
 
-template <int R>
+template <int R, int NSM = MAX_NS>
 struct RunSlots {
-    int sl[MAX_NS];
+    int sl[NSM];
     int ns;
-    bool overflow;               // more than MAX_NS distinct slots
-    float2 w[R][MAX_NS - 1];     // weights of s_1, s_2 per block, as (w, w) pairs
+    bool overflow;               // more than NSM distinct slots
+    float2 w[R][NSM - 1];        // weights of s_1 .. s_{NSM-1} per block, as (w, w) pairs
 };
 
 // Schedule of blocks tf, tf+2, .., tf+2(R-1) (rows past n_blocks repeat the
 // last valid row; their results are dropped).
-template <int R>
+template <int R, int NSM = MAX_NS>
 __device__ __forceinline__ void run_slots(const int32_t *__restrict__ ao, const int32_t *__restrict__ bo,
                                           const float *__restrict__ alo, int tf, int n_blocks,
                                           int n_slots_total, int null_slot, unsigned *err,
-                                          RunSlots<R> &rs)
+                                          RunSlots<R, NSM> &rs)
 {
     int a[R], b[R];
     float al[R];
@@ -66,7 +67,7 @@ __device__ __forceinline__ void run_slots(const int32_t *__restrict__ ao, const 
     int ns = 0;
     bool overflow = false;
 #pragma unroll
-    for (int j = 0; j < MAX_NS; ++j) rs.sl[j] = 0;
+    for (int j = 0; j < NSM; ++j) rs.sl[j] = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
 #pragma unroll
@@ -76,11 +77,11 @@ __device__ __forceinline__ void run_slots(const int32_t *__restrict__ ao, const 
             if (wt == 0.f && !(q == 0 && b[r] == a[r])) continue;   // slot unused by this block
             bool seen = false;
 #pragma unroll
-            for (int j = 0; j < MAX_NS; ++j) seen |= (j < ns) && (rs.sl[j] == v);
+            for (int j = 0; j < NSM; ++j) seen |= (j < ns) && (rs.sl[j] == v);
             if (!seen) {
-                if (ns < MAX_NS) {
+                if (ns < NSM) {
 #pragma unroll
-                    for (int j = 0; j < MAX_NS; ++j)
+                    for (int j = 0; j < NSM; ++j)
                         if (j == ns) rs.sl[j] = v;
                     ++ns;
                 } else {
@@ -98,7 +99,7 @@ __device__ __forceinline__ void run_slots(const int32_t *__restrict__ ao, const 
 #pragma unroll
     for (int r = 0; r < R; ++r) {
 #pragma unroll
-        for (int j = 1; j < MAX_NS; ++j) {
+        for (int j = 1; j < NSM; ++j) {
             const float wj = (a[r] == rs.sl[j] ? 1.f - al[r] : 0.f) + (b[r] == rs.sl[j] ? al[r] : 0.f);
             rs.w[r][j - 1] = make_float2(wj, wj);
         }
@@ -108,9 +109,9 @@ __device__ __forceinline__ void run_slots(const int32_t *__restrict__ ao, const 
 // One step of Eq. 7 for the R blocks of a run: partition values h0 = H_{s_0}(m),
 // hs[j-1] = H_{s_j}(m); xw holds X(tf + 2(r - m)) at index (r - u) mod R, with
 // u = m mod R. Callers unroll over u so every register index is a constant.
-template <int R, int NS>
+template <int R, int NS, int NSM = MAX_NS>
 __device__ __forceinline__ void run_step(float2 (&acc)[R], const float2 (&xw)[R], float2 h0,
-                                         const float2 *hs, const float2 (&w)[R][MAX_NS - 1], int u)
+                                         const float2 *hs, const float2 (&w)[R][NSM - 1], int u)
 {
     // the mix h = h0 + w (h_j - h0) runs as packed pairs (one fma.rn.f32x2 per
     // slot: the same roundings as two fmaf, half the issue slots)

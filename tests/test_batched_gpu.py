@@ -88,7 +88,12 @@ def test_autotune_keeps_results():
     B.run()
     torch.cuda.synchronize()
     for i in range(len(S)):
-        assert torch.equal(B.output(i), before[i])
+        after = B.output(i)
+        if chosen[S[i].L][0] in (0, 1):          # same mixing order: identical
+            assert torch.equal(after, before[i])
+        else:                                    # four-filter groups may round differently
+            rel = float((after - before[i]).norm() / before[i].norm())
+            assert rel <= 1e-6, (i, rel)
 
 
 def test_full_batch_sampled():

@@ -236,6 +236,29 @@ def test_mac_staging_variants_agree_bitwise():
     _assert_close(y_tma, _ref(wl), "variants")
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 8])
+def test_mac_four_filter_groups(k):
+    """Staging option 2 stages up to four filters per group of 64 blocks: a
+    schedule cycling four filters every k blocks then runs without the
+    overflow path. Against the oracle, and against option 0 up to rounding."""
+    dev = _dev()
+    rng = np.random.default_rng(60 + k)
+    L, N, ir_len = 128, 40000, 6000
+    nb = W.blocks_for(N, L)
+    a = W.cyclic_schedule(nb, 4, k)[None, :].astype(np.int32)
+    a = np.concatenate([a, (a + 1) % 4 + 4])                 # output 1: filters 4..7
+    wl = W.Workload(f"cyclic4_k{k}", L, W.white(rng, (2, N)).astype(np.float32),
+                    (rng.standard_normal((8, ir_len)) / np.sqrt(ir_len)).astype(np.float32),
+                    a, a.copy(), np.zeros(a.shape, np.float32), np.arange(2, dtype=np.int32), N)
+    plan = _plan(wl, dev)
+    y0 = _run_signal(wl, dev, plan)
+    plan.set_option(1, 2)
+    y2 = _run_signal(wl, dev, plan)
+    _assert_close(y2, _ref(wl), f"four-filter groups k={k}")
+    rel = np.linalg.norm(y2 - y0) / np.linalg.norm(y0)
+    assert rel <= 1e-6, rel
+
+
 def test_deterministic_bitwise():
     dev = _dev()
     wl = W.random_case(13, L=128, ir_len=3000, N=20000, n_in=2, n_out=2, n_slots=3)
