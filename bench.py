@@ -121,6 +121,19 @@ def mac_terms(nb: int, M: int) -> int:
     return int(np.minimum(M, t // 2 + 1).sum())
 
 
+def job_rate(elapsed_ms: float, units_per_rank_step: float, ws: int, steps: int, device):
+    """Whole-job rate of a replicated run: the slowest rank's elapsed time (an
+    all-reduce MAX; every rank gets it) and the units all ranks processed per
+    second. With one rank no collective is called."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+    return elapsed_ms, units_per_rank_step * ws * steps / (elapsed_ms * 1e-3)
+
+
 # --------------------------------------------------------------------------- ours
 def run_ours(args):
     import torch
@@ -195,14 +208,8 @@ def run_ours(args):
     elapsed_ms = t0.elapsed_time(t1)
     stage_ms = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in evs])
     plan.check()
-    if ws > 1:
-        tt = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
-
-    units_per_step = wl.n_out * wl.out_len * ws
+    elapsed_ms, value = job_rate(elapsed_ms, wl.n_out * wl.out_len, ws, args.steps, dev)
     ms_per_step = elapsed_ms / args.steps
-    value = units_per_step / (ms_per_step * 1e-3)
 
     # dominant kernel: the Eq. 7 multiply-accumulate, FP32 ALU bound
     peaks, peak_kind = _peaks()
@@ -574,7 +581,7 @@ def run_batched(args):
 
 
 # --------------------------------------------------------------------------- serving
-def run_serve(args, lat_ticks=4000, thr_ticks=3000, timed_ticks=300, warm=200):
+def run_serve(args):
     """Streaming server: 1000 streams present at the start, Poisson arrivals
     at 50/s with lifetimes of 2..30 s, hop 64/128/256, binaural banks of 36
     pairs of 12000..144000 taps, a head-orientation walk choosing the pair of
@@ -588,7 +595,13 @@ def run_serve(args, lat_ticks=4000, thr_ticks=3000, timed_ticks=300, warm=200):
     from paper_2310_00319_gb300.server import OPT_TIMING, Server
     from synth import workloads as W
     dev = torch.device("cuda", 0)
-    fs, base, top, cap, n_pairs = 48000, 64, 256, 1024, 36
+    lat_ticks = args.serve_ticks
+    thr_ticks = max(10, args.serve_ticks * 3 // 4)
+    timed_ticks = max(10, args.serve_ticks // 13)
+    warm = max(args.warmup, 20)
+    n_streams = args.streams
+    fs, base, top, n_pairs = 48000, 64, 256, 36
+    cap = n_streams if n_streams < 1000 else 1000
     rng = np.random.default_rng(5)
     # response banks: K distinct banks (lengths uniform 12000..144000), each
     # stream takes one at random and transforms it into its own arena piece
@@ -597,14 +610,15 @@ def run_serve(args, lat_ticks=4000, thr_ticks=3000, timed_ticks=300, warm=200):
     banks = [torch.from_numpy(W.serving_bank(rng, int(n), n_pairs)).to(dev) for n in lens]
     hops = np.array([64, 128, 256])
     total_ticks = warm + lat_ticks + thr_ticks + timed_ticks
-    ev = W.serving_arrivals(seed=5, duration_s=total_ticks * base / fs, prefill=1000,
+    ev = W.serving_arrivals(seed=5, duration_s=total_ticks * base / fs, prefill=n_streams,
                             base_hop=base, fs=fs)
     n_ev = ev.shape[0]
     L_of = hops[rng.integers(0, 3, n_ev)]
     bank_of = rng.integers(0, K, n_ev)
     stream = torch.cuda.Stream(dev)
     free_b = torch.cuda.mem_get_info(dev)[0]
-    arena = int(min(0.6 * free_b, 140e9))
+    # a stream takes at most (36 pairs x 2 + 2) x 144000 taps x 8 B (about 85 MB)
+    arena = int(min(0.6 * free_b, 140e9, cap * 90e6))
     srv = Server(base, top, cap, max_out=2, arena_bytes=arena, device=dev, stream=stream)
     live = {}                 # stream id -> event index
     leave_at = {}
@@ -704,12 +718,12 @@ def run_serve(args, lat_ticks=4000, thr_ticks=3000, timed_ticks=300, warm=200):
     deadline = base / fs * 1e3
     h2h_ms = np.array(h2h) * 1e3
     gpu = np.array(gpu)
-    return {"metric": "channel-samples/s (streaming, 1000 binaural streams)",
+    return {"metric": f"channel-samples/s (streaming, {n_streams} binaural streams)",
             "value": round(samples / (thr_ms * 1e-3), 1), "unit": "channel-samples/s",
             "n_gpus": 1, "steps": thr_ticks, "warmup": warm,
             "ms_per_step": round(thr_ms / thr_ticks, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serving_1000_streams", "base_tick_samples": base,
+            "config": {"workload": f"serving_{n_streams}_streams", "base_tick_samples": base,
                        "hops": [64, 128, 256], "pairs_per_stream": n_pairs,
                        "ir_len": "uniform 12000..144000 (16 banks)", "capacity": cap,
                        "arena_gb": round(arena / 1e9, 1),
@@ -816,6 +830,10 @@ def main():
                     help="ncu dram bytes per launch of the multiply-accumulate kernel")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    ap.add_argument("--streams", type=int, default=1000,
+                    help="serve: streams present at the start (slots capped at 1000)")
+    ap.add_argument("--serve-ticks", type=int, default=4000,
+                    help="serve: ticks of the latency run (throughput run: 3/4 of it)")
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
