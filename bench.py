@@ -55,7 +55,7 @@ SMS, FP32_LANES = 152, 128
 # DRAM bytes (read + write) of one launch of the multiply-accumulate group kernel at the
 # default 64-channel workload: an ncu capture of the same kernel at 32 channels, scaled by
 # the channel count (the traffic grows in proportion to it).
-MAC_TRAFFIC_BYTES = 2 * (311.548160e6 + 215.897088e6)
+MAC_TRAFFIC_BYTES = 2 * (309.401088e6 + 212.599040e6)
 
 
 def fp32_peak_tflops(mhz: float) -> float:
@@ -517,10 +517,10 @@ def run_batched(args):
 
     # plain per-source form: one single-channel process_signal per source in a
     # loop, with the staging the autotuner chose for the source's hop (same
-    # kernels), and again with the default staging
+    # kernels), and again with the default staging (skipped by --skip-extras)
     stream = torch.cuda.current_stream(dev)
     per = []
-    for s in S:
+    for s in (S if not args.skip_extras else []):
         p = Plan(s.L, s.M, n_slots=s.irs.shape[0], device=dev)
         p.load_bank(0, torch.from_numpy(s.irs).to(dev))
         per.append((p, torch.from_numpy(s.x[None, :]).to(dev),
@@ -543,10 +543,13 @@ def run_batched(args):
         torch.cuda.synchronize(dev)
         return a.elapsed_time(b) / reps
 
-    default_ms = time_loop()
-    for p, *_, L in per:
-        p.set_option(1, tuned[L][0])
-    per_ms = time_loop()
+    if args.skip_extras:
+        default_ms = per_ms = None
+    else:
+        default_ms = time_loop()
+        for p, *_, L in per:
+            p.set_option(1, tuned[L][0])
+        per_ms = time_loop()
     for p, *_ in per:
         p.check()
         p.close()
@@ -567,11 +570,11 @@ def run_batched(args):
             "config": {"workload": "batched_uneven_512src", "sources": len(S),
                        "channel_samples": total, "hops": hops,
                        "l2": "inputs larger than L2 (about 1 GB of input, 10 GB of spectra)"},
-            "vs_per_source": {"per_source_ms_per_step": round(per_ms, 4),
-                              "batched_ms_per_step": round(ms, 4),
-                              "ratio": round(per_ms / ms, 3),
-                              "per_source_default_staging_ms": round(default_ms, 4),
-                              "note": "per-source loop with the staging chosen for its hop"},
+            "vs_per_source": None if per_ms is None else {
+                "per_source_ms_per_step": round(per_ms, 4), "batched_ms_per_step": round(ms, 4),
+                "ratio": round(per_ms / ms, 3),
+                "per_source_default_staging_ms": round(default_ms, 4),
+                "note": "per-source loop with the staging chosen for its hop"},
             "roofline": {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1),
                          "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
                          "kernel": "whole step: Eq. 7 flops / replay time (lower bound on "
