@@ -122,3 +122,35 @@ def test_full_batch_sampled():
     got, ref = np.concatenate(got), np.concatenate(ref)
     rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert rel <= 1e-5, rel
+
+
+def test_edge_sources():
+    """Degenerate sources in one batch: an empty signal, signals shorter than
+    one hop, one-tap responses (M = 1), the smallest and largest hops, and a
+    hop group with a single source. Non-empty sources match the oracle; the
+    empty one yields no samples and disturbs nothing."""
+    dev = _dev()
+    from paper_2310_00319_gb300.batch import BatchedTvolap
+    rng = np.random.default_rng(70)
+
+    def src(L, N, ir_len, n_ir=3, k=2):
+        irs = (rng.standard_normal((n_ir, ir_len)) / np.sqrt(ir_len)).astype(np.float32)
+        nb = W.blocks_for(N, L)
+        return W.Source(L, W.white(rng, N).astype(np.float32), irs,
+                        W.cyclic_schedule(max(nb, 1), n_ir, k).astype(np.int32)[:nb], N)
+
+    S = [src(16, 0, 50), src(16, 1, 50), src(16, 15, 1), src(16, 700, 1),
+         src(1024, 1000, 3000), src(1024, 5000, 1), src(64, 3000, 900),
+         src(16, 2000, 333)]
+    B = BatchedTvolap(S, device=dev)
+    B.run()
+    torch.cuda.synchronize()
+    for g in B.groups:
+        g.plan.check()
+    assert B.output(0).numel() == 0
+    for i, s in enumerate(S[1:], start=1):
+        y = B.output(i).cpu().numpy().astype(np.float64)
+        ref = oracle.tvolap_direct(s.x[None, :], s.irs, s.L, s.sched[None, :],
+                                   out_len=s.out_len)[0]
+        ok, err = _close(y, ref)
+        assert ok, (i, s.L, s.out_len, err)

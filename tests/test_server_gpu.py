@@ -230,3 +230,35 @@ def test_input_wait_times_out_and_server_recovers():
         out[:, b, :] = srv.out[i, :2, :s.L]
     np.testing.assert_array_equal(out, ref)
     srv.close()
+
+
+def test_edge_streams():
+    """Hop 1024 with base 128 (eight base ticks per block, 2048 bins), a single
+    filter of one tap (M = 1), a mono stream, and a server of capacity 1 that
+    retires a stream before it turns live and admits another."""
+    dev = _dev()
+    rng = np.random.default_rng(71)
+
+    def stream(L, ir_len, F, nb):
+        irs = np.stack([W.binaural_pair(rng, ir_len, 0.1) for _ in range(F)]).astype(np.float32)
+        return W.ServeStream(L, irs, W.white(rng, nb * L).astype(np.float32),
+                             W.head_walk(rng, nb, F))
+
+    S = [stream(1024, 5000, 3, 12), stream(128, 1, 1, 30), stream(256, 2000, 2, 20)]
+    srv = _server(dev, base=128, top=1024, cap=4, arena=512 << 20)
+    outs = drive(srv, S, [0, 2, 5], dev, n_outs=[2, 2, 1])
+    srv.close()
+    for i, s in enumerate(S):
+        n_out = [2, 2, 1][i]
+        ref = _oracle_stream(s, n_out)
+        y = outs[i].reshape(n_out, -1).astype(np.float64)
+        _assert_close(y[:, s.L:], ref, ("edge", i, s.L))
+    srv = _server(dev, cap=1)
+    t = W.serving_streams(72, 2)
+    i0 = srv.admit(t[0].L, _irs(t[0], 2, dev))
+    srv.retire(i0)                      # before it ever turned live
+    assert srv.state(i0)[0] == 0
+    out = drive(srv, [t[1]], [0], dev)[0]
+    ref = _oracle_stream(t[1], 2)
+    _assert_close(out.reshape(2, -1).astype(np.float64)[:, t[1].L:], ref, "after early retire")
+    srv.close()
