@@ -261,7 +261,8 @@ def run_ours(args):
         out["vs_per_source"] = run_per_source(args, wl, dev, stream, ms_per_step)
         out["stream"] = run_stream(args, wl, dev, stream)
     if rank == 0 and not args.skip_extras and not args.no_cpu:
-        out["cpu_baseline"] = cpu_baseline(args, wl, budget_s=args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(args, wl, budget_s=args.cpu_seconds,
+                                           y_channel0=y[0].cpu().numpy())
     plan.close()
     if ws > 1:
         dist.destroy_process_group()
@@ -373,8 +374,19 @@ def run_stream(args, wl, dev, stream, ticks=600, warm=50):
         p.process_block(blocks[t], out, sa[t], sb[t], sal[t])
         evs[i][1].record(stream)
     torch.cuda.synchronize(dev)
+    # constant load (Section 4): the same ticks with one selection kept for all
+    # blocks (no filter switch) cost the same as a new selection every block
+    fixed = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(ticks)]
+    for i in range(ticks):
+        t = warm + i
+        fixed[i][0].record(stream)
+        p.process_block(blocks[t], out, sa[warm], sb[warm], sal[warm])
+        fixed[i][1].record(stream)
+    torch.cuda.synchronize(dev)
     p.check()
     ms = np.array([a.elapsed_time(b) for a, b in evs])
+    ms_fixed = np.array([a.elapsed_time(b) for a, b in fixed])
     p.close()
     deadline_ms = L / 48000 * 1e3
     bpt = costmodel.stream_mac_bytes_per_tick(wl.n_out, 2 * L, wl.M, 2)
@@ -383,7 +395,9 @@ def run_stream(args, wl, dev, stream, ticks=600, warm=50):
             "deadline_ms": round(deadline_ms, 4),
             "channel_samples_per_s": round(wl.n_out * L / (ms.mean() * 1e-3), 1),
             "mac_bytes_per_tick": bpt,
-            "logical_gbs_per_tick": round(bpt / (ms.mean() * 1e-3) / 1e9, 1)}
+            "logical_gbs_per_tick": round(bpt / (ms.mean() * 1e-3) / 1e9, 1),
+            "constant_load": {"switching_every_block_ms_mean": round(float(ms.mean()), 5),
+                              "fixed_selection_ms_mean": round(float(ms_fixed.mean()), 5)}}
 
 
 # --------------------------------------------------------------------------- adjoint
@@ -498,7 +512,12 @@ def run_batched(args):
     S = W.batched_uneven()
     total = sum(s.out_len for s in S)
     B = BatchedTvolap(S, device=dev)
-    tuned = B.autotune(reps=2)
+    if args.staging is None:
+        tuned = B.autotune(reps=2)
+    else:                                  # fixed staging (profiling: the timing would differ)
+        for g in B.groups:
+            g.plan.set_option(1, args.staging)
+        tuned = {g.L: (args.staging, None) for g in B.groups}
     B.capture()
     for _ in range(args.warmup):
         B.replay()
@@ -554,6 +573,7 @@ def run_batched(args):
         p.check()
         p.close()
 
+    cpu = None if args.no_cpu else batched_oracle(S, B, budget_s=args.cpu_seconds)
     flops = 0.0
     for s in S:
         nb = n_blocks_for(s.out_len, s.L)
@@ -580,7 +600,44 @@ def run_batched(args):
                          "kernel": "whole step: Eq. 7 flops / replay time (lower bound on "
                                    "the multiply-accumulate kernels)"},
             "autotune": {str(L): v[0] for L, v in tuned.items()},
-            "gpu_launches": launches * args.steps, "clocks": clocks}
+            "gpu_launches": launches * args.steps, "clocks": clocks, "cpu_baseline": cpu}
+
+
+def batched_oracle(S, B, budget_s=15.0, n_src=32, seed=11):
+    """The FP64 oracle on a seeded subset of the batched sources: per source a
+    window of consecutive outputs from the middle of its signal, sized so the
+    subset takes about budget_s; also the GPU's accuracy on those samples."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    idx = sorted(int(i) for i in rng.choice(len(S), min(n_src, len(S)), replace=False))
+    probe = 64
+    cost = 0.0
+    for i in idx:
+        s = S[i]
+        t = time.perf_counter()
+        oracle.tvolap_samples(s.x, s.irs, s.L, s.sched[None, :], None, None,
+                              np.zeros(probe, np.int32),
+                              np.arange(s.out_len // 2, s.out_len // 2 + probe, dtype=np.int64))
+        cost += (time.perf_counter() - t) / probe
+    n = int(max(probe, budget_s / max(cost, 1e-9)))
+    got, ref, total, dt = [], [], 0, 0.0
+    for i in idx:
+        s = S[i]
+        a = s.out_len // 2
+        k = min(n, s.out_len - a)
+        ni = np.arange(a, a + k, dtype=np.int64)
+        t = time.perf_counter()
+        r = oracle.tvolap_samples(s.x, s.irs, s.L, s.sched[None, :], None, None,
+                                  np.zeros(k, np.int32), ni)
+        dt += time.perf_counter() - t
+        total += k
+        ref.append(r)
+        got.append(B.output(i)[a:a + k].cpu().numpy())
+    return {"value": round(total / dt, 1), "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "seconds": round(dt, 2),
+            "sample": f"{len(idx)} sources (seed {seed}), up to {n} consecutive outputs each "
+                      "from the middle of the signal",
+            "accuracy": accuracy(np.concatenate(got), np.concatenate(ref))}
 
 
 # --------------------------------------------------------------------------- serving
@@ -610,7 +667,8 @@ def run_serve(args):
     # stream takes one at random and transforms it into its own arena piece
     K = 16
     lens = rng.integers(12000, 144001, K)
-    banks = [torch.from_numpy(W.serving_bank(rng, int(n), n_pairs)).to(dev) for n in lens]
+    banks_np = [W.serving_bank(rng, int(n), n_pairs) for n in lens]
+    banks = [torch.from_numpy(b).to(dev) for b in banks_np]
     hops = np.array([64, 128, 256])
     total_ticks = warm + lat_ticks + thr_ticks + timed_ticks
     ev = W.serving_arrivals(seed=5, duration_s=total_ticks * base / fs, prefill=n_streams,
@@ -625,6 +683,7 @@ def run_serve(args):
     srv = Server(base, top, cap, max_out=2, arena_bytes=arena, device=dev, stream=stream)
     live = {}                 # stream id -> event index
     leave_at = {}
+    track, done_tracks = {}, []
     rejected = 0
     nxt = 0
 
@@ -645,6 +704,8 @@ def run_serve(args):
         for i in [i for i, t in leave_at.items() if t <= tick]:
             srv.retire(i)
             del live[i], leave_at[i]
+            if i in track:                       # the id may be reused: close the record
+                done_tracks.append(track.pop(i))
 
     pool = (0.1 * rng.standard_normal((4096, top))).astype(np.float32)
     steps = np.array([-1, 0, 1], np.int32)
@@ -653,14 +714,36 @@ def run_serve(args):
         srv.inp[ids] = pool[(ids * 7 + tick) % 4096]
         srv.sel[ids] = (srv.sel[ids] + steps[rng.integers(0, 3, ids.shape[0])]) % n_pairs
 
+    # record the first blocks of 16 streams present from the start, for the oracle
+    REC = 120
     tick = 0
     arrivals(0)
+    track.update({i: {"ev": e, "x": [], "sel": [], "y": []} for i, e in list(live.items())[:16]})
     srv.wait()
+
+    def record_in(ids):
+        for i in ids:
+            tr = track.get(int(i))
+            if tr is not None and len(tr["x"]) < REC:
+                L = int(L_of[tr["ev"]])
+                tr["x"].append(srv.inp[i, :L].copy())
+                tr["sel"].append(int(srv.sel[i]))
+
+    def record_out(ids):
+        for i in ids:
+            tr = track.get(int(i))
+            if tr is not None and len(tr["y"]) < len(tr["x"]):
+                L = int(L_of[tr["ev"]])
+                tr["y"].append(srv.out[i, :, :L].copy())
+
     for _ in range(warm):
         arrivals(tick)
         ids = srv.due()
         stage(ids, tick)
+        record_in(ids)
         srv.tick()
+        srv.wait()
+        record_out(ids)
         tick += 1
     srv.wait()
     # latency: one tick at a time
@@ -673,12 +756,14 @@ def run_serve(args):
             arrivals(tick)
             ids = srv.due()
             stage(ids, tick)
+            record_in(ids)
             t0 = time.perf_counter()
             e[k][0].record(stream)
             srv.tick()
             e[k][1].record(stream)
             srv.wait()
             h2h.append(time.perf_counter() - t0)
+            record_out(ids)
             tick += 1
         torch.cuda.synchronize(dev)
         gpu = [a.elapsed_time(b) for a, b in e]
@@ -712,6 +797,9 @@ def run_serve(args):
     srv.set_option(OPT_TIMING, 0)
     st = s4
     srv.close()
+    cpu = None
+    if not args.no_cpu:
+        cpu = serve_oracle(list(track.values()) + done_tracks, banks_np, bank_of, L_of)
     stage_ms = [s4["stage_ms"][i] - s3["stage_ms"][i] for i in range(3)]
     mac_bytes = s4["mac_bytes"] - s3["mac_bytes"]
     mac_gbs = mac_bytes / (stage_ms[1] * 1e-3) / 1e9
@@ -749,16 +837,50 @@ def run_serve(args):
                                    "mac": round(stage_ms[1] / timed_ticks, 4),
                                    "inverse": round(stage_ms[2] / timed_ticks, 4)},
             "gpu_launches": 7 * thr_ticks,
-            "peaks": kind, "clocks": clk.summary()}
+            "peaks": kind, "clocks": clk.summary(), "cpu_baseline": cpu}
+
+
+def serve_oracle(tracks, banks_np, bank_of, L_of):
+    """The FP64 oracle on the recorded first blocks of up to 16 streams: each
+    stream's output (delayed by L) recomputed from its inputs and pair indices;
+    also the server's accuracy on them."""
+    import oracle
+    got, ref, dt, n = [], [], 0.0, 0
+    for tr in tracks:
+        nb = len(tr["y"])
+        if nb < 8:
+            continue
+        L = int(L_of[tr["ev"]])
+        bank = banks_np[bank_of[tr["ev"]]]                   # [pairs, 2, ir_len]
+        F, _, ir_len = bank.shape
+        x = np.concatenate(tr["x"][:nb])
+        sel = np.array(tr["sel"][:nb], np.int32)
+        sched = np.stack([sel * 2, sel * 2 + 1]).astype(np.int32)
+        t = time.perf_counter()
+        r = oracle.tvolap_direct(x[None, :], bank.reshape(F * 2, ir_len), L, sched,
+                                 out_len=(nb - 1) * L, out_to_in=[0, 0])
+        dt += time.perf_counter() - t
+        y = np.concatenate(tr["y"][:nb], axis=1)[:, L:]      # delayed by L
+        got.append(y.ravel())
+        ref.append(r.ravel())
+        n += r.size
+    if not ref:
+        return None
+    return {"value": round(n / dt, 1), "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "seconds": round(dt, 2),
+            "sample": f"first blocks of {len(ref)} streams present from the start "
+                      "(both outputs, up to 120 blocks each)",
+            "accuracy": accuracy(np.concatenate(got), np.concatenate(ref))}
 
 
 # --------------------------------------------------------------------------- oracle
 _F64 = {}
 
 
-def _oracle_sample(wl, n_samples, channel=0, start=None):
+def _oracle_sample(wl, n_samples, channel=0, start=None, values=False):
     """Time the oracle on n_samples consecutive outputs of one channel (inputs
-    are converted to FP64 once, outside the timing)."""
+    are converted to FP64 once, outside the timing); with values, also return
+    the outputs."""
     import oracle
     if id(wl) not in _F64:
         _F64.clear()
@@ -770,23 +892,39 @@ def _oracle_sample(wl, n_samples, channel=0, start=None):
     n_idx = np.arange(start, start + n_samples, dtype=np.int64)
     oc = np.full(n_samples, channel, dtype=np.int32)
     t = time.perf_counter()
-    oracle.tvolap_samples(x64, irs64, wl.L, wl.sched_a, wl.sched_b, al64, oc, n_idx,
-                          out_to_in=wl.out_to_in)
-    return time.perf_counter() - t
+    y = oracle.tvolap_samples(x64, irs64, wl.L, wl.sched_a, wl.sched_b, al64, oc, n_idx,
+                              out_to_in=wl.out_to_in)
+    dt = time.perf_counter() - t
+    return (dt, y) if values else dt
 
 
-def cpu_baseline(args, wl, budget_s=15.0):
+def accuracy(y, ref):
+    """FP32 result against the FP64 oracle on the same samples."""
+    y = np.asarray(y, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    peak = float(np.max(np.abs(ref))) or 1.0
+    return {"rel_l2": float(np.linalg.norm(y - ref) / (np.linalg.norm(ref) or 1.0)),
+            "max_abs_over_peak": float(np.max(np.abs(y - ref)) / peak), "samples": int(y.size),
+            "tolerance": "rel-L2 <= 1e-5 and max-abs <= 1e-4 x peak"}
+
+
+def cpu_baseline(args, wl, budget_s=15.0, y_channel0=None):
     """The FP64 oracle on the host cores: a contiguous run of output samples of
-    one channel in the steady state, sized to about budget_s seconds."""
+    one channel in the steady state, sized to about budget_s seconds. With the
+    GPU's output of that channel, also its accuracy on those samples."""
     import oracle
     probe = 256
     dt = _oracle_sample(wl, probe)
     n = int(max(probe, min(wl.out_len // 2, probe * budget_s / max(dt, 1e-6))))
-    dt = _oracle_sample(wl, n)
-    return {"value": round(n / dt, 1), "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle", "seconds": round(dt, 2),
-            "sample": f"{n} consecutive output samples of channel 0 from n={wl.out_len // 2} "
-                      f"(FP64 time-domain oracle, {2 * wl.ir_len} flop-pairs per sample)"}
+    start = wl.out_len // 2
+    dt, ref = _oracle_sample(wl, n, start=start, values=True)
+    out = {"value": round(n / dt, 1), "unit": UNIT, "cores": oracle.num_threads(),
+           "kind": "oracle", "seconds": round(dt, 2),
+           "sample": f"{n} consecutive output samples of channel 0 from n={start} "
+                     f"(FP64 time-domain oracle, {2 * wl.ir_len} flop-pairs per sample)"}
+    if y_channel0 is not None:
+        out["accuracy"] = accuracy(y_channel0[start:start + n], ref)
+    return out
 
 
 def run_reference(args):
@@ -835,8 +973,10 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
     ap.add_argument("--streams", type=int, default=1000,
                     help="serve: streams present at the start (slots capped at 1000)")
-    ap.add_argument("--serve-ticks", type=int, default=4000,
+    ap.add_argument("--serve-ticks", type=int, default=10000,
                     help="serve: ticks of the latency run (throughput run: 3/4 of it)")
+    ap.add_argument("--staging", type=int, default=None, choices=[0, 1, 2],
+                    help="batched: fixed multiply-accumulate staging instead of the autotuner")
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
