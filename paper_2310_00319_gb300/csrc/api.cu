@@ -173,7 +173,7 @@ int tvolap_create(tvolap_t *out, int L, int partitions, int fft_len, int n_in, i
 
     const size_t P = h->P, M = h->M;
     cudaError_t e;
-    if ((e = dalloc(&h->tw, P)) || (e = dalloc(&h->rot, P)) || (e = dalloc(&h->post, P / 2)) ||
+    if ((e = dalloc(&h->tw, 2 * P)) || (e = dalloc(&h->rot, P)) || (e = dalloc(&h->post, P / 2)) ||
         (e = dalloc(&h->win, 2 * (size_t)L)) ||
         (e = dalloc(&h->bank, (size_t)(h->n_slots_total + 1) * M * P)) ||
         (e = dalloc(&h->out_to_in, (size_t)n_out)) || (e = dalloc(&h->sel_a, (size_t)n_out)) ||

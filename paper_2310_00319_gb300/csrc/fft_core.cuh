@@ -96,24 +96,39 @@ __device__ __forceinline__ void dftR(float2 *v)
     }
 }
 
+// Stages of a P-point transform: Ns = 1, 8, 64, ... with radix 8 while three
+// or more bits remain, then one radix-4 or radix-2 stage.
+__host__ __device__ constexpr int stage_radix(int P, int Ns) { return P / Ns >= 8 ? 8 : P / Ns; }
+
+// Twiddles are stored stage after stage (stages with Ns > 1), each as rows
+// r = 1 .. R-1 of its Ns values: entry tw_offset(P, Ns) + (r - 1) Ns + k holds
+// e^{-2 pi i r k / (Ns R)}, so the lanes of a warp (consecutive k) read
+// consecutive entries.
+__host__ __device__ constexpr int tw_offset(int P, int Ns)
+{
+    int off = 0;
+    for (int n = stage_radix(P, 1); n < Ns; n *= stage_radix(P, n)) off += (stage_radix(P, n) - 1) * n;
+    return off;
+}
+__host__ __device__ constexpr int tw_size(int P) { return tw_offset(P, P); }
+
 // One Stockham stage of radix R on a P-point transform: butterfly j reads
 // src[j + r P/R], rotates input r by the twiddle r * (j mod Ns) / (Ns R) of a
 // turn, transforms, and writes dst[(j / Ns) Ns R + (j mod Ns) + s Ns].
-// tw[i] = e^{-2 pi i i / P}.
 template <int P, int Ns, int R, bool INV>
 __device__ __forceinline__ void stockham_stage(const float2 *__restrict__ src, float2 *__restrict__ dst,
                                                int j, const float2 *__restrict__ tw)
 {
     constexpr int stride = P / R;
-    constexpr int step = P / (Ns * R);
     const int k = j & (Ns - 1);
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[j + r * stride];
     if constexpr (Ns > 1) {
+        const float2 *tws = tw + tw_offset(P, Ns) + k;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-            float2 w = __ldg(tw + r * k * step);
+            float2 w = __ldg(tws + (r - 1) * Ns);
             v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
         }
     }

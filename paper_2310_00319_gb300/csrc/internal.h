@@ -17,7 +17,7 @@ struct tvolap_plan {
     cudaStream_t stream;
 
     // transform tables (FP32, generated in FP64 on the device)
-    float2 *tw;                   // [P]   e^{-2 pi i n / P}
+    float2 *tw;                   // [2P]  FFT twiddles, stage by stage (tw_offset in fft_core.cuh)
     float2 *rot;                  // [P]   e^{-i pi r / P}
     float2 *post;                 // [P/2] e^{-i pi (2k+1) / 2P}
     float *win;                   // [2L]  (1 - cos(pi n / L)) / 2

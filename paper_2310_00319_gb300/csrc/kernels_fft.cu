@@ -17,10 +17,21 @@ namespace {
 __global__ void k_tables(float2 *tw, float2 *rot, float2 *post, float *win, int L)
 {
     const int P = 2 * L;
+    const int n_tw = tw_size(P);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_tw; i += gridDim.x * blockDim.x) {
+        // stage-major twiddle rows (see tw_offset): find the stage of entry i
+        int q = i, Ns = stage_radix(P, 1);
+        while (q >= (stage_radix(P, Ns) - 1) * Ns) {
+            q -= (stage_radix(P, Ns) - 1) * Ns;
+            Ns *= stage_radix(P, Ns);
+        }
+        const int r = q / Ns + 1, k = q % Ns, R = stage_radix(P, Ns);
+        double s, c;
+        sincospi(2.0 * (double)(r * k) / (double)(Ns * R), &s, &c);   // e^{-2 pi i r k / (Ns R)}
+        tw[i] = make_float2((float)c, (float)-s);
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
         double s, c;
-        sincospi(2.0 * (double)i / (double)P, &s, &c);      // e^{-2 pi i n / P}
-        tw[i] = make_float2((float)c, (float)-s);
         sincospi((double)i / (double)P, &s, &c);            // e^{-i pi r / P}
         rot[i] = make_float2((float)c, (float)-s);
         if (i < P / 2) {

@@ -292,14 +292,14 @@ int tvolap_server_create(tvolap_server_t *out, int base_hop, int max_hop, int ca
         t.lgP = lg2(2 * L);
     }
     size_t tab_floats = 0;
-    for (int c = 0; c < s->n_cls; ++c) tab_floats += (size_t)2 * s->cls[c].L * 7;
+    for (int c = 0; c < s->n_cls; ++c) tab_floats += (size_t)2 * s->cls[c].L * 8;   // 8P floats
     if (cudaMalloc(&s->tables, tab_floats * sizeof(float)) != cudaSuccess) return fail(TVOLAP_ERR_OOM);
     float *p = s->tables;
     for (int c = 0; c < s->n_cls; ++c) {
         SrvClassTables &t = s->cls[c];
         const int P = 2 * t.L;
-        float2 *tw = reinterpret_cast<float2 *>(p);
-        float2 *rot = tw + P;
+        float2 *tw = reinterpret_cast<float2 *>(p);          // 2P twiddles (stage-major)
+        float2 *rot = tw + 2 * P;
         float2 *post = rot + P;
         float *win = reinterpret_cast<float *>(post + P / 2);
         p = win + P;
