@@ -31,18 +31,18 @@ __device__ __forceinline__ void forward_block(float2 *A, float2 *B, int j, bool 
                                               const float2 *__restrict__ tw, Store st)
 {
     constexpr int T = P / 8;
+    float2 z[8];
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
         const int r = j + s * T;
-        float2 z = make_float2(0.f, 0.f);
+        z[s] = make_float2(0.f, 0.f);
         // r < P/2 = L unless FULL: the upper half is the zero padding of Eqs. 3-4
         if ((FULL || s < 4) && active) {
-            z = cmul(src(2 * r), __ldg(rot + r));
+            z[s] = cmul(src(2 * r), __ldg(rot + r));
         }
-        A[r] = z;
     }
-    __syncthreads();
-    float2 *Z = fft_complex<P, false>(A, B, j, tw);
+    // the first stage reads exactly inputs j + s T: it runs on the registers
+    float2 *Z = fft_complex_regs<P, false>(z, A, B, j, tw);
     split_forward<P>(Z, j, post, st);
 }
 
@@ -59,14 +59,12 @@ __device__ __forceinline__ void inverse_stream_block(float2 *A, float2 *B, int j
     constexpr int T = P / 8, L = P / 2;
     merge_inverse<P>(A, j, post, [&](int k) { return active ? ld(k) : make_float2(0.f, 0.f); });
     __syncthreads();
-    float2 *Z = fft_complex<P, true>(A, B, j, tw);
+    // undo the pre-rotation and scale as the last stage stores:
+    // y(2r) + i y(2r+1) = Z(r) e^{+i pi r/P} / P
     const float inv_p = 1.0f / (float)P;
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        const int r = j + s * T;
-        Z[r] = cscale(cmulc(Z[r], __ldg(rot + r)), inv_p);
-    }
-    __syncthreads();
+    float2 *Z = fft_complex<P, true>(A, B, j, tw, [&](int r, float2 v) {
+        return cscale(cmulc(v, __ldg(rot + r)), inv_p);
+    });
     const float *yb = reinterpret_cast<const float *>(Z);
     // read every pending sum this thread rewrites before any thread writes;
     // T = L/4 threads cover the 3L pending sums in exactly 12 steps

@@ -115,9 +115,14 @@ __host__ __device__ constexpr int tw_size(int P) { return tw_offset(P, P); }
 // One Stockham stage of radix R on a P-point transform: butterfly j reads
 // src[j + r P/R], rotates input r by the twiddle r * (j mod Ns) / (Ns R) of a
 // turn, transforms, and writes dst[(j / Ns) Ns R + (j mod Ns) + s Ns].
-template <int P, int Ns, int R, bool INV>
+// Output transform of the last stage: epi(n, v) is stored at natural index n.
+struct NoEpi {
+    __device__ __forceinline__ float2 operator()(int, float2 v) const { return v; }
+};
+
+template <int P, int Ns, int R, bool INV, class Epi = NoEpi>
 __device__ __forceinline__ void stockham_stage(const float2 *__restrict__ src, float2 *__restrict__ dst,
-                                               int j, const float2 *__restrict__ tw)
+                                               int j, const float2 *__restrict__ tw, Epi epi = Epi())
 {
     constexpr int stride = P / R;
     const int k = j & (Ns - 1);
@@ -135,31 +140,36 @@ __device__ __forceinline__ void stockham_stage(const float2 *__restrict__ src, f
     dftR<R, INV>(v);
     const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
-    for (int s = 0; s < R; ++s) dst[base + s * Ns] = v[s];
+    for (int s = 0; s < R; ++s) dst[base + s * Ns] = epi(base + s * Ns, v[s]);
 }
 
 // Stages for P = 2^LG: radix 8 while three or more bits remain, then one
 // radix-4 or radix-2 stage. Thread j of T = P/8 runs one butterfly per
-// radix-8 stage, two per radix-4 stage, four per radix-2 stage.
-template <int P, int Ns, bool INV>
-__device__ __forceinline__ float2 *fft_stages(float2 *a, float2 *b, int j, const float2 *__restrict__ tw)
+// radix-8 stage, two per radix-4 stage, four per radix-2 stage. epi is applied
+// to the values of the last stage as they are stored.
+template <int P, int Ns, bool INV, class Epi = NoEpi>
+__device__ __forceinline__ float2 *fft_stages(float2 *a, float2 *b, int j, const float2 *__restrict__ tw,
+                                              Epi epi = Epi())
 {
     constexpr int T = P / 8;
     if constexpr (Ns == P) {
         return a;
     } else if constexpr (P / Ns >= 8) {
-        stockham_stage<P, Ns, 8, INV>(a, b, j, tw);
+        if constexpr (P / Ns == 8)
+            stockham_stage<P, Ns, 8, INV>(a, b, j, tw, epi);
+        else
+            stockham_stage<P, Ns, 8, INV>(a, b, j, tw);
         __syncthreads();
-        return fft_stages<P, Ns * 8, INV>(b, a, j, tw);
+        return fft_stages<P, Ns * 8, INV>(b, a, j, tw, epi);
     } else if constexpr (P / Ns == 4) {
-        stockham_stage<P, Ns, 4, INV>(a, b, j, tw);
-        stockham_stage<P, Ns, 4, INV>(a, b, j + T, tw);
+        stockham_stage<P, Ns, 4, INV>(a, b, j, tw, epi);
+        stockham_stage<P, Ns, 4, INV>(a, b, j + T, tw, epi);
         __syncthreads();
         return b;
     } else {
         static_assert(P / Ns == 2, "radix plan");
 #pragma unroll
-        for (int u = 0; u < 4; ++u) stockham_stage<P, Ns, 2, INV>(a, b, j + u * T, tw);
+        for (int u = 0; u < 4; ++u) stockham_stage<P, Ns, 2, INV>(a, b, j + u * T, tw, epi);
         __syncthreads();
         return b;
     }
@@ -167,10 +177,25 @@ __device__ __forceinline__ float2 *fft_stages(float2 *a, float2 *b, int j, const
 
 // Complex P-point FFT of a[0..P) (natural order), result returned (a or b).
 // Caller must __syncthreads() after filling a.
-template <int P, bool INV>
-__device__ __forceinline__ float2 *fft_complex(float2 *a, float2 *b, int j, const float2 *__restrict__ tw)
+template <int P, bool INV, class Epi = NoEpi>
+__device__ __forceinline__ float2 *fft_complex(float2 *a, float2 *b, int j, const float2 *__restrict__ tw,
+                                               Epi epi = Epi())
 {
-    return fft_stages<P, 1, INV>(a, b, j, tw);
+    return fft_stages<P, 1, INV>(a, b, j, tw, epi);
+}
+
+// The same FFT when thread j already holds inputs j + s T (s < 8) in z: the
+// first radix-8 stage (no twiddles) runs on the registers and stores into b.
+template <int P, bool INV, class Epi = NoEpi>
+__device__ __forceinline__ float2 *fft_complex_regs(float2 (&z)[8], float2 *a, float2 *b, int j,
+                                                    const float2 *__restrict__ tw, Epi epi = Epi())
+{
+    static_assert(P >= 16, "a radix-8 first stage and at least one stage after it");
+    dftR<8, INV>(z);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) b[j * 8 + s] = z[s];   // stage Ns = 1: dst (j * 8 + s)
+    __syncthreads();
+    return fft_stages<P, 8, INV>(b, a, j, tw, epi);
 }
 
 // Split step after the forward FFT: thread j handles pairs k = j + s T.

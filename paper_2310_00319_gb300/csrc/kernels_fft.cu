@@ -183,14 +183,11 @@ k_inverse_ola(const float2 *__restrict__ Y, int n_blocks, int L, int seg, float 
             return active ? Yt[k] : make_float2(0.f, 0.f);
         });
         __syncthreads();
-        float2 *Z = fft_complex<P, true>(A, B, j, tw);
-        // undo the pre-rotation and scale: y(2r) + i y(2r+1) = Z(r) e^{+i pi r/P} / P
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const int r = j + s * T;
-            Z[r] = cscale(cmulc(Z[r], __ldg(rot + r)), inv_p);
-        }
-        __syncthreads();
+        // undo the pre-rotation and scale as the last stage stores:
+        // y(2r) + i y(2r+1) = Z(r) e^{+i pi r/P} / P
+        float2 *Z = fft_complex<P, true>(A, B, j, tw, [&](int r, float2 v) {
+            return cscale(cmulc(v, __ldg(rot + r)), inv_p);
+        });
         // overlap-add: the round's blocks cover samples [(tb-1)L, (tb+F-1)L + 4L)
         const float2 *Zbase = Z - f * P;               // all transforms end in the same half
         const int64_t w0 = (tb - 1) * L;               // first sample of block tb
@@ -255,13 +252,9 @@ k_adjoint_input(const float2 *__restrict__ dX, int q_count, int64_t q_first, int
             return active ? Xq[k] : make_float2(0.f, 0.f);
         });
         __syncthreads();
-        float2 *Z = fft_complex<P, true>(A, B, j, tw);
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const int r = j + s * T;
-            Z[r] = cmulc(Z[r], __ldg(rot + r));
-        }
-        __syncthreads();
+        float2 *Z = fft_complex<P, true>(A, B, j, tw, [&](int r, float2 v) {
+            return cmulc(v, __ldg(rot + r));
+        });
         const float2 *Zbase = Z - f * P;
         const int64_t w0 = (qb - 1) * L;                 // first sample of block qb
         const int span = (F + 1) * L;
