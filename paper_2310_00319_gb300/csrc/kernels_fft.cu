@@ -143,8 +143,12 @@ k_adjoint_output(const float *__restrict__ g, int64_t g_len, int64_t g_stride, i
 }
 
 // Offline inverse + overlap-add. CTA (segment, output channel) owns output
-// samples [s0, s0 + seg*L) and transforms every block that reaches them
-// (l = s0/L - 3 .. s0/L + seg - 1), F at a time; each output sample sums its
+// samples [s0, s0 + seg*L) and transforms the blocks that reach them
+// (t = s0/L - 2 .. s0/L + seg), F at a time. The blocks of a round cover the
+// window [(tb-1)L, (tb+F+2)L): its first 3L samples start from the pending
+// sums of the earlier blocks (the carry), each block adds its 4L samples in
+// increasing block order, the first F*L samples are then final and go to y,
+// and the last 3L become the next carry. Every output sample thus sums its
 // contributions in increasing block order, so the result does not depend on
 // the tiling.
 template <int LG>
@@ -153,28 +157,31 @@ k_inverse_ola(const float2 *__restrict__ Y, int n_blocks, int L, int seg, float 
               int64_t out_len, int64_t y_stride, const float2 *__restrict__ rot,
               const float2 *__restrict__ post, const float2 *__restrict__ tw, Ragged rg)
 {
-    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F;
+    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F, LC = P / 2;
     extern __shared__ float2 sm[];
-    float *acc = reinterpret_cast<float *>(sm + 2 * F * P);
+    float *carry = reinterpret_cast<float *>(sm + 2 * F * P);    // two buffers of 3L
     const int f = threadIdx.x / T, j = threadIdx.x % T;
     float2 *A = sm + f * P, *B = sm + (F + f) * P;
     const int o = blockIdx.y;
     const int64_t tile0 = (int64_t)blockIdx.x * seg;    // first output hop of the segment
-    const int64_t s0 = tile0 * L;
-    const int nseg = seg * L;
+    const int64_t s0 = tile0 * LC;
+    const int64_t s_end = s0 + (int64_t)seg * LC;
     const float2 *Yo = Y + (int64_t)o * n_blocks * P;
     int64_t nb_o = n_blocks;
     if (rg.out_len) {                                  // ragged: this output's length
         const int64_t oc = rg.out_len[o];
         if (oc < out_len) out_len = oc < 0 ? 0 : oc;
         if (s0 >= out_len) return;                     // whole CTA, before any barrier
-        nb_o = blocks_of(out_len, L);
+        nb_o = blocks_of(out_len, LC);
     }
-    for (int i = threadIdx.x; i < nseg; i += blockDim.x) acc[i] = 0.f;
+    const int64_t w_end = s_end < out_len ? s_end : out_len;   // samples this CTA writes
+    for (int i = threadIdx.x; i < 3 * LC; i += blockDim.x) carry[i] = 0.f;
     const int64_t t_lo = tile0 - 2 > 0 ? tile0 - 2 : 0;
     int64_t t_hi = tile0 + seg;
     if (t_hi > nb_o - 1) t_hi = nb_o - 1;
     const float inv_p = 1.0f / (float)P;
+    float *yo = y + (int64_t)o * y_stride;
+    int cb = 0;
     for (int64_t tb = t_lo; tb <= t_hi; tb += F) {
         const int64_t t = tb + f;
         const bool active = t <= t_hi;
@@ -188,29 +195,30 @@ k_inverse_ola(const float2 *__restrict__ Y, int n_blocks, int L, int seg, float 
         float2 *Z = fft_complex<P, true>(A, B, j, tw, [&](int r, float2 v) {
             return cscale(cmulc(v, __ldg(rot + r)), inv_p);
         });
-        // overlap-add: the round's blocks cover samples [(tb-1)L, (tb+F-1)L + 4L)
         const float2 *Zbase = Z - f * P;               // all transforms end in the same half
-        const int64_t w0 = (tb - 1) * L;               // first sample of block tb
-        const int span = (F + 3) * L;
+        const int nr = (int)(t_hi - tb + 1 < F ? t_hi - tb + 1 : F);   // blocks in this round
+        const int fin = nr * LC;                       // samples final after this round
+        const int span = fin + 3 * LC;
+        const float *cin = carry + cb * 3 * LC;
+        float *cout = carry + (1 - cb) * 3 * LC;
+        const int64_t w0 = (tb - 1) * LC;              // first sample of block tb
         for (int p = threadIdx.x; p < span; p += blockDim.x) {
-            const int64_t n = w0 + p;                  // absolute sample
-            const int64_t a = n - s0;                  // index in acc
-            if (a < 0 || a >= nseg) continue;
-            float v = acc[a];
+            float v = p < 3 * LC ? cin[p] : 0.f;
 #pragma unroll 4
             for (int ff = 0; ff < F; ++ff) {
-                if (tb + ff > t_hi) break;
-                const int i = p - ff * L;              // position within block tb+ff
-                if (i >= 0 && i < 4 * L) v += reinterpret_cast<const float *>(Zbase + ff * P)[i];
+                if (ff >= nr) break;
+                const int i = p - ff * LC;             // position within block tb+ff
+                if (i >= 0 && i < 4 * LC) v += reinterpret_cast<const float *>(Zbase + ff * P)[i];
             }
-            acc[a] = v;
+            if (p < fin) {
+                const int64_t n = w0 + p;
+                if (n >= s0 && n < w_end) yo[n] = v;
+            } else {
+                cout[p - fin] = v;
+            }
         }
+        cb ^= 1;
         __syncthreads();
-    }
-    float *yo = y + (int64_t)o * y_stride;
-    for (int i = threadIdx.x; i < nseg; i += blockDim.x) {
-        const int64_t n = s0 + i;
-        if (n < out_len) yo[n] = acc[i];
     }
 }
 
@@ -327,7 +335,10 @@ k_inverse_stream(const float2 *__restrict__ Ys, float *__restrict__ ola, float *
     inverse_stream_block<P>(A, B, j, active, [&](int k) { return Yo[k]; }, st, ou, rot, post, tw);
 }
 
-// Segment length (output hops per CTA) of the offline inverse.
+// Output hops per CTA of the offline inverse (its blocks: seg + 3 = 32).
+constexpr int OLA_SEG = 29;
+
+// Segment length (output hops per CTA) of the input adjoint.
 int inverse_seg(int L)
 {
     int seg = 12288 / L - 3;            // about 48 KB of accumulator
@@ -415,11 +426,11 @@ cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, fl
                                int64_t out_len, int64_t y_stride, Ragged rg)
 {
     if (out_len <= 0) return cudaSuccess;
-    const int seg = inverse_seg(h->L);
+    const int seg = OLA_SEG;
     const int64_t n_seg = (out_len + (int64_t)seg * h->L - 1) / ((int64_t)seg * h->L);
     TVOLAP_DISPATCH(h->lgP, {
         constexpr int P = 1 << LG;
-        const size_t sm = smem_fft<LG>() + (size_t)seg * h->L * sizeof(float);
+        const size_t sm = smem_fft<LG>() + (size_t)6 * h->L * sizeof(float);
         cudaError_t e = set_smem(k_inverse_ola<LG>, sm);
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)n_seg, (unsigned)h->n_out);
