@@ -24,8 +24,9 @@ struct tvolap_server {
     SrvClassTables cls[SRV_MAX_CLASSES] = {};
     float *tables = nullptr;                 // all classes' tables, one allocation
     SrvDesc *desc_d = nullptr, *desc_h = nullptr;
-    float2 *Ys = nullptr;
-    int Pmax = 0, gmax = 1;
+    float2 *part = nullptr;                  // partial sums [part_slots][max_out][64]
+    int64_t part_slots = 0;
+    int Pmax = 0, gmax = 1, max_chunks = SRV_MAX_CHUNKS;
     char *ctl_h[2] = {nullptr, nullptr};     // mapped pinned: head, due[capacity], items
     size_t ctl_bytes = 0;
     unsigned *counter = nullptr;             // device
@@ -94,7 +95,7 @@ void release(tvolap_server *s)
     cudaFree(s->arena);
     cudaFree(s->tables);
     cudaFree(s->desc_d);
-    cudaFree(s->Ys);
+    cudaFree(s->part);
     cudaFree(s->counter);
     cudaFree(s->skip);
     cudaFreeHost(s->desc_h);
@@ -195,18 +196,14 @@ cudaError_t enqueue(tvolap_server *s, int b, bool with_events)
     e = cudaMemsetAsync(s->counter, 0, sizeof(unsigned), s->stream);
     if (e != cudaSuccess) return e;
     if (with_events) cudaEventRecord(s->tev[b][0], s->stream);
-    for (int c = 0; c < s->n_cls; ++c) {
-        e = srv_launch_forward(a, c, s->cls[c], s->stream);
-        if (e != cudaSuccess) return e;
-    }
+    e = srv_launch_forward(a, s->stream);
+    if (e != cudaSuccess) return e;
     if (with_events) cudaEventRecord(s->tev[b][1], s->stream);
     e = srv_launch_mac(a, s->stream);
     if (e != cudaSuccess) return e;
     if (with_events) cudaEventRecord(s->tev[b][2], s->stream);
-    for (int c = 0; c < s->n_cls; ++c) {
-        e = srv_launch_inverse(a, c, s->cls[c], s->stream);
-        if (e != cudaSuccess) return e;
-    }
+    e = srv_launch_inverse(a, s->stream);
+    if (e != cudaSuccess) return e;
     if (with_events) cudaEventRecord(s->tev[b][3], s->stream);
     return cudaSuccess;
 }
@@ -309,23 +306,29 @@ int tvolap_server_create(tvolap_server_t *out, int base_hop, int max_hop, int ca
         t.win = win;
         if (launch_tables_raw(tw, rot, post, win, t.L, s->stream) != cudaSuccess)
             return fail(TVOLAP_ERR_CUDA);
-        if (srv_prepare_kernels(t.lgP) != cudaSuccess) return fail(TVOLAP_ERR_CUDA);
         t.fwd_grid = srv_grid_transforms(t.lgP, capacity, s->n_sm);
         t.inv_grid = srv_grid_transforms(t.lgP, (int64_t)capacity * max_out, s->n_sm);
     }
     s->Pmax = 2 * max_hop;
     s->gmax = std::max(1, s->Pmax / SRV_GROUP_BINS);
+    // partial-sum slots: every due stream at most gmax groups x max_chunks chunks
+    // (fewer chunks when that would take more than 1 GiB)
+    const int64_t slot_bytes = (int64_t)max_out * SRV_GROUP_BINS * sizeof(float2);
+    while (s->max_chunks > 1 &&
+           (int64_t)capacity * s->gmax * s->max_chunks * slot_bytes > ((int64_t)1 << 30))
+        s->max_chunks /= 2;
+    s->part_slots = (int64_t)capacity * s->gmax * s->max_chunks;
     const int64_t arena = s->sch.arena_bytes;
     if (arena > 0 && cudaMalloc(&s->arena, arena) != cudaSuccess) return fail(TVOLAP_ERR_OOM);
     if (cudaMalloc(&s->desc_d, (size_t)capacity * sizeof(SrvDesc)) != cudaSuccess ||
-        cudaMalloc(&s->Ys, (size_t)capacity * max_out * s->Pmax * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&s->part, (size_t)(s->part_slots * slot_bytes)) != cudaSuccess ||
         cudaMalloc(&s->counter, 64) != cudaSuccess || cudaMalloc(&s->skip, 64) != cudaSuccess)
         return fail(TVOLAP_ERR_OOM);
     if (cudaMemsetAsync(s->desc_d, 0, (size_t)capacity * sizeof(SrvDesc), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->skip, 0, 64, s->stream) != cudaSuccess)
         return fail(TVOLAP_ERR_CUDA);
     const unsigned mapped = cudaHostAllocMapped | cudaHostAllocPortable;
-    s->ctl_bytes = item_offset(s) + (size_t)capacity * s->gmax * sizeof(SrvItem);
+    s->ctl_bytes = item_offset(s) + (size_t)s->part_slots * sizeof(SrvItem);
     const size_t io = (size_t)2 * capacity * max_hop * sizeof(float);    // two staging sets
     if (cudaHostAlloc((void **)&s->desc_h, (size_t)capacity * sizeof(SrvDesc), cudaHostAllocPortable) != cudaSuccess ||
         cudaHostAlloc((void **)&s->status, sizeof(SrvStatus), mapped) != cudaSuccess ||
@@ -356,8 +359,7 @@ int tvolap_server_create(tvolap_server_t *out, int base_hop, int max_hop, int ca
         a.due = reinterpret_cast<const SrvDue *>(cd + due_offset());
         a.items = reinterpret_cast<const SrvItem *>(cd + item_offset(s));
         a.desc = s->desc_d;
-        a.Ys = s->Ys;
-        a.Pmax = s->Pmax;
+        a.part = s->part;
         a.max_out = max_out;
         a.capacity = capacity;
         a.in = in_d + (size_t)b * capacity * max_hop;
@@ -366,6 +368,13 @@ int tvolap_server_create(tvolap_server_t *out, int base_hop, int max_hop, int ca
         a.counter = s->counter;
         a.skip = s->skip;
         a.mac_grid = s->n_sm * occ;
+        a.n_cls = s->n_cls;
+        a.fwd_start[0] = a.inv_start[0] = 0;
+        for (int c = 0; c < s->n_cls; ++c) {
+            a.cls[c] = s->cls[c];
+            a.fwd_start[c + 1] = a.fwd_start[c] + s->cls[c].fwd_grid;
+            a.inv_start[c + 1] = a.inv_start[c] + s->cls[c].inv_grid;
+        }
         s->head_d[b] = a.head;
         if (cudaEventCreateWithFlags(&s->tick_ev[b], cudaEventDisableTiming) != cudaSuccess)
             return fail(TVOLAP_ERR_CUDA);
@@ -522,14 +531,15 @@ int tvolap_server_tick(tvolap_server_t s)
         const int f = s->sel_h[id];
         if (f < 0 || f >= s->sch.st[id].n_filters) return TVOLAP_ERR_ARG;
     }
-    // due entries grouped by hop class; items ordered by depth, deepest first
+    // due entries grouped by hop class; each stream's partitions cut into at
+    // most max_chunks chunks of >= SRV_MIN_CHUNK partitions
     char *ctl = s->ctl_h[b];
     SrvHead *head = reinterpret_cast<SrvHead *>(ctl);
     SrvDue *due = reinterpret_cast<SrvDue *>(ctl + due_offset());
     SrvItem *items = reinterpret_cast<SrvItem *>(ctl + item_offset(s));
     std::memset(head, 0, sizeof(SrvHead));
     int n = 0;
-    int64_t mac_bytes = 0, samples = 0;
+    int64_t mac_bytes = 0, samples = 0, slots = 0;
     for (int c = 0; c < s->n_cls; ++c) {
         head->cls_off[c] = n;
         for (int id : ids) {
@@ -542,6 +552,11 @@ int tvolap_server_tick(tvolap_server_t s)
             d.pos = (int)(t % R);
             d.sel = s->sel_h[id];
             d.m_end = (int)std::min<int64_t>(ss.M, t / 2 + 1);
+            d.chunk_len = std::max(SRV_MIN_CHUNK, (d.m_end + s->max_chunks - 1) / s->max_chunks);
+            d.n_chunks = (d.m_end + d.chunk_len - 1) / d.chunk_len;
+            d.part_base = (int)slots;
+            d.pad = 0;
+            slots += (int64_t)std::max(1, 2 * ss.L / SRV_GROUP_BINS) * d.n_chunks;
             due[n++] = d;
             const int64_t spec = 2 * (int64_t)ss.L * 8;
             mac_bytes += (int64_t)(1 + ss.n_out) * d.m_end * spec + (int64_t)ss.n_out * spec;
@@ -549,19 +564,13 @@ int tvolap_server_tick(tvolap_server_t s)
         }
         head->cls_n[c] = n - head->cls_off[c];
     }
-    // order due entries by depth for the item list (stable: equal depths keep id order)
-    std::vector<int> order(n);
-    for (int i = 0; i < n; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        const int64_t cx = (int64_t)due[x].m_end * (2 * s->sch.st[due[x].slot].L);
-        const int64_t cy = (int64_t)due[y].m_end * (2 * s->sch.st[due[y].slot].L);
-        return cx > cy;
-    });
+    // chunks are at most max_chunks per group and at least SRV_MIN_CHUNK long,
+    // so items are of similar size: they go in due order, chunk by chunk
     int n_items = 0;
-    for (int i : order) {
-        const int P = 2 * s->sch.st[due[i].slot].L;
-        const int groups = std::max(1, P / SRV_GROUP_BINS);
-        for (int g = 0; g < groups; ++g) items[n_items++] = SrvItem{i, g};
+    for (int i = 0; i < n; ++i) {
+        const int groups = std::max(1, 2 * s->sch.st[due[i].slot].L / SRV_GROUP_BINS);
+        for (int g = 0; g < groups; ++g)
+            for (int ch = 0; ch < due[i].n_chunks; ++ch) items[n_items++] = SrvItem{i, g, ch, 0};
     }
     head->seq = s->seq + 1;
     head->n_items = (uint32_t)n_items;
