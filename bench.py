@@ -836,7 +836,7 @@ def run_serve(args):
             "stages_ms_per_tick": {"forward": round(stage_ms[0] / timed_ticks, 4),
                                    "mac": round(stage_ms[1] / timed_ticks, 4),
                                    "inverse": round(stage_ms[2] / timed_ticks, 4)},
-            "gpu_launches": 7 * thr_ticks,
+            "gpu_launches": 3 * thr_ticks,           # forward, MAC, inverse per tick
             "peaks": kind, "clocks": clk.summary(), "cpu_baseline": cpu}
 
 
