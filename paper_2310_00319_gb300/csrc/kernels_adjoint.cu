@@ -73,8 +73,8 @@ k_mac_params(const float4 *__restrict__ X, int64_t x_first, int x_count, const f
     if (m_end > M) m_end = M;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 8
-    for (int m = 0; m < m_end; ++m)
-        cmac4(acc, __ldg(Pt + (int64_t)m * P4), __ldg(Xt - (int64_t)(2 * m) * P4));
+    for (int m = 0; m < m_end; ++m)   // P is read once: evict-first; X comes from L2
+        cmac4(acc, __ldcs(Pt + (int64_t)m * P4), __ldg(Xt - (int64_t)(2 * m) * P4));
     Y[((int64_t)o * y_rows + i) * P4 + k] = acc;
 }
 
