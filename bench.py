@@ -404,10 +404,11 @@ def run_stream(args, wl, dev, stream, ticks=600, warm=50):
 def run_adjoint(args):
     """Differentiable model at 16 channels x 240000 samples, L = 256, M = 47:
     one training step = forward (block spectra, Eq. 7 with per-block parameter
-    spectra, inverse + overlap-add) and backward (gradient spectra, fused
-    adjoint of Eq. 7, input gradient), the input spectra recomputed per segment
-    of 32 blocks in the backward. The parameter kernels stream P (2.9 GB) and dP:
-    HBM-bound."""
+    spectra, inverse + overlap-add) and backward (gradient spectra, adjoint of
+    Eq. 7, input gradient). The backward recomputes each block's input spectrum
+    inside the adjoint kernel (no spectra kept); the same step with the spectra
+    recomputed per segment of 32 blocks by the transform kernel is reported
+    beside it. The parameter kernels stream P (2.9 GB) and dP: HBM-bound."""
     import torch
     from paper_2310_00319_gb300 import Plan
     from synth import workloads as W
@@ -428,8 +429,7 @@ def run_adjoint(args):
     names = ["fwd_spectra", "mac_params", "inverse_ola", "adjoint_output", "bwd_spectra",
              "adjoint_mac", "adjoint_input"]
 
-    def step(ev):
-        tm = {k: 0.0 for k in names}
+    def step(ev, fused=True):
         marks = []
 
         def mark(name):
@@ -445,12 +445,17 @@ def run_adjoint(args):
         mark("inverse_ola")
         G = plan.adjoint_output(r, 0, nb)
         mark("adjoint_output")
-        for q0 in range(0, nb, K):                       # backward: X recomputed per segment
-            qc = min(K, nb - q0)
-            Xs = plan.block_spectra(x, q0, qc)
+        if fused:                                        # X(q) recomputed in the kernel
             mark("bwd_spectra")
-            plan.adjoint_mac(G, 0, Xs, q0, Pm, q0, qc, dP, dX=dX, dx_row=q0)
+            plan.adjoint_mac_x(G, 0, x, Pm, 0, nb, dP, dX=dX, dx_row=0)
             mark("adjoint_mac")
+        else:
+            for q0 in range(0, nb, K):                   # X recomputed per segment
+                qc = min(K, nb - q0)
+                Xs = plan.block_spectra(x, q0, qc)
+                mark("bwd_spectra")
+                plan.adjoint_mac(G, 0, Xs, q0, Pm, q0, qc, dP, dX=dX, dx_row=q0)
+                mark("adjoint_mac")
         dx.zero_()
         mark("copy")
         plan.adjoint_input(dX, 0, dx)
@@ -470,6 +475,16 @@ def run_adjoint(args):
         torch.cuda.synchronize(dev)
     plan.check()
     ms = t0e.elapsed_time(t1e) / args.steps
+    # the same step with segments of K blocks recomputed by the transform kernel
+    for _ in range(2):
+        step([], fused=False)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(args.steps):
+        step([], fused=False)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    seg_ms = s0.elapsed_time(s1) / args.steps
     tot = {k: 0.0 for k in names + ["copy"]}
     for marks in evs:
         for (n0, e0), (n1, e1) in zip(marks[:-1], marks[1:]):
@@ -484,11 +499,13 @@ def run_adjoint(args):
             "value": round(C * N / (ms * 1e-3), 1), "unit": "channel-samples/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "differentiable_16ch_L256_M47_N240000", "segment_blocks": K,
+            "config": {"workload": "differentiable_16ch_L256_M47_N240000",
+                       "backward": "input spectra recomputed inside the adjoint kernel",
                        "param_bytes": pbytes},
+            "segmented_k32_ms_per_step": round(seg_ms, 4),
             "roofline": {"bound": "hbm", "achieved": round(adj_gbs, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(adj_gbs / hbm, 4), "traffic": None,
-                         "kernel": "k_adjoint_mac (read P, write dP)"},
+                         "kernel": "k_adjoint_mac_x (read P, write dP; X recomputed)"},
             "mac_params_gbs": round(fwd_gbs, 1),
             "stages_ms": {k: round(v, 4) for k, v in tot.items()},
             "peaks": kind, "clocks": clk.summary()}

@@ -280,6 +280,21 @@ TVOLAP_API int tvolap_adjoint_mac(tvolap_t h, const float *G_dev, int64_t g_firs
                                   int q_count, float *dP_dev, float *dX_dev, int64_t dx_rows);
 
 /*
+ * tvolap_adjoint_mac with the input spectra recomputed inside the kernel
+ * instead of read: each CTA transforms the blocks q it handles from x_dev
+ * (Eqs. 1, 3, 5, the same arithmetic as tvolap_block_spectra) and uses them at
+ * once, so no input spectra are stored between forward and backward (the
+ * limit of recomputing per segment, segment length 1). Results equal those of
+ * tvolap_block_spectra followed by tvolap_adjoint_mac.
+ *   x_dev  device float [n_in][x_stride], N valid samples per channel
+ * Other arguments and requirements as tvolap_adjoint_mac.
+ */
+TVOLAP_API int tvolap_adjoint_mac_x(tvolap_t h, const float *G_dev, int64_t g_first, int g_count,
+                                    const float *x_dev, int64_t N, int64_t x_stride,
+                                    const float *P_dev, int64_t p_blocks, int64_t q_first,
+                                    int q_count, float *dP_dev, float *dX_dev, int64_t dx_rows);
+
+/*
  * Adjoint of Eqs. 1, 3, 5: for each block q of the range,
  *   dx[c][(q-1)L + n] += w(n) Re sum_{k<P} dX[c][q - q_first](k) e^{+i pi n (2k+1)/4L},
  * 0 <= n < 2L, samples outside [0, N) dropped. Adds to what dx_dev holds, so

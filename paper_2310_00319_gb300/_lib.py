@@ -56,6 +56,9 @@ SIGNATURES = {
     "tvolap_adjoint_mac": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int,
                                    c_void_p, c_int64, c_int64, c_int, c_void_p, c_void_p,
                                    c_int64]),
+    "tvolap_adjoint_mac_x": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_void_p, c_int64,
+                                     c_int64, c_void_p, c_int64, c_int64, c_int, c_void_p,
+                                     c_void_p, c_int64]),
     "tvolap_adjoint_input": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_void_p, c_int64,
                                      c_int64]),
     "tvolap_process_signal_static": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p,

@@ -8,9 +8,11 @@ C ABI; this module only orders the calls and holds the tensors.
     loss = ((y - target) ** 2).mean(); loss.backward()
 
 The input spectra X are not kept from the forward to the backward: the
-backward recomputes them, by default all at once, or with ``segment=K`` per
-segment of K blocks, so that at most K blocks of X are held (the adjoint of
-Eq. 7 at block q reads only X(q)). With ``fwd_segment=K`` the forward too
+backward recomputes them. By default each block's spectrum is recomputed
+inside the adjoint kernel where it is used (tvolap_adjoint_mac_x: no X stored
+at all, one launch); with ``segment=K`` they are recomputed per segment of K
+blocks by the transform kernel, so that at most K blocks of X are held (the
+adjoint of Eq. 7 at block q reads only X(q)). With ``fwd_segment=K`` the forward too
 holds X for at most K blocks plus the 2(M-1)-block history a segment reads.
 Results are the same with and without segments.
 """
@@ -31,7 +33,7 @@ class SpectralTvolap(torch.autograd.Function):
             raise ValueError(f"P must be [{plan.n_out}, {nb}, {plan.M}, {plan.P}]")
         x = x.contiguous()
         Pspec = Pspec.contiguous()
-        K = nb if not segment else int(segment)
+        K = 0 if not segment else int(segment)          # 0: recompute inside the kernel
         Kf = nb if not fwd_segment else int(fwd_segment)
         if Kf >= nb:
             X = plan.block_spectra(x, 0, nb)
@@ -56,10 +58,13 @@ class SpectralTvolap(torch.autograd.Function):
         G = plan.adjoint_output(gy.contiguous(), 0, nb)
         dP = torch.empty_like(Pspec)
         dX = torch.empty((plan.n_out, nb, plan.P), dtype=torch.complex64, device=x.device)
-        for q0 in range(0, nb, K):
-            qc = min(K, nb - q0)
-            X = plan.block_spectra(x, q0, qc)
-            plan.adjoint_mac(G, 0, X, q0, Pspec, q0, qc, dP, dX=dX, dx_row=q0)
+        if K == 0:
+            plan.adjoint_mac_x(G, 0, x, Pspec, 0, nb, dP, dX=dX, dx_row=0)
+        else:
+            for q0 in range(0, nb, K):
+                qc = min(K, nb - q0)
+                X = plan.block_spectra(x, q0, qc)
+                plan.adjoint_mac(G, 0, X, q0, Pspec, q0, qc, dP, dX=dX, dx_row=q0)
         dx = None
         if ctx.needs_input_grad[0]:
             dx = torch.zeros_like(x)

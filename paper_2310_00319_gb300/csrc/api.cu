@@ -475,6 +475,30 @@ int tvolap_adjoint_mac(tvolap_t h, const float *G_dev, int64_t g_first, int g_co
         reinterpret_cast<float2 *>(dP_dev), reinterpret_cast<float2 *>(dX_dev), dx_rows));
 }
 
+int tvolap_adjoint_mac_x(tvolap_t h, const float *G_dev, int64_t g_first, int g_count,
+                         const float *x_dev, int64_t N, int64_t x_stride, const float *P_dev,
+                         int64_t p_blocks, int64_t q_first, int q_count, float *dP_dev,
+                         float *dX_dev, int64_t dx_rows)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (!h->identity_routing) return TVOLAP_ERR_ARG;
+    if (q_count < 0 || q_first < 0 || g_first < 0 || g_count < 0 || N < 0 || x_stride < N)
+        return TVOLAP_ERR_ARG;
+    if (q_count == 0) return TVOLAP_OK;
+    if (!G_dev || (!x_dev && N > 0) || !P_dev || !dP_dev || !dX_dev || !a16(G_dev) ||
+        !a16(P_dev) || !a16(dP_dev) || !a16(dX_dev))
+        return TVOLAP_ERR_ARG;
+    int64_t g_need = q_first + q_count + 2 * (int64_t)(h->M - 1);
+    if (g_need > p_blocks) g_need = p_blocks;
+    if (q_first + q_count > p_blocks || g_first > q_first || g_first + g_count < g_need ||
+        dx_rows < q_count)
+        return TVOLAP_ERR_ARG;
+    return cuda_status(launch_adjoint_mac_x(
+        h, reinterpret_cast<const float2 *>(G_dev), g_first, g_count, x_dev, N, x_stride,
+        reinterpret_cast<const float2 *>(P_dev), p_blocks, q_first, q_count,
+        reinterpret_cast<float2 *>(dP_dev), reinterpret_cast<float2 *>(dX_dev), dx_rows));
+}
+
 int tvolap_adjoint_input(tvolap_t h, const float *dX_dev, int64_t q_first, int q_count,
                          float *dx_dev, int64_t N, int64_t x_stride)
 {

@@ -101,6 +101,10 @@ cudaError_t launch_adjoint_mac(tvolap_plan *h, const float2 *G, int64_t g_first,
                                const float2 *X, int64_t x_first, int x_count, const float2 *Pm,
                                int64_t p_blocks, int64_t q_first, int q_count, float2 *dP,
                                float2 *dX, int64_t dx_rows);
+cudaError_t launch_adjoint_mac_x(tvolap_plan *h, const float2 *G, int64_t g_first, int g_count,
+                                 const float *x, int64_t N, int64_t x_stride, const float2 *Pm,
+                                 int64_t p_blocks, int64_t q_first, int q_count, float2 *dP,
+                                 float2 *dX, int64_t dx_rows);
 
 // kernels_mac.cu
 cudaError_t launch_mac_signal_lsu(tvolap_plan *h, const float2 *X, int n_blocks,

@@ -15,7 +15,7 @@
 //                  blocks before the signal.
 // A thread owns two bins (16-byte loads and stores) of one block; the partition
 // loop is unrolled 8 deep to keep enough loads in flight.
-#include "fft_core.cuh"
+#include "fft_block.cuh"
 #include "internal.h"
 
 namespace tvolap {
@@ -122,6 +122,82 @@ k_adjoint_mac(const float4 *__restrict__ G, int64_t g_first, int g_count,
     dX[((int64_t)o * dx_rows + (q - q_first)) * P4 + k] = acc;
 }
 
+// The adjoint of k_adjoint_mac with the input spectra recomputed in place: a
+// CTA transforms F consecutive blocks q of its output's input channel (Eqs. 1,
+// 3, 5, the same arithmetic as the forward transform kernel), leaves their
+// spectra in the FFT buffer not holding the result, then runs the adjoint of
+// Eq. 7 for those blocks exactly as k_adjoint_mac does. No input spectra are
+// stored anywhere. grid: x = ceil(q_count / F), y = outputs.
+template <int LG>
+__global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
+k_adjoint_mac_x(const float4 *__restrict__ G, int64_t g_first, int g_count,
+                const float *__restrict__ x, int64_t N, int64_t x_stride, int L,
+                const float *__restrict__ win, const float2 *__restrict__ rot,
+                const float2 *__restrict__ post, const float2 *__restrict__ tw,
+                const float4 *__restrict__ Pm, int64_t p_blocks, int M, int64_t q_first,
+                int q_count, const int32_t *__restrict__ out_to_in, float4 *__restrict__ dP,
+                float4 *__restrict__ dX, int64_t dx_rows)
+{
+    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F, P4 = P / 2;
+    extern __shared__ float2 sm[];
+    const int f = threadIdx.x / T, j = threadIdx.x % T;
+    float2 *A = sm + f * P, *B = sm + (F + f) * P;
+    const int o = blockIdx.y;
+    const int c = out_to_in[o];
+    const int64_t q0 = q_first + (int64_t)blockIdx.x * F;
+    const int64_t q_end = q_first + q_count;
+    // forward transform of block q = q0 + f into the buffer the FFT result is not in
+    bool z_in_a;
+    {
+        const int64_t q = q0 + f;
+        const bool active = q < q_end;
+        const int64_t start = (q - 1) * (int64_t)L;     // block l = q - 1 starts at l*L
+        const float *xc = x + (int64_t)c * x_stride;
+        auto src = [&](int n) {
+            const int64_t i0 = start + n;
+            const float a = (i0 >= 0 && i0 < N) ? __ldg(xc + i0) : 0.f;
+            const float b = (i0 + 1 >= 0 && i0 + 1 < N) ? __ldg(xc + i0 + 1) : 0.f;
+            return make_float2(a * __ldg(win + n), b * __ldg(win + n + 1));
+        };
+        // the window, pre-rotation and FFT of forward_block (upper half zero)
+        float2 z[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int r = j + s * T;
+            z[s] = (s < 4 && active) ? cmul(src(2 * r), __ldg(rot + r)) : make_float2(0.f, 0.f);
+        }
+        float2 *Z = fft_complex_regs<P, false>(z, A, B, j, tw);
+        z_in_a = (Z == A);                               // the same for every transform
+        float2 *Xs = z_in_a ? B : A;
+        split_forward<P>(Z, j, post, [&](int k, float2 v) { Xs[k] = v; });
+    }
+    __syncthreads();
+    const int64_t MP4 = (int64_t)M * P4;
+    float4 *dPo = dP + (int64_t)o * p_blocks * MP4;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int it = threadIdx.x; it < F * P4; it += blockDim.x) {
+        const int ff = it / P4, k = it % P4;
+        const int64_t q = q0 + ff;
+        if (q >= q_end) continue;
+        const float4 xq = reinterpret_cast<const float4 *>(z_in_a ? sm + (F + ff) * P
+                                                                  : sm + ff * P)[k];
+        const float4 *Gq = G + ((int64_t)o * g_count + (q - g_first)) * P4 + k;
+        const float4 *Pq = Pm + (int64_t)o * p_blocks * MP4 + q * MP4 + k;
+        float4 *dPq = dPo + q * MP4 + k;
+        int m_end = M;
+        if (q + 2 * (int64_t)(M - 1) >= p_blocks) m_end = (int)((p_blocks - 1 - q) / 2) + 1;
+        float4 acc = zero;
+#pragma unroll 8
+        for (int m = 0; m < m_end; ++m) {
+            const int64_t off = (int64_t)(2 * m) * MP4 + (int64_t)m * P4;
+            const float4 g = __ldg(Gq + (int64_t)(2 * m) * P4);
+            cmacc4(acc, g, __ldg(Pq + off));
+            dPq[off] = mulc4(g, xq);
+        }
+        dX[((int64_t)o * dx_rows + (q - q_first)) * P4 + k] = acc;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_mac_params(tvolap_plan *h, const float2 *X, int64_t x_first, int x_count,
@@ -151,6 +227,38 @@ cudaError_t launch_adjoint_mac(tvolap_plan *h, const float2 *G, int64_t g_first,
         reinterpret_cast<const float4 *>(G), g_first, g_count, reinterpret_cast<const float4 *>(X),
         x_first, x_count, reinterpret_cast<const float4 *>(Pm), p_blocks, h->M, P4, q_first, q_count,
         h->out_to_in, reinterpret_cast<float4 *>(dP), reinterpret_cast<float4 *>(dX), dx_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_mac_x(tvolap_plan *h, const float2 *G, int64_t g_first, int g_count,
+                                 const float *x, int64_t N, int64_t x_stride, const float2 *Pm,
+                                 int64_t p_blocks, int64_t q_first, int q_count, float2 *dP,
+                                 float2 *dX, int64_t dx_rows)
+{
+    if (q_count <= 0) return cudaSuccess;
+    const int P4 = h->P / 2;
+    if (q_first == 0 && h->M > 1) {
+        // dP(t, m) with t < 2m: the virtual blocks before the signal (no X, no G read)
+        dim3 grid((unsigned)(2 * (h->M - 1)), (unsigned)h->n_out, (unsigned)((P4 + AT - 1) / AT));
+        k_adjoint_mac<<<grid, AT, 0, h->stream>>>(
+            reinterpret_cast<const float4 *>(G), g_first, g_count, nullptr, 0, 0,
+            reinterpret_cast<const float4 *>(Pm), p_blocks, h->M, P4, 0, 0, h->out_to_in,
+            reinterpret_cast<float4 *>(dP), reinterpret_cast<float4 *>(dX), dx_rows);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    TVOLAP_DISPATCH(h->lgP, {
+        constexpr int P = 1 << LG;
+        const size_t sm = smem_fft<LG>();
+        cudaError_t e = set_smem(k_adjoint_mac_x<LG>, sm);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)((q_count + Geo<P>::F - 1) / Geo<P>::F), (unsigned)h->n_out);
+        k_adjoint_mac_x<LG><<<grid, Geo<P>::THREADS, sm, h->stream>>>(
+            reinterpret_cast<const float4 *>(G), g_first, g_count, x, N, x_stride, h->L, h->win,
+            h->rot, h->post, h->tw, reinterpret_cast<const float4 *>(Pm), p_blocks, h->M, q_first,
+            q_count, h->out_to_in, reinterpret_cast<float4 *>(dP), reinterpret_cast<float4 *>(dX),
+            dx_rows);
+    });
     return cudaGetLastError();
 }
 

@@ -280,6 +280,21 @@ class Plan:
                    ptr, dX.shape[1])
         return dX
 
+    def adjoint_mac_x(self, G, g_first, x, Pspec, q_first, q_count, dP, dX=None, dx_row=0):
+        """adjoint_mac with the input spectra recomputed inside the kernel from
+        x [n_in, N] (nothing stored between forward and backward)."""
+        if dX is None:
+            dX = torch.empty((self.n_out, q_count, self.P), dtype=torch.complex64,
+                             device=self.device)
+        if dx_row < 0 or dx_row + q_count > dX.shape[1]:
+            raise ValueError("dX rows out of range")
+        x = x.contiguous()
+        ptr = ctypes.c_void_p(dX.data_ptr() + dx_row * self.P * 8)
+        self._call("tvolap_adjoint_mac_x", _ptr(G), int(g_first), G.shape[1], _ptr(x), x.shape[1],
+                   x.shape[1], _ptr(Pspec), Pspec.shape[1], int(q_first), int(q_count), _ptr(dP),
+                   ptr, dX.shape[1])
+        return dX
+
     def adjoint_input(self, dX: torch.Tensor, q_first: int, dx: torch.Tensor):
         """dx [n_in, N] += the input gradient of blocks q_first .. + dX.shape[1] - 1."""
         self._call("tvolap_adjoint_input", _ptr(dX), int(q_first), dX.shape[1], _ptr(dx),

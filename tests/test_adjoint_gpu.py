@@ -121,8 +121,9 @@ def test_mse_training_step_against_oracle():
 
 def test_full_size_sampled_gradients():
     """16 channels, L = 256, M = 47, 240000 samples: parameters 2.9 GB. Forward
-    and backward run whole on the GPU; gradient entries are checked against the
-    oracle computed entry by entry."""
+    and backward run whole on the GPU (the backward recomputing every input
+    spectrum inside the adjoint kernel); gradient entries are checked against
+    the oracle computed entry by entry."""
     dev = _dev()
     from paper_2310_00319_gb300.autograd import spectral_tvolap
     d = W.differentiable(seed=4)
@@ -131,7 +132,7 @@ def test_full_size_sampled_gradients():
     x = torch.from_numpy(d["x"]).to(dev).requires_grad_(True)
     P = torch.from_numpy(d["P"]).to(dev).requires_grad_(True)
     r = torch.from_numpy(d["r"]).to(dev)
-    y = spectral_tvolap(x, P, plan, segment=32)
+    y = spectral_tvolap(x, P, plan)                 # backward recomputes X inside the kernel
     (y * r).sum().backward()
     assert torch.isfinite(y).all() and torch.isfinite(P.grad).all() and torch.isfinite(x.grad).all()
     rng = np.random.default_rng(5)
@@ -146,3 +147,27 @@ def test_full_size_sampled_gradients():
         assert np.max(np.abs(gP - sP)) <= 1e-3 * peakP, c
         relx, _ = _rel(gx, sx)
         assert relx <= 1e-3, (c, relx)
+
+
+@pytest.mark.parametrize("L,q_first,q_count", [(32, 0, None), (64, 0, 37), (64, 9, 23)])
+def test_adjoint_mac_x_equals_two_step(L, q_first, q_count):
+    """tvolap_adjoint_mac_x (input spectra recomputed in the kernel) gives the
+    same dP and dX, bit for bit, as tvolap_block_spectra + tvolap_adjoint_mac,
+    for the whole range and for ranges that start inside the signal."""
+    dev = _dev()
+    d = W.differentiable(seed=15, n_ch=3, N=40 * L + 7, L=L, ir_len=9 * L)
+    plan = _plan(d, dev)
+    nb = d["n_blocks"]
+    qc = nb - q_first if q_count is None else q_count
+    x = torch.from_numpy(d["x"]).to(dev)
+    Pm = torch.from_numpy(d["P"]).to(dev)
+    r = torch.from_numpy(d["r"]).to(dev)
+    G = plan.adjoint_output(r, 0, nb)
+    dP1 = torch.zeros_like(Pm)
+    dP2 = torch.zeros_like(Pm)
+    X = plan.block_spectra(x, q_first, qc)
+    dX1 = plan.adjoint_mac(G, 0, X, q_first, Pm, q_first, qc, dP1)
+    dX2 = plan.adjoint_mac_x(G, 0, x, Pm, q_first, qc, dP2)
+    torch.cuda.synchronize()
+    assert torch.equal(dX1, dX2)
+    assert torch.equal(dP1, dP2)
