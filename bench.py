@@ -413,7 +413,7 @@ def run_adjoint(args):
     from paper_2310_00319_gb300 import Plan
     from synth import workloads as W
     dev = torch.device("cuda", 0)
-    d = W.differentiable(seed=4)
+    d = W.differentiable(seed=4, n_ch=args.adj_channels)
     C, N = d["x"].shape
     L, M, nb, P = d["L"], d["M"], d["n_blocks"], 2 * d["L"]
     plan = Plan(L, M, n_in=C, n_out=C, n_slots=1, device=dev)
@@ -499,7 +499,7 @@ def run_adjoint(args):
             "value": round(C * N / (ms * 1e-3), 1), "unit": "channel-samples/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "differentiable_16ch_L256_M47_N240000",
+            "config": {"workload": f"differentiable_{C}ch_L256_M47_N240000",
                        "backward": "input spectra recomputed inside the adjoint kernel",
                        "param_bytes": pbytes},
             "segmented_k32_ms_per_step": round(seg_ms, 4),
@@ -992,6 +992,8 @@ def main():
                     help="serve: streams present at the start (slots capped at 1000)")
     ap.add_argument("--serve-ticks", type=int, default=10000,
                     help="serve: ticks of the latency run (throughput run: 3/4 of it)")
+    ap.add_argument("--adj-channels", type=int, default=16,
+                    help="adjoint: channels of the differentiable workload")
     ap.add_argument("--staging", type=int, default=None, choices=[0, 1, 2],
                     help="batched: fixed multiply-accumulate staging instead of the autotuner")
     ap.add_argument("--skip-extras", action="store_true")
