@@ -532,9 +532,8 @@ def run_batched(args):
     if args.staging is None:
         tuned = B.autotune(reps=2)
     else:                                  # fixed staging (profiling: the timing would differ)
-        for g in B.groups:
-            g.plan.set_option(1, args.staging)
-        tuned = {g.L: (args.staging, None) for g in B.groups}
+        B.set_staging(args.staging)
+        tuned = {B.group_info(g)[0]: args.staging for g in range(B.n_groups)}
     B.capture()
     for _ in range(args.warmup):
         B.replay()
@@ -546,10 +545,9 @@ def run_batched(args):
             B.replay()
         t1e.record(B.stream)
         torch.cuda.synchronize(dev)
-    for g in B.groups:
-        g.plan.check()
+    B.check()
     ms = t0e.elapsed_time(t1e) / args.steps
-    launches = 4 * len(B.groups)    # per hop group: forward, MAC group + overflow, inverse
+    launches = 4 * B.n_groups       # per hop group: forward, MAC group + overflow, inverse
 
     # plain per-source form: one single-channel process_signal per source in a
     # loop, with the staging the autotuner chose for the source's hop (same
@@ -584,7 +582,7 @@ def run_batched(args):
     else:
         default_ms = time_loop()
         for p, *_, L in per:
-            p.set_option(1, tuned[L][0])
+            p.set_option(1, tuned[L])
         per_ms = time_loop()
     for p, *_ in per:
         p.check()
@@ -616,7 +614,7 @@ def run_batched(args):
                          "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
                          "kernel": "whole step: Eq. 7 flops / replay time (lower bound on "
                                    "the multiply-accumulate kernels)"},
-            "autotune": {str(L): v[0] for L, v in tuned.items()},
+            "autotune": {str(L): v for L, v in tuned.items()},
             "gpu_launches": launches * args.steps, "clocks": clocks, "cpu_baseline": cpu}
 
 

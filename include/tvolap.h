@@ -364,6 +364,95 @@ TVOLAP_API int tvolap_set_option(tvolap_t h, int option, int value);
 TVOLAP_API int tvolap_check(tvolap_t h);
 
 /* ========================================================================
+ * Batched sources: many independent sources with different hops, partition
+ * counts, numbers of stored filters and signal lengths, run together. The
+ * sources are grouped by hop; each group is one plan whose channels are the
+ * group's sources (tvolap_process_ragged), all groups share one stream, and
+ * the whole batch can be captured once as a CUDA graph and replayed. The
+ * multiply-accumulate staging (TVOLAP_OPT_MAC_STAGING) can be chosen per
+ * group by timing the variants on the batch itself.
+ * ======================================================================== */
+typedef struct tvolap_batch *tvolap_batch_t;
+
+/* One source of a batch. */
+typedef struct tvolap_batch_source {
+    int L;             /* hop, a power of two in [16, 1024] */
+    int M;             /* partitions: responses of up to 2*L*M taps */
+    int n_filters;     /* stored filters (responses) >= 1 */
+    int64_t N;         /* input samples >= 0 */
+    int64_t out_len;   /* output samples >= 0 */
+} tvolap_batch_source;
+
+/*
+ * Create a batch of n_src sources (host array src). Allocates, per hop group,
+ * a plan, the inputs [sources][max N], schedules [sources][max blocks] and
+ * outputs [sources][max out_len] in device memory (all zero), and the
+ * per-source lengths and partition counts. stream: cudaStream_t of every call
+ * (NULL = the batch creates its own; graphs cannot be captured on the legacy
+ * stream). Synchronises before returning.
+ */
+TVOLAP_API int tvolap_batch_create(tvolap_batch_t *out, const tvolap_batch_source *src, int n_src,
+                                   void *stream);
+TVOLAP_API int tvolap_batch_destroy(tvolap_batch_t b);
+
+/*
+ * Where source i lives (device pointers, valid for the batch's life):
+ *   x     float [N]            its input (write it before running)
+ *   sched int32 [n_blocks]     filter of each block, t = l + 1, as slot_base +
+ *                              the source's own filter index (0 .. n_filters-1)
+ *   y     float [out_len]      its output after a run
+ * n_blocks = floor((out_len - 1) / L) + 2. Any pointer argument may be NULL.
+ */
+TVOLAP_API int tvolap_batch_source_view(tvolap_batch_t b, int i, float **x, int32_t **sched,
+                                        float **y, int *slot_base, int64_t *n_blocks);
+
+/*
+ * Copy source i's input (device float [N]) and schedule (device int32
+ * [n_blocks], the source's own filter indices 0 .. n_filters - 1) into the
+ * batch, on the batch's stream. A schedule entry outside that range selects an
+ * all-zero filter and makes tvolap_batch_check return TVOLAP_ERR_ARG.
+ */
+TVOLAP_API int tvolap_batch_set_source(tvolap_batch_t b, int i, const float *x_dev,
+                                       const int32_t *sched_dev);
+
+/* Copy source i's output (out_len floats) to y_dev, on the batch's stream. */
+TVOLAP_API int tvolap_batch_get_output(tvolap_batch_t b, int i, float *y_dev);
+
+/* Transform source i's n_filters responses (device float [n_filters][ir_stride],
+   ir_len <= 2*L*M taps) into its filter slots (Eqs. 2, 4, 6). */
+TVOLAP_API int tvolap_batch_load_filters(tvolap_batch_t b, int i, const float *ir_dev,
+                                         int ir_len, int64_t ir_stride);
+
+/* Enqueue one run of every source: the captured graph if there is one, else
+   the groups' calls directly. */
+TVOLAP_API int tvolap_batch_run(tvolap_batch_t b);
+
+/* Record one run of the whole batch as a CUDA graph (after one direct run,
+   so every workspace has its size); later runs replay it. */
+TVOLAP_API int tvolap_batch_capture(tvolap_batch_t b);
+
+/*
+ * For every hop group, time each multiply-accumulate staging (0, 1, 2) over
+ * reps runs on the batch itself and keep the fastest; drops a captured graph.
+ * chosen (may be NULL): host int [number of groups], the staging per group in
+ * increasing hop order. Synchronises.
+ */
+TVOLAP_API int tvolap_batch_autotune(tvolap_batch_t b, int reps, int *chosen);
+
+/* Set the multiply-accumulate staging of group g (-1: every group); drops a
+   captured graph. */
+TVOLAP_API int tvolap_batch_set_staging(tvolap_batch_t b, int g, int staging);
+
+/* Number of hop groups, and group g's hop, sources and staging. */
+TVOLAP_API int tvolap_batch_groups(tvolap_batch_t b, int *n_groups);
+TVOLAP_API int tvolap_batch_group_info(tvolap_batch_t b, int g, int *L, int *n_sources,
+                                       int *staging);
+
+/* Synchronise the batch's stream and report deferred errors of every group
+   (as tvolap_check). */
+TVOLAP_API int tvolap_batch_check(tvolap_batch_t b);
+
+/* ========================================================================
  * Streaming server: many independent streams, each with its own hop L,
  * partition count M, outputs (1 or 2, e.g. a binaural pair fed by one input)
  * and a bank of stored filters, processed block by block as in

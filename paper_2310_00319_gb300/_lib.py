@@ -64,6 +64,22 @@ SIGNATURES = {
     "tvolap_process_signal_static": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p,
                                              c_void_p, c_void_p, c_int64, c_void_p, c_int64,
                                              c_int64]),
+    # batched sources
+    "tvolap_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_void_p, c_int, c_void_p]),
+    "tvolap_batch_destroy": (c_int, [c_void_p]),
+    "tvolap_batch_source_view": (c_int, [c_void_p, c_int, ctypes.POINTER(c_void_p),
+                                         ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), P_int,
+                                         P_int64]),
+    "tvolap_batch_set_source": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "tvolap_batch_get_output": (c_int, [c_void_p, c_int, c_void_p]),
+    "tvolap_batch_load_filters": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int64]),
+    "tvolap_batch_run": (c_int, [c_void_p]),
+    "tvolap_batch_capture": (c_int, [c_void_p]),
+    "tvolap_batch_autotune": (c_int, [c_void_p, c_int, P_int]),
+    "tvolap_batch_set_staging": (c_int, [c_void_p, c_int, c_int]),
+    "tvolap_batch_groups": (c_int, [c_void_p, P_int]),
+    "tvolap_batch_group_info": (c_int, [c_void_p, c_int, P_int, P_int, P_int]),
+    "tvolap_batch_check": (c_int, [c_void_p]),
     # streaming server
     "tvolap_server_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int, c_int64,
                                      c_void_p]),

@@ -1,126 +1,147 @@
-"""Many independent sources with different hops, impulse-response lengths and
-signal lengths in a few launches.
+"""Python binding of batched sources (tvolap_batch_*): argument marshalling only.
 
-Sources are grouped by hop L (the transform size); each group is one plan
-whose channels are the group's sources, processed with
-tvolap_process_ragged (per-channel lengths and partition counts). All plans
-share one CUDA stream, so the whole batch can be captured once as a CUDA graph
-and replayed. ``autotune`` picks the multiply-accumulate staging per group by
-timing the variants on the batch itself.
+Many independent sources with different hops, impulse-response lengths and
+signal lengths run together: the library groups them by hop (one plan per
+group, channels = sources, tvolap_process_ragged), runs every group on one
+stream, can capture the whole batch as one CUDA graph, and picks the
+multiply-accumulate staging per group by timing the variants on the batch.
 """
 from __future__ import annotations
+
+import ctypes
 
 import numpy as np
 import torch
 
-from .tvolap import Plan, n_blocks_for
+from . import _lib
+from .tvolap import _ptr
 
 
-class HopGroup:
-    def __init__(self, L, sources, index, device, stream):
-        self.L, self.index = L, index
-        n = len(sources)
-        self.M = max(s.M for s in sources)
-        n_slots = sum(s.irs.shape[0] for s in sources)
-        self.plan = Plan(L, self.M, n_in=n, n_out=n, n_slots=n_slots, device=device, stream=stream)
-        self.N = [s.x.shape[0] for s in sources]
-        self.out_len = [s.out_len for s in sources]
-        self.max_out = max(self.out_len)
-        nb = n_blocks_for(self.max_out, L)
-        xs = max(self.N)
-        x = np.zeros((n, xs), np.float32)
-        sched = np.zeros((n, nb), np.int32)
-        slot0 = 0
-        dev = device
-        with torch.cuda.stream(stream):
-            for c, s in enumerate(sources):
-                x[c, :s.x.shape[0]] = s.x
-                k = min(nb, s.sched.shape[0])
-                sched[c, :k] = s.sched[:k] + slot0
-                self.plan.load_bank(slot0, torch.from_numpy(s.irs).to(dev))
-                slot0 += s.irs.shape[0]
-            self.x = torch.from_numpy(x).to(dev)
-            self.sched = torch.from_numpy(sched).to(dev)
-            self.n = torch.tensor(self.N, dtype=torch.int64, device=dev)
-            self.ol = torch.tensor(self.out_len, dtype=torch.int64, device=dev)
-            self.parts = torch.tensor([s.M for s in sources], dtype=torch.int32, device=dev)
-            self.y = torch.zeros((n, self.max_out), dtype=torch.float32, device=dev)
+class _Source(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("M", ctypes.c_int), ("n_filters", ctypes.c_int),
+                ("N", ctypes.c_int64), ("out_len", ctypes.c_int64)]
 
-    def run(self):
-        self.plan.process_ragged(self.x, self.n, self.ol, self.parts, self.max_out, self.sched,
-                                 out=self.y)
+
+def _partitions(ir_len: int, L: int) -> int:
+    return max(1, -(-ir_len // (2 * L)))
 
 
 class BatchedTvolap:
-    """sources: objects with L, x [N], irs [n_ir, ir_len], sched [n_blocks]
-    (index into irs per block, t = l + 1), out_len."""
+    """sources: objects with L, x [N] (float32), irs [n_filters, ir_len]
+    (float32), sched [n_blocks] (int32 index into irs per block, t = l + 1) and
+    out_len. All calls are ordered on ``stream`` (default: a new stream)."""
 
-    def __init__(self, sources, device=None):
+    def __init__(self, sources, device=None, stream=None):
+        self.lib = _lib.load()
         self.device = torch.device(device if device is not None else "cuda")
-        self.stream = torch.cuda.Stream(self.device)
-        by_L = {}
-        for i, s in enumerate(sources):
-            by_L.setdefault(int(s.L), []).append(i)
-        self.groups = []
-        for L in sorted(by_L):
-            idx = by_L[L]
-            self.groups.append(HopGroup(L, [sources[i] for i in idx], idx, self.device,
-                                        self.stream))
-        self.n_sources = len(sources)
-        self.graph = None
-        torch.cuda.synchronize(self.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self.sources = sources
+        n = len(sources)
+        arr = (_Source * n)(*[_Source(int(s.L), _partitions(s.irs.shape[1], int(s.L)),
+                                      s.irs.shape[0], s.x.shape[0], int(s.out_len))
+                              for s in sources])
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.tvolap_batch_create(ctypes.byref(h), arr, n,
+                                                    ctypes.c_void_p(self.stream.cuda_stream)),
+                       "tvolap_batch_create")
+        self.h = h
+        keep = []                       # device copies alive until the stream has read them
+        with torch.cuda.device(self.device):
+            for i, s in enumerate(sources):
+                nb = 0 if s.out_len <= 0 else (int(s.out_len) - 1) // int(s.L) + 2
+                x = torch.from_numpy(np.ascontiguousarray(s.x, np.float32)).to(self.device)
+                sc = torch.from_numpy(np.ascontiguousarray(s.sched[:nb], np.int32)).to(self.device)
+                irs = torch.from_numpy(np.ascontiguousarray(s.irs, np.float32)).to(self.device)
+                self.stream.wait_stream(torch.cuda.current_stream(self.device))
+                self._call("tvolap_batch_set_source", i,
+                           _ptr(x) if x.numel() else None, _ptr(sc) if sc.numel() else None)
+                self._call("tvolap_batch_load_filters", i, _ptr(irs), irs.shape[1], irs.shape[1])
+                keep += [x, sc, irs]
+            self.stream.synchronize()
+        del keep
+        self.graph = False
 
+    def set_source(self, i: int, x: torch.Tensor, sched: torch.Tensor):
+        """Replace source i's input (device float32 [N]) and schedule (device
+        int32 [n_blocks], indices into its filters); later runs and graph
+        replays read them."""
+        x = x.contiguous()
+        sched = sched.to(torch.int32).contiguous()
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self._call("tvolap_batch_set_source", int(i), _ptr(x) if x.numel() else None,
+                   _ptr(sched) if sched.numel() else None)
+        x.record_stream(self.stream)
+        sched.record_stream(self.stream)
+
+    # ------------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.lib.tvolap_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, name, *args):
+        return _lib.check(getattr(self.lib, name)(self.h, *args), name)
+
+    # ------------------------------------------------------------------ runs
     def run(self):
-        """Enqueue every group on the batch's stream."""
-        for g in self.groups:
-            g.run()
+        """Enqueue one run of every source (a graph replay once captured)."""
+        self._call("tvolap_batch_run")
 
     def capture(self):
-        """Record the whole batch as one CUDA graph (after one eager run, so
-        every workspace already has its size)."""
-        self.run()
-        torch.cuda.synchronize(self.device)
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph, stream=self.stream):
-            self.run()
-        torch.cuda.synchronize(self.device)
-        return self.graph
+        """Record one run of the whole batch as a CUDA graph."""
+        self._call("tvolap_batch_capture")
+        self.graph = True
 
     def replay(self):
-        """Replay the captured batch on the batch's stream."""
-        if self.graph is None:
+        if not self.graph:
             self.capture()
-        with torch.cuda.stream(self.stream):
-            self.graph.replay()
+        self.run()
 
-    def output(self, i):
-        """Output of source i (a view into its group's buffer)."""
-        for g in self.groups:
-            if i in g.index:
-                c = g.index.index(i)
-                return g.y[c, :g.out_len[c]]
-        raise IndexError(i)
+    def autotune(self, reps: int = 3) -> dict:
+        """Per hop group, keep the fastest multiply-accumulate staging.
+        Returns {L: staging}."""
+        ng = self.n_groups
+        chosen = (ctypes.c_int * ng)()
+        self._call("tvolap_batch_autotune", int(reps), chosen)
+        self.graph = False
+        return {self.group_info(g)[0]: int(chosen[g]) for g in range(ng)}
 
-    def autotune(self, reps=3):
-        """Per group, time the multiply-accumulate stagings on this batch (TMA
-        groups of up to 3 or 4 filters, cp.async) and keep the fastest.
-        Returns {L: (chosen option, ms per option)}."""
-        chosen = {}
-        for g in self.groups:
-            times = []
-            for opt in (0, 1, 2):
-                g.plan.set_option(1, opt)
-                g.run()
-                torch.cuda.synchronize(self.device)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(self.stream)
-                for _ in range(reps):
-                    g.run()
-                e1.record(self.stream)
-                torch.cuda.synchronize(self.device)
-                times.append(e0.elapsed_time(e1) / reps)
-            best = int(np.argmin(times))
-            g.plan.set_option(1, best)
-            chosen[g.L] = (best, times)
-        self.graph = None                               # recapture with the chosen kernels
-        return chosen
+    def set_staging(self, staging: int, group: int = -1):
+        """Multiply-accumulate staging of one hop group (-1: all)."""
+        self._call("tvolap_batch_set_staging", int(group), int(staging))
+        self.graph = False
+
+    def check(self):
+        """Synchronise and raise on deferred device errors of any group."""
+        self._call("tvolap_batch_check")
+
+    # ------------------------------------------------------------------ results
+    def output(self, i: int) -> torch.Tensor:
+        """Output of source i (a copy, ordered after the batch's work)."""
+        n = int(self.sources[i].out_len)
+        y = torch.empty(n, dtype=torch.float32, device=self.device)
+        if n:
+            self.stream.wait_stream(torch.cuda.current_stream(self.device))
+            self._call("tvolap_batch_get_output", int(i), _ptr(y))
+            torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return y
+
+    @property
+    def n_groups(self) -> int:
+        n = ctypes.c_int()
+        self._call("tvolap_batch_groups", ctypes.byref(n))
+        return n.value
+
+    def group_info(self, g: int):
+        """(hop L, sources, staging) of hop group g (increasing hop order)."""
+        L, n, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._call("tvolap_batch_group_info", int(g), ctypes.byref(L), ctypes.byref(n),
+                   ctypes.byref(st))
+        return L.value, n.value, st.value
