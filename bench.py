@@ -263,6 +263,7 @@ def run_ours(args):
     if rank == 0 and not args.skip_extras and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(args, wl, budget_s=args.cpu_seconds,
                                            y_channel0=y[0].cpu().numpy())
+        out["accuracy_plain_mono"] = accuracy_plain_mono(dev)
     plan.close()
     if ws > 1:
         dist.destroy_process_group()
@@ -494,6 +495,7 @@ def run_adjoint(args):
         torch.cuda.synchronize(dev)
     plan.check()
     ms = t0e.elapsed_time(t1e) / args.steps
+    grad_acc = None if args.no_cpu else adjoint_accuracy(d, dP, dx, dX, plan, x, r)
     # the same step with segments of K blocks recomputed by the transform kernel
     for _ in range(2):
         step([], fused=False)
@@ -527,7 +529,33 @@ def run_adjoint(args):
                          "kernel": "k_adjoint_mac_x (read P, write dP; X recomputed)"},
             "mac_params_gbs": round(fwd_gbs, 1),
             "stages_ms": {k: round(v, 4) for k, v in tot.items()},
-            "peaks": kind, "clocks": clk.summary()}
+            "peaks": kind, "clocks": clk.summary(), "gradient_accuracy": grad_acc}
+
+
+def adjoint_accuracy(d, dP, dx, dX, plan, x, r, seed=5):
+    """Sampled gradient entries of the timed step against the oracle: 26
+    parameter entries and 8 input samples in each of 3 channels, each computed
+    on its own in FP64 from the definitions."""
+    import oracle
+    dx.zero_()
+    plan.adjoint_input(dX, 0, dx)                      # the step's input gradient
+    L, M, nb = d["L"], d["M"], d["n_blocks"]
+    rng = np.random.default_rng(seed)
+    C = d["x"].shape[0]
+    errs_p, errs_x = [], []
+    for c in sorted({0, C // 2, C - 1}):
+        idx = [(int(rng.integers(0, nb)), int(rng.integers(0, M)), int(rng.integers(0, 2 * L)))
+               for _ in range(24)] + [(nb - 1, M - 1, 5), (3, M - 1, 0)]
+        sidx = [int(v) for v in rng.integers(0, d["x"].shape[1], 6)] + [0, d["x"].shape[1] - 1]
+        sP, sx = oracle.params_grad_sampled(d["x"][c], d["P"][c], L, d["r"][c], idx, sidx)
+        gP = np.array([dP[c, t, m, k].item() for (t, m, k) in idx])
+        gx = dx[c, sidx].cpu().numpy()
+        peak = float(dP[c].abs().max())
+        errs_p.append(float(np.max(np.abs(gP - sP))) / peak)
+        errs_x.append(float(np.linalg.norm(gx - sx) / np.linalg.norm(sx)))
+    return {"dP_max_abs_over_peak": max(errs_p), "dx_rel_l2": max(errs_x),
+            "entries": "26 dP entries and 8 dx samples in each of 3 channels",
+            "tolerance": "1e-3 (gradients)"}
 
 
 # --------------------------------------------------------------------------- batched
@@ -930,6 +958,27 @@ def _oracle_sample(wl, n_samples, channel=0, start=None, values=False):
                               out_to_in=wl.out_to_in)
     dt = time.perf_counter() - t
     return (dt, y) if values else dt
+
+
+def accuracy_plain_mono(dev):
+    """The mono configuration (L = 128, 96000 samples, 4 responses of 4096 taps
+    switched every 16 blocks) through process_signal, against the FP64 oracle
+    over the whole signal."""
+    import torch
+    import oracle
+    from paper_2310_00319_gb300 import Plan
+    from synth import workloads as W
+    wl = W.plain_mono()
+    p = Plan(wl.L, wl.M, n_slots=wl.irs.shape[0], device=dev)
+    p.load_bank(0, torch.from_numpy(wl.irs).to(dev))
+    y = p.process_signal(torch.from_numpy(wl.x).to(dev), torch.from_numpy(wl.sched_a).to(dev),
+                         out_len=wl.out_len).cpu().numpy()
+    p.check()
+    p.close()
+    ref = oracle.tvolap_direct(wl.x, wl.irs, wl.L, wl.sched_a, out_len=wl.out_len)
+    out = accuracy(y, ref)
+    out["workload"] = "plain_mono_L128_N96000_ir4096 (whole signal)"
+    return out
 
 
 def accuracy(y, ref):

@@ -153,11 +153,18 @@ k_adjoint_mac_x(const float4 *__restrict__ G, int64_t g_first, int g_count,
         const bool active = q < q_end;
         const int64_t start = (q - 1) * (int64_t)L;     // block l = q - 1 starts at l*L
         const float *xc = x + (int64_t)c * x_stride;
-        auto src = [&](int n) {
+        const bool pairs = (reinterpret_cast<uintptr_t>(xc) & 7) == 0;
+        auto src = [&](int n) {      // as the forward transform kernel
             const int64_t i0 = start + n;
-            const float a = (i0 >= 0 && i0 < N) ? __ldg(xc + i0) : 0.f;
-            const float b = (i0 + 1 >= 0 && i0 + 1 < N) ? __ldg(xc + i0 + 1) : 0.f;
-            return make_float2(a * __ldg(win + n), b * __ldg(win + n + 1));
+            const float2 w = __ldg(reinterpret_cast<const float2 *>(win) + (n >> 1));
+            float2 v;
+            if (pairs && i0 >= 0 && i0 + 1 < N) {
+                v = __ldg(reinterpret_cast<const float2 *>(xc + i0));
+            } else {
+                v.x = (i0 >= 0 && i0 < N) ? __ldg(xc + i0) : 0.f;
+                v.y = (i0 + 1 >= 0 && i0 + 1 < N) ? __ldg(xc + i0 + 1) : 0.f;
+            }
+            return make_float2(v.x * w.x, v.y * w.y);
         };
         // the window, pre-rotation and FFT of forward_block (upper half zero)
         float2 z[8];

@@ -69,11 +69,19 @@ k_forward_signal(const float *__restrict__ x, int64_t N, int64_t x_stride, int L
     }
     const int64_t start = (t_first + t - 1) * (int64_t)L;   // block l = t - 1 starts at l*L
     const float *xc = x + c * x_stride;
+    // start and n are even: a pair is one 8-byte load when the row is 8-byte aligned
+    const bool pairs = (reinterpret_cast<uintptr_t>(xc) & 7) == 0;
     auto src = [&](int n) {
         const int64_t i0 = start + n;
-        const float a = (i0 >= 0 && i0 < N) ? __ldg(xc + i0) : 0.f;
-        const float b = (i0 + 1 >= 0 && i0 + 1 < N) ? __ldg(xc + i0 + 1) : 0.f;
-        return make_float2(a * __ldg(win + n), b * __ldg(win + n + 1));
+        const float2 w = __ldg(reinterpret_cast<const float2 *>(win) + (n >> 1));
+        float2 v;
+        if (pairs && i0 >= 0 && i0 + 1 < N) {
+            v = __ldg(reinterpret_cast<const float2 *>(xc + i0));
+        } else {
+            v.x = (i0 >= 0 && i0 < N) ? __ldg(xc + i0) : 0.f;
+            v.y = (i0 + 1 >= 0 && i0 + 1 < N) ? __ldg(xc + i0 + 1) : 0.f;
+        }
+        return make_float2(v.x * w.x, v.y * w.y);
     };
     float2 *Xo = X + g * P;
     forward_block<P>(A, B, j, active, src, rot, post, tw, [&](int k, float2 v) {
@@ -301,9 +309,14 @@ k_forward_stream(const float *__restrict__ in, float *__restrict__ hist, int L, 
     const bool active = c < n_in;
     const float *hc = hist + (int64_t)(active ? c : 0) * L;
     const float *ic = in + (int64_t)(active ? c : 0) * L;
+    // the history rows are 8-byte aligned; the caller's input may not be
+    const bool pairs = (reinterpret_cast<uintptr_t>(ic) & 7) == 0;
     auto src = [&](int n) {       // n even, so n and n + 1 lie on the same side of L
         const float *p = (n < L) ? (hc + n) : (ic + n - L);
-        return make_float2(p[0] * __ldg(win + n), p[1] * __ldg(win + n + 1));
+        const float2 v = (n < L || pairs) ? *reinterpret_cast<const float2 *>(p)
+                                          : make_float2(p[0], p[1]);
+        const float2 w = __ldg(reinterpret_cast<const float2 *>(win) + (n >> 1));
+        return make_float2(v.x * w.x, v.y * w.y);
     };
     float2 *Xo = ring + ((int64_t)(active ? c : 0) * R + slot) * P;
     forward_block<P>(A, B, j, active, src, rot, post, tw, [&](int k, float2 v) {

@@ -78,8 +78,9 @@ __device__ __forceinline__ void srv_forward_body(const SrvLaunch &a, int c, int 
         const float *hc = ds.hist;
         const float *ic = a.in + (int64_t)d.slot * a.io_stride;
         auto src = [&](int s) {      // s even: s and s + 1 lie on the same side of L
-            const float *p = (s < L) ? (hc + s) : (ic + s - L);
-            return make_float2(p[0] * __ldg(t.win + s), p[1] * __ldg(t.win + s + 1));
+            const float2 v = *reinterpret_cast<const float2 *>((s < L) ? (hc + s) : (ic + s - L));
+            const float2 w = __ldg(reinterpret_cast<const float2 *>(t.win) + (s >> 1));
+            return make_float2(v.x * w.x, v.y * w.y);
         };
         float2 *Xo = ds.ring + (int64_t)d.pos * P;
         forward_block<P>(A, B, j, active, src, t.rot, t.post, t.tw, [&](int k, float2 v) {
