@@ -1018,7 +1018,9 @@ def run_reference(args):
     wl = workload(args)
     probe = 128
     dt = _oracle_sample(wl, probe)
-    per_step = int(max(probe, probe * args.ref_step_seconds / max(dt, 1e-6)))
+    # every step a bounded sample: the whole run stays within about 150 s
+    step_s = min(args.ref_step_seconds, 150.0 / max(1, args.steps + args.warmup))
+    per_step = int(max(probe, probe * step_s / max(dt, 1e-6)))
     for _ in range(args.warmup):
         _oracle_sample(wl, per_step)
     total = 0.0
