@@ -80,6 +80,52 @@ def test_null_handle_calls(lib):
     assert lib.tvolap_process_block(None, None, None, None, None, None) == -4
 
 
+@pytest.mark.parametrize("args", [
+    (24, 64, 8, 2, 1 << 20),     # base hop not a power of two
+    (64, 32, 8, 2, 1 << 20),     # max hop below base hop
+    (16, 256, 8, 2, 1 << 20),    # more than 8 base hops per block
+    (64, 256, 0, 2, 1 << 20),    # no capacity
+    (64, 256, 8, 3, 1 << 20),    # more than two outputs
+])
+def test_server_create_rejects_bad_arguments_without_gpu(lib, args):
+    h = ctypes.c_void_p()
+    assert lib.tvolap_server_create(ctypes.byref(h), *args, None) == -1
+    assert not h.value
+
+
+class _BSrc(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("M", ctypes.c_int), ("n_filters", ctypes.c_int),
+                ("N", ctypes.c_int64), ("out_len", ctypes.c_int64)]
+
+
+@pytest.mark.parametrize("src", [
+    (48, 2, 1, 100, 100),        # hop not a power of two
+    (2048, 2, 1, 100, 100),      # hop too large
+    (64, 0, 1, 100, 100),        # no partitions
+    (64, 2, 0, 100, 100),        # no filters
+    (64, 2, 1, -1, 100),         # negative length
+])
+def test_batch_create_rejects_bad_sources_without_gpu(lib, src):
+    arr = (_BSrc * 2)(_BSrc(64, 2, 1, 100, 100), _BSrc(*src))
+    h = ctypes.c_void_p()
+    assert lib.tvolap_batch_create(ctypes.byref(h), arr, 2, None) == -1
+    assert not h.value
+    assert lib.tvolap_batch_create(ctypes.byref(h), arr, 0, None) == -1
+
+
+def test_null_handles_of_batch_server_and_adjoint(lib):
+    assert lib.tvolap_batch_destroy(None) == 0
+    assert lib.tvolap_server_destroy(None) == 0
+    assert lib.tvolap_batch_run(None) == -4
+    assert lib.tvolap_batch_check(None) == -4
+    assert lib.tvolap_server_tick(None) == -4
+    assert lib.tvolap_server_wait(None) == -4
+    assert lib.tvolap_adjoint_mac_x(None, None, 0, 0, None, 0, 0, None, 0, 0, 0, None, None,
+                                    0) == -4
+    assert lib.tvolap_process_ragged(None, None, 0, None, None, None, 0, None, None, None, 0,
+                                     None, 0) == -4
+
+
 def test_paper_op_counts_tables():
     """Section 3 arithmetic and Tables 1-2 (tests/golden/paper_tables.json)."""
     g = json.load(open(os.path.join(GOLDEN, "paper_tables.json")))
