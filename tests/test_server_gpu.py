@@ -262,3 +262,53 @@ def test_edge_streams():
     ref = _oracle_stream(t[1], 2)
     _assert_close(out.reshape(2, -1).astype(np.float64)[:, t[1].L:], ref, "after early retire")
     srv.close()
+
+
+def test_pipelined_ticks_equal_one_at_a_time():
+    """Two ticks in flight: due() hands out the staging set of the tick two
+    back (waiting for it), whose outputs are read before the set is refilled.
+    Results equal those of ticks run one at a time, bit for bit."""
+    dev = _dev()
+    S = W.serving_streams(48, 4, hops=(16, 32, 64), blocks=(20, 40))
+    srv = _server(dev)
+    ref = drive(srv, S, [0, 0, 0, 0], dev)
+    srv.close()
+
+    srv = _server(dev)
+    ids = [srv.admit(s.L, _irs(s, 2, dev)) for s in S]
+    srv.wait()
+    owner = {sid: i for i, sid in enumerate(ids)}
+    given = [0] * len(S)
+    outs = [np.zeros((2, s.n_blocks, s.L), np.float32) for s in S]
+    inflight = {}                       # staging set -> [(stream, block)] of its last tick
+    done = 0
+
+    def collect(buf):
+        for i, b in inflight.pop(buf, []):
+            outs[i][:, b, :] = srv.outs(buf)[ids[i], :2, :S[i].L]
+
+    for _ in range(100000):
+        if done == len(S):
+            break
+        due = srv.due()                 # waits for the tick that used this set
+        collect(srv.buf)
+        batch = []
+        for sid in due:
+            i = owner[int(sid)]
+            s, b = S[i], given[i]
+            srv.inp[sid, :s.L] = s.x[b * s.L:(b + 1) * s.L]
+            srv.sel[sid] = s.sel[b]
+            batch.append((i, b))
+            given[i] += 1
+        inflight[srv.buf] = batch
+        srv.tick()
+        for i, b in batch:
+            if b + 1 == S[i].n_blocks:
+                srv.retire(ids[i])      # its last block is enqueued; the slot is free later
+                done += 1
+    srv.wait()
+    for buf in list(inflight):
+        collect(buf)
+    srv.close()
+    for a, b in zip(ref, outs):
+        np.testing.assert_array_equal(a, b)
