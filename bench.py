@@ -112,7 +112,7 @@ class ClockSampler:
 
 def workload(args):
     from synth import workloads as W
-    return W.plain_at_scale(n_ch=args.channels, N=args.samples)
+    return W.plain_at_scale(n_ch=args.channels, N=args.samples, ir_len=args.ir_len)
 
 
 def mac_terms(nb: int, M: int) -> int:
@@ -156,6 +156,8 @@ def run_ours(args):
 
     plan = Plan(L, M, n_in=n_ch, n_out=wl.n_out, out_to_in=wl.out_to_in,
                 n_slots=wl.irs.shape[0], device=dev)
+    if args.staging is not None:
+        plan.set_option(1, args.staging)
     x = torch.from_numpy(wl.x).to(dev)
     irs = torch.from_numpy(wl.irs).to(dev)
     sa = torch.from_numpy(wl.sched_a).to(dev)
@@ -219,7 +221,7 @@ def run_ours(args):
     achieved = flops / (mac_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
     traffic = args.traffic
-    if traffic is None and args.channels == 64 and args.samples == 480000:
+    if traffic is None and args.channels == 64 and args.samples == 480000 and args.ir_len == 48000:
         traffic = MAC_TRAFFIC_BYTES
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
@@ -1052,6 +1054,8 @@ def main():
                     choices=["plain_at_scale", "adjoint", "batched", "serve"])
     ap.add_argument("--channels", type=int, default=64)
     ap.add_argument("--samples", type=int, default=480000)
+    ap.add_argument("--ir-len", type=int, default=48000,
+                    help="taps of the stored responses of the default workload")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the multiply-accumulate kernel")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -1063,7 +1067,8 @@ def main():
     ap.add_argument("--adj-channels", type=int, default=16,
                     help="adjoint: channels of the differentiable workload")
     ap.add_argument("--staging", type=int, default=None, choices=[0, 1, 2],
-                    help="batched: fixed multiply-accumulate staging instead of the autotuner")
+                    help="multiply-accumulate staging (default workload: instead of the default; "
+                         "batched: instead of the autotuner)")
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

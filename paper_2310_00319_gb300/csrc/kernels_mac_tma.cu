@@ -428,7 +428,8 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
     int T0;
     group_origin(p, grp, T0);
     if (T0 >= n_blocks) return;                        // whole CTA
-    if (*(volatile unsigned *)err & ERR_TIMEOUT) return;
+    // a copy wait of another CTA gave up: the whole CTA leaves (one decision for all threads)
+    if (__syncthreads_or(threadIdx.x == 0 && (*(volatile unsigned *)err & ERR_TIMEOUT))) return;
     GroupSmem<NSM> *gs = reinterpret_cast<GroupSmem<NSM> *>(smem_raw);
     float2 *xring = reinterpret_cast<float2 *>(smem_raw + 256);
     float2 *hst = reinterpret_cast<float2 *>(smem_raw + 256 + XRING * ROW_BYTES);
