@@ -51,12 +51,9 @@ struct tvolap_server {
     uint64_t seq = 0;                        // ticks enqueued
     tvolap_server_stats stats = {};
     std::vector<int> ids;                    // scratch
-    std::vector<SrvDue> due_tmp;
 };
 
 namespace {
-
-bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 int lg2(int v)
 {
@@ -71,12 +68,6 @@ int cuda_status(cudaError_t e)
     if (e == cudaErrorMemoryAllocation) return TVOLAP_ERR_OOM;
     return TVOLAP_ERR_CUDA;
 }
-
-#define SRV_TRY(expr)                                   \
-    do {                                                \
-        cudaError_t e_ = (expr);                        \
-        if (e_ != cudaSuccess) return cuda_status(e_);  \
-    } while (0)
 
 void release(tvolap_server *s)
 {
