@@ -52,10 +52,10 @@ def _peaks():
 # FP32 FMA peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops x clock.
 SMS, FP32_LANES = 152, 128
 
-# DRAM bytes (read + write) of one launch of the multiply-accumulate group kernel at the
-# default 64-channel workload: an ncu capture of the same kernel at 32 channels, scaled by
-# the channel count (the traffic grows in proportion to it).
-MAC_TRAFFIC_BYTES = 2 * (309.401088e6 + 212.599040e6)
+# DRAM bytes (read + write) of one launch of the persistent multiply-accumulate kernel at
+# the default 64-channel workload: an ncu capture of the same kernel at 32 channels, scaled
+# by the channel count (the traffic grows in proportion to it).
+MAC_TRAFFIC_BYTES = 2 * (309.679360e6 + 214.811648e6)
 
 
 def fp32_peak_tflops(mhz: float) -> float:
@@ -220,12 +220,15 @@ def run_ours(args):
     flops = mac_terms(nb, M) * P * wl.n_out * costmodel.mac_flops_per_block_bin_partition(True)
     achieved = flops / (mac_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    staging = 0 if args.staging is None else args.staging
     traffic = args.traffic
-    if traffic is None and args.channels == 64 and args.samples == 480000 and args.ir_len == 48000:
+    if (traffic is None and staging == 0 and args.channels == 64 and args.samples == 480000
+            and args.ir_len == 48000):
         traffic = MAC_TRAFFIC_BYTES
+    kernel = {0: "k_mac_signal_persist", 1: "k_mac_signal_lsu"}.get(staging, "k_mac_signal_group")
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": traffic, "kernel": "k_mac_signal_group",
+                "traffic": traffic, "kernel": kernel,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}
     # the transform stages are memory bound: algorithmic bytes / time vs measured HBM copy
     bytes_fwd = 4.0 * n_ch * N + 8.0 * P * n_ch * nb
@@ -1066,7 +1069,7 @@ def main():
                     help="serve: ticks of the latency run (throughput run: 3/4 of it)")
     ap.add_argument("--adj-channels", type=int, default=16,
                     help="adjoint: channels of the differentiable workload")
-    ap.add_argument("--staging", type=int, default=None, choices=[0, 1, 2],
+    ap.add_argument("--staging", type=int, default=None, choices=[0, 1, 2, 3, 4],
                     help="multiply-accumulate staging (default workload: instead of the default; "
                          "batched: instead of the autotuner)")
     ap.add_argument("--skip-extras", action="store_true")

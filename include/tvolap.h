@@ -342,12 +342,15 @@ TVOLAP_API int tvolap_process_signal_static(tvolap_t h, const float *x_dev, int6
 /* Options of tvolap_set_option. */
 typedef enum tvolap_option {
     /* Staging of the offline multiply-accumulate: 0 = tiled bulk tensor copies
-       (TMA) when the buffers allow it, else cp.async (default); 1 = always
-       cp.async; 2 = as 0, with up to four distinct filters staged per group of
-       64 consecutive blocks instead of three (for schedules that cycle four
-       filters; fewer resident groups per SM). 0 and 1 give identical results;
-       2 differs from them only in the rounding of blocks whose group holds
-       four filters. */
+       (TMA) when the buffers allow it, else cp.async (default): resident CTAs
+       take groups of 64 consecutive blocks from a work counter, staging up to
+       three distinct filters per group; 1 = always cp.async; 2 = TMA, one
+       group per CTA, up to four distinct filters per group (for schedules that
+       cycle four filters; fewer resident groups per SM); 3 = TMA, one group
+       per CTA, up to three filters; 4 = as 3 with two adjacent bins per thread
+       when 2L is a multiple of 64 (fastest for slowly changing filters).
+       0, 1, 3 and 4 give identical results; 2 differs from them only in the
+       rounding of blocks whose group holds four filters. */
     TVOLAP_OPT_MAC_STAGING = 1
 } tvolap_option;
 
@@ -432,7 +435,7 @@ TVOLAP_API int tvolap_batch_run(tvolap_batch_t b);
 TVOLAP_API int tvolap_batch_capture(tvolap_batch_t b);
 
 /*
- * For every hop group, time each multiply-accumulate staging (0, 1, 2) over
+ * For every hop group, time each multiply-accumulate staging (0 .. 4) over
  * reps runs on the batch itself and keep the fastest; drops a captured graph.
  * chosen (may be NULL): host int [number of groups], the staging per group in
  * increasing hop order. Synchronises.

@@ -105,7 +105,7 @@ namespace tvolap {
 cudaError_t ensure_overflow(tvolap_plan *h, int64_t entries)
 {
     if (!h->ovf_count) {
-        cudaError_t e = cudaMalloc(&h->ovf_count, sizeof(int));
+        cudaError_t e = cudaMalloc(&h->ovf_count, 2 * sizeof(int));
         if (e != cudaSuccess) return e;
     }
     if (entries <= h->ovf_cap) return cudaSuccess;
@@ -515,7 +515,7 @@ int tvolap_set_option(tvolap_t h, int option, int value)
 {
     if (!h) return TVOLAP_ERR_STATE;
     if (option == TVOLAP_OPT_MAC_STAGING) {
-        if (value < 0 || value > 2) return TVOLAP_ERR_ARG;
+        if (value < 0 || value > 4) return TVOLAP_ERR_ARG;
         h->mac_variant = value;
         return TVOLAP_OK;
     }

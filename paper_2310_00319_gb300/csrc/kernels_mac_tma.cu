@@ -318,7 +318,7 @@ k_mac_overflow_tma(const __grid_constant__ CUtensorMap xmap, const __grid_consta
 // Group kernel. The 4 consumer warps of a CTA take the 4 runs of a group; a
 // fifth warp only loads. Two facts make the loads cheap:
 //  * all four runs of a group share the group's slots, so one copy of each
-//    slot's rows serves four runs (groups mixing more than MAX_NS slots go to
+//    slot's rows serves four runs (groups mixing more than NSM slots go to
 //    the overflow list and the per-warp kernel);
 //  * the runs are consecutive, so the X rows warp w needs at chunk c + 1 are
 //    the rows warp w - 1 used at chunk c: every chunk brings only 8 new X rows.
@@ -328,15 +328,21 @@ k_mac_overflow_tma(const __grid_constant__ CUtensorMap xmap, const __grid_consta
 // release a stage on its 'empty' barrier. Rows before block 0 and partitions
 // at or past M arrive as zeros, so a chunk always runs all D steps: the extra
 // products are exact zeros.
+// BPL: adjacent bins per lane (1 or 2); a CTA covers 32 * BPL bins. Two bins
+// per lane give each warp two independent bins per step under one set of
+// weights and halve the per-CTA costs (census, barriers, window, run set-up)
+// per unit of work; each bin's arithmetic is the same either way.
 constexpr int NSTAGE = 3;
 constexpr int XRING = 64;                             // rows; chunk c writes slots [-8c, -8c+8) mod 64
 // NSM: most distinct slots a group may stage (3, or 4 for schedules cycling
 // four filters); groups with more go to the overflow list.
-template <int NSM>
+template <int NSM, int BPL>
 struct GroupGeo {
+    static constexpr int ROWB = 32 * BPL;              // float2 per staged row
     static constexpr int HSTAGE_ROWS = NSM * TMA_D;
-    static constexpr int BYTES = 256 + XRING * ROW_BYTES + NSTAGE * HSTAGE_ROWS * ROW_BYTES;
-    static constexpr int MIN_CTAS = NSM <= 3 ? 4 : 3;  // CTAs per SM the registers must allow
+    static constexpr int BYTES = 256 + (XRING + NSTAGE * HSTAGE_ROWS) * ROW_BYTES * BPL;
+    // CTAs per SM the registers must allow
+    static constexpr int MIN_CTAS = BPL == 2 ? (NSM <= 3 ? 3 : 2) : (NSM <= 3 ? 4 : 3);
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
@@ -354,48 +360,64 @@ static_assert(sizeof(GroupSmem<4>) <= 256, "group header must fit its 256 bytes"
 
 __device__ __forceinline__ int ring_slot(int j) { return j & (XRING - 1); }
 
-template <int NS, int NSM>
-__device__ __forceinline__ void group_chunk(const float2 *xs, const float2 *const (&hb)[NSM],
-                                            int c, const RunSlots<TMA_R, NSM> &rs,
-                                            float2 (&xw)[TMA_R], float2 (&acc)[TMA_R])
+// the lane's BPL adjacent bins of one staged row
+template <int BPL>
+__device__ __forceinline__ void ld_bins(const float2 *p, float2 (&v)[BPL])
 {
-    constexpr int D = TMA_D, R = TMA_R;
-#pragma unroll
-    for (int u = 0; u < D; ++u) {
-        if (c > 0 || u > 0) xw[(R - u) % R] = xs[(D - 1 - u) * 32];   // X(tf - 2m) enters
-        float2 hs[NS > 1 ? NS - 1 : 1];
-#pragma unroll
-        for (int j = 1; j < NS; ++j) hs[j - 1] = hb[j][u * 32];
-        run_step<R, NS, NSM>(acc, xw, hb[0][u * 32], hs, rs.w, u);
+    if constexpr (BPL == 2) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = make_float2(q.x, q.y);
+        v[1] = make_float2(q.z, q.w);
+    } else {
+        v[0] = *p;
     }
 }
 
-template <int NS, int NSM>
+template <int NS, int NSM, int BPL>
+__device__ __forceinline__ void group_chunk(const float2 *xs, const float2 *const (&hb)[NSM],
+                                            int c, const RunSlots<TMA_R, NSM> &rs,
+                                            float2 (&xw)[TMA_R][BPL], float2 (&acc)[TMA_R][BPL])
+{
+    constexpr int D = TMA_D, R = TMA_R, ROWB = 32 * BPL;
+#pragma unroll
+    for (int u = 0; u < D; ++u) {
+        if (c > 0 || u > 0) ld_bins<BPL>(xs + (D - 1 - u) * ROWB, xw[(R - u) % R]);   // X(tf - 2m) enters
+        float2 h0[BPL];
+        float2 hs[NS > 1 ? NS - 1 : 1][BPL];
+        ld_bins<BPL>(hb[0] + u * ROWB, h0);
+#pragma unroll
+        for (int j = 1; j < NS; ++j) ld_bins<BPL>(hb[j] + u * ROWB, hs[j - 1]);
+        run_step_bins<R, NS, NSM, BPL>(acc, xw, h0, hs, rs.w, u);
+    }
+}
+
+template <int NS, int NSM, int BPL>
 __device__ __forceinline__ bool group_consume(GroupSmem<NSM> *gs, const float2 *xring,
                                               const float2 *hst, int w, int lane, int nchunks,
                                               int m_end, const RunSlots<TMA_R, NSM> &rs,
-                                              const int (&idx)[NSM], float2 (&acc)[TMA_R])
+                                              const int (&idx)[NSM], float2 (&acc)[TMA_R][BPL])
 {
-    constexpr int D = TMA_D, R = TMA_R;
-    float2 xw[R];
+    constexpr int D = TMA_D, R = TMA_R, ROWB = 32 * BPL;
+    float2 xw[R][BPL];
     // window rows i = 8w + r, r < R, at ring slots 8w + 7 + r (row 0 comes with chunk 0)
     if (!mbar_wait(gs->bar, 0u) || !mbar_wait(gs->bar + 1, 0u)) return false;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        xw[r] = xring[ring_slot(R * w + 7 + r) * 32 + lane];
-        acc[r] = make_float2(0.f, 0.f);
+        ld_bins<BPL>(xring + ring_slot(R * w + 7 + r) * ROWB + lane * BPL, xw[r]);
+#pragma unroll
+        for (int b = 0; b < BPL; ++b) acc[r][b] = make_float2(0.f, 0.f);
     }
     for (int c = 0; c < nchunks; ++c) {
         const int q = c % NSTAGE;
         if (c > 0 && !mbar_wait(gs->bar + 1 + q, (uint32_t)(c / NSTAGE) & 1u)) return false;
         if (c * D < m_end) {
             // rows i = 8w - 8c - u, u < 8: ring slots 8(w - c) .. 8(w - c) + 7, row 7 - u
-            const float2 *xs = xring + ring_slot(D * (w - c)) * 32 + lane;
-            const float2 *st = hst + q * GroupGeo<NSM>::HSTAGE_ROWS * 32 + lane;
+            const float2 *xs = xring + ring_slot(D * (w - c)) * ROWB + lane * BPL;
+            const float2 *st = hst + q * GroupGeo<NSM, BPL>::HSTAGE_ROWS * ROWB + lane * BPL;
             const float2 *hb[NSM];
 #pragma unroll
-            for (int j = 0; j < NSM; ++j) hb[j] = st + idx[j] * D * 32;
-            group_chunk<NS, NSM>(xs, hb, c, rs, xw, acc);
+            for (int j = 0; j < NSM; ++j) hb[j] = st + idx[j] * D * ROWB;
+            group_chunk<NS, NSM, BPL>(xs, hb, c, rs, xw, acc);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(gs->bar + 1 + NSTAGE + q);
@@ -403,10 +425,11 @@ __device__ __forceinline__ bool group_consume(GroupSmem<NSM> *gs, const float2 *
     return true;
 }
 
-// grid: x = (group, parity) pairs, y = 32-bin tiles, z = output channels;
-// 4 consumer warps + 1 loader warp.
-template <int NSM>
-__global__ void __launch_bounds__(32 * (GW + 1), GroupGeo<NSM>::MIN_CTAS)
+// grid: x = (group, parity) pairs, y = (32 * BPL)-bin tiles, z = output
+// channels; 4 consumer warps + 1 loader warp. The tensor maps' boxes are
+// 32 * BPL bins wide.
+template <int NSM, int BPL>
+__global__ void __launch_bounds__(32 * (GW + 1), GroupGeo<NSM, BPL>::MIN_CTAS)
 k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap hmap,
                    int n_blocks, int M, int P, int n_slots_total, int null_slot,
                    const int32_t *__restrict__ out_to_in, const int32_t *__restrict__ sa,
@@ -415,7 +438,8 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
                    int4 *__restrict__ list, int *__restrict__ count, Ragged rg)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    constexpr int R = TMA_R, D = TMA_D;
+    constexpr int R = TMA_R, D = TMA_D, ROWB = 32 * BPL;
+    constexpr int RB = ROW_BYTES * BPL;                // bytes per staged row
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int p = blockIdx.x & 1, grp = blockIdx.x >> 1;
     const int64_t y_rows = n_blocks;                   // row stride of Y for every output
@@ -432,8 +456,8 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
     if (__syncthreads_or(threadIdx.x == 0 && (*(volatile unsigned *)err & ERR_TIMEOUT))) return;
     GroupSmem<NSM> *gs = reinterpret_cast<GroupSmem<NSM> *>(smem_raw);
     float2 *xring = reinterpret_cast<float2 *>(smem_raw + 256);
-    float2 *hst = reinterpret_cast<float2 *>(smem_raw + 256 + XRING * ROW_BYTES);
-    const int o = blockIdx.z, k0 = blockIdx.y * 32;
+    float2 *hst = reinterpret_cast<float2 *>(smem_raw + 256 + XRING * RB);
+    const int o = blockIdx.z, k0 = blockIdx.y * ROWB;
     const int32_t *ao = sa + (int64_t)o * sched_stride;
     const int32_t *bo = sb ? sb + (int64_t)o * sched_stride : nullptr;
     const float *alo = sal ? sal + (int64_t)o * sched_stride : nullptr;
@@ -481,7 +505,12 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
     }
     __syncthreads();
     if (gs->overflow) {
-        if (threadIdx.x == 0) list[atomicAdd(count, 1)] = make_int4(o, blockIdx.y, p, grp);
+        // the per-warp kernel takes 32-bin tiles
+        if (threadIdx.x == 0) {
+            const int e = atomicAdd(count, BPL);
+#pragma unroll
+            for (int b = 0; b < BPL; ++b) list[e + b] = make_int4(o, blockIdx.y * BPL + b, p, grp);
+        }
         return;
     }
     const int n_active = gs->n_active;
@@ -498,9 +527,9 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
         bool ok = true;
         if (lane == 0) {
             // window rows i = 1 .. 32 (ring slots 8 .. 39); row i = 0 comes with chunk 0
-            mbar_expect_tx(gs->bar, (uint32_t)(4 * D * ROW_BYTES));
+            mbar_expect_tx(gs->bar, (uint32_t)(4 * D * RB));
             for (int k = 0; k < 4; ++k)
-                tma_load_3d(xring + (8 + k * D) * 32, &xmap, k0, T0 + 2 + 2 * k * D, cin, gs->bar);
+                tma_load_3d(xring + (8 + k * D) * ROWB, &xmap, k0, T0 + 2 + 2 * k * D, cin, gs->bar);
         }
         for (int c = 0; c < nchunks && ok; ++c) {
             const int q = c % NSTAGE;
@@ -514,13 +543,13 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
             ppar = (ppar & ~(1u << q)) | ((uint32_t)(c / NSTAGE & 1) << q);
             if (lane == 0) {
                 uint64_t *bar = gs->bar + 1 + q;
-                mbar_expect_tx(bar, (uint32_t)((1 + U) * D * ROW_BYTES));
+                mbar_expect_tx(bar, (uint32_t)((1 + U) * D * RB));
                 // new X rows i = -8c - 7 .. -8c (blocks T0 - 16c - 14 .. T0 - 16c)
-                tma_load_3d(xring + ring_slot(-D * c) * 32, &xmap, k0, T0 - 2 * D * c - 2 * (D - 1),
+                tma_load_3d(xring + ring_slot(-D * c) * ROWB, &xmap, k0, T0 - 2 * D * c - 2 * (D - 1),
                             cin, bar);
                 for (int j = 0; j < U; ++j)
-                    tma_load_3d(hst + (q * GroupGeo<NSM>::HSTAGE_ROWS + j * D) * 32, &hmap, k0, c * D,
-                                gs->slot[j], bar);
+                    tma_load_3d(hst + (q * GroupGeo<NSM, BPL>::HSTAGE_ROWS + j * D) * ROWB, &hmap, k0,
+                                c * D, gs->slot[j], bar);
             }
         }
         if (!ok) {
@@ -546,26 +575,413 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
     }
     int m_end = (tf + 2 * (R - 1)) / 2 + 1;
     if (m_end > M) m_end = M;
-    float2 acc[R];
+    float2 acc[R][BPL];
     bool ok;
     if (rs.ns == 1)
-        ok = group_consume<1, NSM>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
+        ok = group_consume<1, NSM, BPL>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
     else if (rs.ns == 2)
-        ok = group_consume<2, NSM>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
+        ok = group_consume<2, NSM, BPL>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
     else if (NSM == 3 || rs.ns == 3)
-        ok = group_consume<3, NSM>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
+        ok = group_consume<3, NSM, BPL>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
     else
-        ok = group_consume<NSM, NSM>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
+        ok = group_consume<NSM, NSM, BPL>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
     if (!ok) {
         if (lane == 0) atomicOr(err, ERR_TIMEOUT);
         return;
     }
-    float2 *Yo = Y + (int64_t)o * y_rows * P + k0 + lane;
+    float2 *Yo = Y + (int64_t)o * y_rows * P + k0 + lane * BPL;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int t = tf + 2 * r;
-        if (t < n_blocks) Yo[(int64_t)t * P] = acc[r];
+        if (t < n_blocks) {
+            if constexpr (BPL == 2)
+                *reinterpret_cast<float4 *>(Yo + (int64_t)t * P) =
+                    make_float4(acc[r][0].x, acc[r][0].y, acc[r][1].x, acc[r][1].y);
+            else
+                Yo[(int64_t)t * P] = acc[r][0];
+        }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent group kernel: the same groups, runs and chunks as
+// k_mac_signal_group, but each CTA takes group after group from a work
+// counter, so a group's first copies are issued while the CTA still computes
+// the previous group. Two group contexts alternate: each has its half of a
+// two-part X ring, its window barrier and the group's description (output,
+// tile, slots, and the 32 blocks' schedule entries, so the consumers set up
+// their runs from shared memory). The filter stages and their full/empty
+// barriers are shared and run on through the groups; with PSTAGE stages the
+// loader keeps up to PSTAGE chunks in flight. The loader fills context k for
+// group i as soon as the consumers have released it (group i - 2 done:
+// barrier 'freed'), publishes it ('ready'), issues its window, then its chunks
+// as stages come free; the next group's work index and schedule entries are
+// fetched while the current group's chunks are issued. Consumer warps without
+// a run in a group (past the output's last block) still take part in every
+// chunk's barriers, so the empty barriers always count four arrivals.
+//
+// X ring halves: row i of a group (block T0 + 2i) sits at slot (i + 7) mod
+// PRING. Chunks 0 .. PSTAGE-1 of a group may land before the group's window
+// has been read into registers, so they must miss the window's slots 8..39:
+// chunk c writes slots -8c .. -8c + 7 (mod PRING), hence PRING >= 8 (PSTAGE + 4);
+// later chunks wait for chunk c - PSTAGE to be released, after which the
+// rows still to be read span 24 + 8 PSTAGE slots, which that bound also covers.
+
+struct PersistCtx {
+    int T0, o, k0, cin, n_blocks, M, nchunks, n_active, U, end;
+    int slot[4];
+    int a[GROUP_ROWS], b[GROUP_ROWS];          // checked schedule entries of blocks T0 + 2i
+    float al[GROUP_ROWS];
+};
+
+struct PersistSmem {
+    uint64_t win[2], ready[2], freed[2], full[5], empty[5];
+    PersistCtx ctx[2];
+};
+constexpr int PERSIST_HEAD = 1024;
+static_assert(sizeof(PersistSmem) <= PERSIST_HEAD, "persistent header must fit its bytes");
+
+// PST filter stages (at most 5: the barrier arrays), ring halves of PRING rows.
+template <int NSM, int BPL, int PST>
+struct PersistGeo {
+    static_assert(PST >= 2 && PST <= 5, "stages");
+    static constexpr int ROWB = 32 * BPL;
+    static constexpr int PSTAGE = PST;
+    static constexpr int PRING = PST <= 4 ? 64 : 8 * (PST + 4);   // >= 8 (PST + 4)
+    static constexpr int HSTAGE_ROWS = NSM * TMA_D;
+    static constexpr int BYTES = PERSIST_HEAD + (2 * PRING + PSTAGE * HSTAGE_ROWS) * ROW_BYTES * BPL;
+};
+
+template <int N>
+__device__ __forceinline__ int pring_slot(int j)
+{
+    const int s = j % N;
+    return s < 0 ? s + N : s;
+}
+
+// One group for a consumer warp: chunk loop over the shared stages (seq: the
+// CTA's running chunk count). m_end = 0 for a warp without a run: it only
+// keeps the barriers' count.
+template <int NS, int NSM, int BPL, int PST>
+__device__ __forceinline__ bool persist_consume(PersistSmem *ps, const float2 *xring, const float2 *hst,
+                                                int w, int lane, int nchunks, int m_end, uint32_t &seq,
+                                                const RunSlots<TMA_R, NSM> &rs, const int (&idx)[NSM],
+                                                float2 (&acc)[TMA_R][BPL])
+{
+    using G = PersistGeo<NSM, BPL, PST>;
+    constexpr int D = TMA_D, R = TMA_R, ROWB = 32 * BPL, NST = PST;
+    float2 xw[R][BPL];
+    {
+        const int q = seq % NST;
+        if (!mbar_wait(&ps->full[q], (seq / NST) & 1u)) return false;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        ld_bins<BPL>(xring + pring_slot<G::PRING>(R * w + 7 + r) * ROWB + lane * BPL, xw[r]);
+#pragma unroll
+        for (int b = 0; b < BPL; ++b) acc[r][b] = make_float2(0.f, 0.f);
+    }
+    for (int c = 0; c < nchunks; ++c, ++seq) {
+        const int q = seq % NST;
+        if (c > 0 && !mbar_wait(&ps->full[q], (seq / NST) & 1u)) return false;
+        if (c * D < m_end) {
+            const float2 *xs = xring + pring_slot<G::PRING>(D * (w - c)) * ROWB + lane * BPL;
+            const float2 *st = hst + q * G::HSTAGE_ROWS * ROWB + lane * BPL;
+            const float2 *hb[NSM];
+#pragma unroll
+            for (int j = 0; j < NSM; ++j) hb[j] = st + idx[j] * D * ROWB;
+            group_chunk<NS, NSM, BPL>(xs, hb, c, rs, xw, acc);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ps->empty[q]);
+    }
+    return true;
+}
+
+// A work item (output o, bin tile, parity, group) and the raw schedule entries
+// of its 32 blocks (lane i: block T0 + 2i), loaded ahead of use.
+struct PersistItem {
+    int id, o, tile, p, grp, T0, nb, M;
+    int a, b;
+    float al;
+};
+
+template <int NSM, int BPL, int PST, int MINB>
+__global__ void __launch_bounds__(32 * (GW + 1), MINB)
+k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap hmap,
+                     int n_blocks, int M, int P, int n_slots_total, int null_slot,
+                     const int32_t *__restrict__ out_to_in, const int32_t *__restrict__ sa,
+                     const int32_t *__restrict__ sb, const float *__restrict__ sal,
+                     int64_t sched_stride, float2 *__restrict__ Y, unsigned *err,
+                     int4 *__restrict__ list, int *__restrict__ count, int n_items, Ragged rg)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    using G = PersistGeo<NSM, BPL, PST>;
+    constexpr int R = TMA_R, D = TMA_D, ROWB = 32 * BPL, NST = PST;
+    constexpr int RB = ROW_BYTES * BPL;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    PersistSmem *ps = reinterpret_cast<PersistSmem *>(smem_raw);
+    float2 *xring = reinterpret_cast<float2 *>(smem_raw + PERSIST_HEAD);
+    float2 *hst = xring + 2 * G::PRING * ROWB;
+    const int groups2 = 2 * (((n_blocks + 1) / 2 + GROUP_ROWS - 1) / GROUP_ROWS);
+    const int tiles = P / ROWB;
+    const int64_t y_rows = n_blocks;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&ps->win[k], 1);
+            mbar_init(&ps->ready[k], 1);
+            mbar_init(&ps->freed[k], GW);
+        }
+        for (int q = 0; q < NST; ++q) {
+            mbar_init(&ps->full[q], 1);
+            mbar_init(&ps->empty[q], GW);
+        }
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    if (w == GW) {                                     // ---- loader
+        // next work index (uniform); stops once a wait anywhere gave up
+        // work indices come from a counter, one request kept in flight (lane 0)
+        // so that its latency hides behind a group; none once a wait anywhere
+        // gave up
+        int pend = lane == 0 ? atomicAdd(count + 1, 1) : 0;
+        auto fetch = [&]() {
+            int v = __shfl_sync(0xffffffffu, pend, 0);
+            if (lane == 0) pend = atomicAdd(count + 1, 1);
+            if (*(volatile unsigned *)err & ERR_TIMEOUT) v = n_items;
+            return v;
+        };
+        // decode item id and start loading its blocks' schedule entries
+        auto prefetch = [&](int id, PersistItem &I) {
+            I.id = id;
+            if (id >= n_items) return;
+            const int x = id % groups2, rest = id / groups2;
+            I.tile = rest % tiles;
+            I.o = rest / tiles;
+            I.p = x & 1;
+            I.grp = x >> 1;
+            group_origin(I.p, I.grp, I.T0);
+            I.nb = n_blocks;
+            I.M = M;
+            if (rg.out_len) {
+                const int64_t bo_ = blocks_of(rg.out_len[I.o], P / 2);
+                if (bo_ < n_blocks) I.nb = (int)bo_;
+                const int po = rg.parts[I.o];
+                I.M = po < 1 ? 1 : (po < M ? po : M);
+            }
+            const int t = I.T0 + 2 * lane;
+            const int64_t off = (int64_t)I.o * sched_stride + t;
+            I.a = 0;
+            I.b = 0;
+            I.al = 0.f;
+            if (t < I.nb) {
+                I.a = __ldg(sa + off);
+                I.b = sb ? __ldg(sb + off) : I.a;
+                I.al = sal ? __ldg(sal + off) : 0.f;
+            }
+        };
+        uint32_t seq = 0, filled = 0, ppar = 0, wdone = 0, wpar = 0;
+        bool ok = true;
+        PersistItem I;
+        prefetch(fetch(), I);
+        for (int it = 0;; ++it) {
+            const int k = it & 1;
+            if (it >= 2 && !(ok = mbar_wait(&ps->freed[k], (uint32_t)((it >> 1) - 1) & 1u))) break;
+            PersistCtx &cx = ps->ctx[k];
+            // the next item with work that fits the staging (others: skipped or listed)
+            bool found = false;
+            int U = 0, a = 0, b = 0;
+            float al = 0.f;
+            while (I.id < n_items) {
+                if (I.T0 >= I.nb) {
+                    prefetch(fetch(), I);
+                    continue;
+                }
+                const int t = I.T0 + 2 * lane;
+                bool va = false, vb = false;
+                a = b = 0;
+                al = 0.f;
+                if (t < I.nb) {
+                    a = checked_slot(I.a, n_slots_total, null_slot, err);
+                    b = sb ? checked_slot(I.b, n_slots_total, null_slot, err) : a;
+                    al = I.al;
+                    va = (al != 1.f) || (a == b);
+                    vb = (al != 0.f) && (b != a);
+                }
+                // rows past the output's last block repeat its last valid entry
+                const int last = (I.nb - 1 - I.T0) / 2 < 31 ? (I.nb - 1 - I.T0) / 2 : 31;
+                a = __shfl_sync(0xffffffffu, a, lane < last ? lane : last);
+                b = __shfl_sync(0xffffffffu, b, lane < last ? lane : last);
+                al = __shfl_sync(0xffffffffu, al, lane < last ? lane : last);
+                U = 0;
+                int ovf = 0;
+                for (int i = 0; i <= NSM; ++i) {
+                    const unsigned ma = __ballot_sync(0xffffffffu, va), mb = __ballot_sync(0xffffffffu, vb);
+                    if (!ma && !mb) break;
+                    const int v = ma ? __shfl_sync(0xffffffffu, a, __ffs(ma) - 1)
+                                     : __shfl_sync(0xffffffffu, b, __ffs(mb) - 1);
+                    if (U == NSM) {
+                        ovf = 1;
+                        break;
+                    }
+                    if (lane == 0) cx.slot[U] = v;
+                    ++U;
+                    va = va && (a != v);
+                    vb = vb && (b != v);
+                }
+                if (ovf) {
+                    // the per-warp kernel takes 32-bin tiles
+                    if (lane == 0) {
+                        const int e = atomicAdd(count, BPL);
+#pragma unroll
+                        for (int bb = 0; bb < BPL; ++bb) list[e + bb] = make_int4(I.o, I.tile * BPL + bb, I.p, I.grp);
+                    }
+                    prefetch(fetch(), I);
+                    continue;
+                }
+                found = true;
+                break;
+            }
+            if (!found) {
+                if (lane == 0) {
+                    cx.end = 1;
+                    mbar_arrive(&ps->ready[k]);
+                }
+                break;
+            }
+            const PersistItem cur = I;
+            int n_active = (cur.nb - cur.T0 + 2 * R - 1) / (2 * R);
+            if (n_active > GW) n_active = GW;
+            const int t_last = cur.T0 + 2 * R * (n_active - 1);
+            int m_all = (t_last + 2 * (R - 1)) / 2 + 1;
+            if (m_all > cur.M) m_all = cur.M;
+            const int nchunks = (m_all + D - 1) / D;
+            const int k0 = cur.tile * ROWB, cin = out_to_in[cur.o];
+            cx.a[lane] = a;
+            cx.b[lane] = b;
+            cx.al[lane] = al;
+            if (lane == 0) {
+                cx.T0 = cur.T0;
+                cx.o = cur.o;
+                cx.k0 = k0;
+                cx.cin = cin;
+                cx.n_blocks = cur.nb;
+                cx.M = cur.M;
+                cx.nchunks = nchunks;
+                cx.n_active = n_active;
+                cx.U = U;
+                cx.end = 0;
+            }
+            __syncwarp();
+            float2 *half = xring + k * G::PRING * ROWB;
+            if (lane == 0) {
+                mbar_arrive(&ps->ready[k]);
+                // window rows i = 1 .. 32 (ring slots 8 .. 39); row i = 0 comes with chunk 0
+                mbar_expect_tx(&ps->win[k], (uint32_t)(4 * D * RB));
+                for (int kk = 0; kk < 4; ++kk)
+                    tma_load_3d(half + (8 + kk * D) * ROWB, &xmap, k0, cur.T0 + 2 + 2 * kk * D, cin, &ps->win[k]);
+            }
+            wdone |= 1u << k;
+            wpar = (wpar & ~(1u << k)) | (((uint32_t)(it >> 1) & 1u) << k);
+            prefetch(fetch(), I);                      // the next item's schedule entries load meanwhile
+            for (int c = 0; c < nchunks; ++c, ++seq) {
+                const int q = seq % NST;
+                // stage q last held chunk seq - NST
+                if (seq >= NST && !(ok = mbar_wait(&ps->empty[q], ((seq - NST) / NST) & 1u))) break;
+                filled |= 1u << q;
+                ppar = (ppar & ~(1u << q)) | (((seq / NST) & 1u) << q);
+                if (lane == 0) {
+                    uint64_t *bar = &ps->full[q];
+                    mbar_expect_tx(bar, (uint32_t)((1 + U) * D * RB));
+                    // new X rows i = -8c - 7 .. -8c, then the group's slots' rows
+                    tma_load_3d(half + pring_slot<G::PRING>(-D * c) * ROWB, &xmap, k0,
+                                cur.T0 - 2 * D * c - 2 * (D - 1), cin, bar);
+                    for (int j = 0; j < U; ++j)
+                        tma_load_3d(hst + (q * G::HSTAGE_ROWS + j * D) * ROWB, &hmap, k0, c * D, cx.slot[j], bar);
+                }
+            }
+            if (!ok) break;
+        }
+        if (!ok) {
+            // a wait gave up: report it and give the copies this warp issued a
+            // bounded chance to land before the CTA's shared memory is released
+            // (the consumers' own waits end by their bounds)
+            if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+            for (int kk = 0; kk < 2; ++kk)
+                if (wdone & (1u << kk)) mbar_wait(&ps->win[kk], (wpar >> kk) & 1u);
+            for (int q = 0; q < NST; ++q)
+                if (filled & (1u << q)) mbar_wait(&ps->full[q], (ppar >> q) & 1u);
+        }
+        return;
+    }
+
+    // ---- consumers
+    uint32_t seq = 0;
+    for (int it = 0;; ++it) {
+        const int k = it & 1;
+        const uint32_t use = (uint32_t)(it >> 1) & 1u;
+        if (!mbar_wait(&ps->ready[k], use)) break;
+        const PersistCtx &cx = ps->ctx[k];
+        if (cx.end) return;
+        const int T0 = cx.T0, nb_o = cx.n_blocks, nchunks = cx.nchunks, U = cx.U;
+        const int tf = T0 + 2 * R * w;
+        const bool active = w < cx.n_active;
+        RunSlots<R, NSM> rs;
+        {
+            int a[R], b[R];
+            float al[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                a[r] = cx.a[R * w + r];
+                b[r] = cx.b[R * w + r];
+                al[r] = cx.al[R * w + r];
+            }
+            run_slots_core<R, NSM>(a, b, al, rs);
+        }
+        int idx[NSM];
+#pragma unroll
+        for (int j = 0; j < NSM; ++j) {
+            idx[j] = 0;
+            for (int q = 0; q < U; ++q)
+                if (j < rs.ns && cx.slot[q] == rs.sl[j]) idx[j] = q;
+        }
+        int m_end = 0;
+        if (active) {
+            m_end = (tf + 2 * (R - 1)) / 2 + 1;
+            if (m_end > cx.M) m_end = cx.M;
+        }
+        if (!mbar_wait(&ps->win[k], use)) break;
+        const float2 *half = xring + k * G::PRING * ROWB;
+        float2 acc[R][BPL];
+        bool ok;
+        if (!active || rs.ns == 1)
+            ok = persist_consume<1, NSM, BPL, PST>(ps, half, hst, w, lane, nchunks, m_end, seq, rs, idx, acc);
+        else if (rs.ns == 2)
+            ok = persist_consume<2, NSM, BPL, PST>(ps, half, hst, w, lane, nchunks, m_end, seq, rs, idx, acc);
+        else if (NSM == 3 || rs.ns == 3)
+            ok = persist_consume<3, NSM, BPL, PST>(ps, half, hst, w, lane, nchunks, m_end, seq, rs, idx, acc);
+        else
+            ok = persist_consume<NSM, NSM, BPL, PST>(ps, half, hst, w, lane, nchunks, m_end, seq, rs, idx, acc);
+        if (!ok) break;
+        if (active) {
+            float2 *Yo = Y + (int64_t)cx.o * y_rows * P + cx.k0 + lane * BPL;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int t = tf + 2 * r;
+                if (t < nb_o) {
+                    if constexpr (BPL == 2)
+                        *reinterpret_cast<float4 *>(Yo + (int64_t)t * P) =
+                            make_float4(acc[r][0].x, acc[r][0].y, acc[r][1].x, acc[r][1].y);
+                    else
+                        Yo[(int64_t)t * P] = acc[r][0];
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ps->freed[k]);
+    }
+    if (lane == 0) atomicOr(err, ERR_TIMEOUT);         // only a wait that gave up gets here
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -589,15 +1005,15 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// 3-D map over [dim2][dim1][P] spectra (8-byte elements), box 32 bins x rows.
+// 3-D map over [dim2][dim1][P] spectra (8-byte elements), box box_bins bins x rows.
 bool encode_spectra(CUtensorMap *map, const void *base, int P, int64_t dim1, int64_t dim2,
-                    int box_rows, int row_stride)
+                    int box_rows, int row_stride, int box_bins = 32)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
     cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)dim1, (cuuint64_t)dim2};
     cuuint64_t strides[2] = {(cuuint64_t)P * 8, (cuuint64_t)P * 8 * (cuuint64_t)dim1};
-    cuuint32_t box[3] = {32, (cuuint32_t)(box_rows * row_stride), 1};
+    cuuint32_t box[3] = {(cuuint32_t)box_bins, (cuuint32_t)(box_rows * row_stride), 1};
     cuuint32_t estr[3] = {1, (cuuint32_t)row_stride, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<void *>(base), dims, strides,
                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -605,20 +1021,56 @@ bool encode_spectra(CUtensorMap *map, const void *base, int P, int64_t dim1, int
     return r == CUDA_SUCCESS;
 }
 
-template <int NSM>
-cudaError_t launch_group(dim3 grid, const CUtensorMap &xrun, const CUtensorMap &hmap,
-                         tvolap_plan *h, int n_blocks, const int32_t *sa, const int32_t *sb,
-                         const float *sal, int64_t sched_stride, float2 *Y, Ragged rg)
+template <int NSM, int BPL>
+cudaError_t launch_group(const float2 *X, int n_blocks, tvolap_plan *h, int groups,
+                         const int32_t *sa, const int32_t *sb, const float *sal,
+                         int64_t sched_stride, float2 *Y, Ragged rg)
 {
-    const size_t gsmem = GroupGeo<NSM>::BYTES;
+    CUtensorMap xmap, hmap;
+    if (!encode_spectra(&xmap, X, h->P, n_blocks, h->n_in, TMA_D, 2, 32 * BPL) ||
+        !encode_spectra(&hmap, h->bank, h->P, h->M, h->n_slots_total + 1, TMA_D, 1, 32 * BPL))
+        return cudaErrorInvalidValue;
+    const size_t gsmem = GroupGeo<NSM, BPL>::BYTES;
     if (gsmem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_mac_signal_group<NSM>,
+        cudaError_t e = cudaFuncSetAttribute(k_mac_signal_group<NSM, BPL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
         if (e != cudaSuccess) return e;
     }
-    k_mac_signal_group<NSM><<<grid, 32 * (GW + 1), gsmem, h->stream>>>(
-        xrun, hmap, n_blocks, h->M, h->P, h->n_slots_total, h->null_slot, h->out_to_in, sa, sb,
+    dim3 grid((unsigned)(2 * groups), (unsigned)(h->P / (32 * BPL)), (unsigned)h->n_out);
+    k_mac_signal_group<NSM, BPL><<<grid, 32 * (GW + 1), gsmem, h->stream>>>(
+        xmap, hmap, n_blocks, h->M, h->P, h->n_slots_total, h->null_slot, h->out_to_in, sa, sb,
         sal, sched_stride, Y, h->err, h->ovf_list, h->ovf_count, rg);
+    return cudaGetLastError();
+}
+
+template <int NSM, int BPL, int PST, int MINB>
+cudaError_t launch_persist(const float2 *X, int n_blocks, tvolap_plan *h, int groups,
+                           const int32_t *sa, const int32_t *sb, const float *sal,
+                           int64_t sched_stride, float2 *Y, Ragged rg)
+{
+    CUtensorMap xmap, hmap;
+    if (!encode_spectra(&xmap, X, h->P, n_blocks, h->n_in, TMA_D, 2, 32 * BPL) ||
+        !encode_spectra(&hmap, h->bank, h->P, h->M, h->n_slots_total + 1, TMA_D, 1, 32 * BPL))
+        return cudaErrorInvalidValue;
+    const int smem = PersistGeo<NSM, BPL, PST>::BYTES;
+    static int per_sm = 0;                       // resident CTAs per SM (same for every device here)
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_mac_signal_persist<NSM, BPL, PST, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mac_signal_persist<NSM, BPL, PST, MINB>,
+                                                          32 * (GW + 1), smem);
+        if (e != cudaSuccess) return e;
+        per_sm = n > 0 ? n : 1;
+    }
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    const int64_t n_items = (int64_t)2 * groups * (h->P / (32 * BPL)) * h->n_out;
+    const int64_t grid = n_items < (int64_t)per_sm * sms ? n_items : (int64_t)per_sm * sms;
+    k_mac_signal_persist<NSM, BPL, PST, MINB><<<(unsigned)grid, 32 * (GW + 1), smem, h->stream>>>(
+        xmap, hmap, n_blocks, h->M, h->P, h->n_slots_total, h->null_slot, h->out_to_in, sa, sb,
+        sal, sched_stride, Y, h->err, h->ovf_list, h->ovf_count, (int)n_items, rg);
     return cudaGetLastError();
 }
 
@@ -639,12 +1091,18 @@ cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, con
     const int64_t max_entries = (int64_t)2 * groups * tiles * h->n_out;
     cudaError_t e = ensure_overflow(h, max_entries);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(h->ovf_count, 0, sizeof(int), h->stream);
+    e = cudaMemsetAsync(h->ovf_count, 0, 2 * sizeof(int), h->stream);   // overflow count, work counter
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)(2 * groups), (unsigned)tiles, (unsigned)h->n_out);
-    e = h->mac_variant == 2
-            ? launch_group<4>(grid, xrun, hmap, h, n_blocks, sa, sb, sal, sched_stride, Y, rg)
-            : launch_group<3>(grid, xrun, hmap, h, n_blocks, sa, sb, sal, sched_stride, Y, rg);
+    // 0: persistent groups; 2: groups of up to four filters; 3: one group per
+    // CTA; 4: as 3 with two bins per thread where the bins split into 64-bin tiles
+    if (h->mac_variant == 0)
+        e = launch_persist<3, 1, 3, 4>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
+    else if (h->mac_variant == 2)
+        e = launch_group<4, 1>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
+    else if (h->mac_variant == 4 && h->P % 64 == 0)
+        e = launch_group<3, 2>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
+    else
+        e = launch_group<3, 1>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
     if (e != cudaSuccess) return e;
     const size_t wsmem = (size_t)TMA_WARPS * WARP_BYTES;
     if (wsmem > 48 * 1024) {

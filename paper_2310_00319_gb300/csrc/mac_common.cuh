@@ -41,29 +41,13 @@ struct RunSlots {
     float2 w[R][NSM - 1];        // weights of s_1 .. s_{NSM-1} per block, as (w, w) pairs
 };
 
-// Schedule of blocks tf, tf+2, .., tf+2(R-1) (rows past n_blocks repeat the
-// last valid row; their results are dropped).
-template <int R, int NSM = MAX_NS>
-__device__ __forceinline__ void run_slots(const int32_t *__restrict__ ao, const int32_t *__restrict__ bo,
-                                          const float *__restrict__ alo, int tf, int n_blocks,
-                                          int n_slots_total, int null_slot, unsigned *err,
-                                          RunSlots<R, NSM> &rs)
+// Distinct slots and mix weights of a run from its blocks' schedule entries
+// a[r], b[r], al[r] (already checked): slots in order of first use (block
+// order, a before b), a slot counted only where its weight is nonzero.
+template <int R, int NSM>
+__device__ __forceinline__ void run_slots_core(const int (&a)[R], const int (&b)[R],
+                                               const float (&al)[R], RunSlots<R, NSM> &rs)
 {
-    int a[R], b[R];
-    float al[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int t = tf + 2 * r;
-        if (t < n_blocks) {
-            a[r] = checked_slot(__ldg(ao + t), n_slots_total, null_slot, err);
-            b[r] = bo ? checked_slot(__ldg(bo + t), n_slots_total, null_slot, err) : a[r];
-            al[r] = alo ? __ldg(alo + t) : 0.f;
-        } else {
-            a[r] = r ? a[r - 1] : 0;
-            b[r] = r ? b[r - 1] : 0;
-            al[r] = r ? al[r - 1] : 0.f;
-        }
-    }
     int ns = 0;
     bool overflow = false;
 #pragma unroll
@@ -106,6 +90,32 @@ __device__ __forceinline__ void run_slots(const int32_t *__restrict__ ao, const 
     }
 }
 
+// Schedule of blocks tf, tf+2, .., tf+2(R-1) (rows past n_blocks repeat the
+// last valid row; their results are dropped).
+template <int R, int NSM = MAX_NS>
+__device__ __forceinline__ void run_slots(const int32_t *__restrict__ ao, const int32_t *__restrict__ bo,
+                                          const float *__restrict__ alo, int tf, int n_blocks,
+                                          int n_slots_total, int null_slot, unsigned *err,
+                                          RunSlots<R, NSM> &rs)
+{
+    int a[R], b[R];
+    float al[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int t = tf + 2 * r;
+        if (t < n_blocks) {
+            a[r] = checked_slot(__ldg(ao + t), n_slots_total, null_slot, err);
+            b[r] = bo ? checked_slot(__ldg(bo + t), n_slots_total, null_slot, err) : a[r];
+            al[r] = alo ? __ldg(alo + t) : 0.f;
+        } else {
+            a[r] = r ? a[r - 1] : 0;
+            b[r] = r ? b[r - 1] : 0;
+            al[r] = r ? al[r - 1] : 0.f;
+        }
+    }
+    run_slots_core<R, NSM>(a, b, al, rs);
+}
+
 // One step of Eq. 7 for the R blocks of a run: partition values h0 = H_{s_0}(m),
 // hs[j-1] = H_{s_j}(m); xw holds X(tf + 2(r - m)) at index (r - u) mod R, with
 // u = m mod R. Callers unroll over u so every register index is a constant.
@@ -125,6 +135,32 @@ __device__ __forceinline__ void run_step(float2 (&acc)[R], const float2 (&xw)[R]
 #pragma unroll
         for (int j = 1; j < NS; ++j) h = __ffma2_rn(w[r][j - 1], dj[j - 1], h);
         cmac(acc[r], h, xw[(r - u % R + R) % R]);
+    }
+}
+
+// run_step for a lane that owns BPL adjacent bins: the run's weights are
+// shared by the bins, every bin takes exactly the operations of run_step.
+template <int R, int NS, int NSM, int BPL>
+__device__ __forceinline__ void run_step_bins(float2 (&acc)[R][BPL], const float2 (&xw)[R][BPL],
+                                              const float2 (&h0)[BPL],
+                                              const float2 (&hs)[NS > 1 ? NS - 1 : 1][BPL],
+                                              const float2 (&w)[R][NSM - 1], int u)
+{
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 dj[NS > 1 ? NS - 1 : 1][BPL];
+#pragma unroll
+    for (int j = 1; j < NS; ++j)
+#pragma unroll
+        for (int b = 0; b < BPL; ++b) dj[j - 1][b] = __ffma2_rn(h0[b], m1, hs[j - 1][b]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int b = 0; b < BPL; ++b) {
+            float2 h = h0[b];
+#pragma unroll
+            for (int j = 1; j < NS; ++j) h = __ffma2_rn(w[r][j - 1], dj[j - 1][b], h);
+            cmac(acc[r][b], h, xw[(r - u % R + R) % R][b]);
+        }
     }
 }
 

@@ -222,18 +222,23 @@ def test_invalid_slot_is_silenced_and_reported():
     _assert_close(y.cpu().numpy(), ref, "invalid slot")
 
 
-def test_mac_staging_variants_agree_bitwise():
-    """TMA-staged and cp.async-staged multiply-accumulate run the same
-    arithmetic in the same order: their outputs are identical."""
+@pytest.mark.parametrize("L,n_slots,interp", [(16, 6, True), (256, 6, True), (128, 3, False),
+                                               (512, 2, True)])
+def test_mac_staging_variants_agree_bitwise(L, n_slots, interp):
+    """The persistent and the one-group-per-CTA TMA kernels (one or two bins
+    per thread) and the cp.async kernel run the same arithmetic in the same
+    order: their outputs are identical. L = 16 (32 bins) has no 64-bin tiles;
+    six random slots per block send most groups to the overflow kernel, two or
+    three keep them in the group kernels."""
     dev = _dev()
-    wl = W.random_case(14, L=256, ir_len=20000, N=50000, n_in=2, n_out=3, n_slots=6,
-                       out_to_in=[0, 1, 1])
+    wl = W.random_case(14 + L, L=L, ir_len=80 * L, N=200 * L, n_in=2, n_out=3, n_slots=n_slots,
+                       out_to_in=[0, 1, 1], interp=interp)
     plan = _plan(wl, dev)
-    y_tma = _run_signal(wl, dev, plan)
-    plan.set_option(1, 1)
-    y_lsu = _run_signal(wl, dev, plan)
-    np.testing.assert_array_equal(y_tma, y_lsu)
-    _assert_close(y_tma, _ref(wl), "variants")
+    y0 = _run_signal(wl, dev, plan)
+    for staging in (1, 3, 4):
+        plan.set_option(1, staging)
+        np.testing.assert_array_equal(_run_signal(wl, dev, plan), y0)
+    _assert_close(y0, _ref(wl), "variants")
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 8])
