@@ -112,15 +112,25 @@ __host__ __device__ constexpr int tw_offset(int P, int Ns)
 }
 __host__ __device__ constexpr int tw_size(int P) { return tw_offset(P, P); }
 
+// Between stages the transform lives in shared memory in a swizzled order:
+// value n sits at swz(n), which permutes the 16 values of each 128-byte row by
+// XOR with the row index. The butterflies' scattered stores (index 8j + s at
+// the first stage, (j/8) 64 + j mod 8 + 8s at the second) then spread over all
+// banks instead of hitting every second or eighth row's banks; the strided
+// loads stay one row per half warp. A transform's input (filled by the caller)
+// and output are in natural order.
+__device__ __forceinline__ int swz(int n) { return n ^ ((n >> 4) & 15); }
+
 // One Stockham stage of radix R on a P-point transform: butterfly j reads
 // src[j + r P/R], rotates input r by the twiddle r * (j mod Ns) / (Ns R) of a
-// turn, transforms, and writes dst[(j / Ns) Ns R + (j mod Ns) + s Ns].
-// Output transform of the last stage: epi(n, v) is stored at natural index n.
+// turn, transforms, and writes dst[(j / Ns) Ns R + (j mod Ns) + s Ns] (SW_IN,
+// SW_OUT: src, dst in swizzled order). Output transform of the last stage:
+// epi(n, v) is stored at natural index n.
 struct NoEpi {
     __device__ __forceinline__ float2 operator()(int, float2 v) const { return v; }
 };
 
-template <int P, int Ns, int R, bool INV, class Epi = NoEpi>
+template <int P, int Ns, int R, bool INV, bool SW_IN, bool SW_OUT, class Epi = NoEpi>
 __device__ __forceinline__ void stockham_stage(const float2 *__restrict__ src, float2 *__restrict__ dst,
                                                int j, const float2 *__restrict__ tw, Epi epi = Epi())
 {
@@ -128,7 +138,10 @@ __device__ __forceinline__ void stockham_stage(const float2 *__restrict__ src, f
     const int k = j & (Ns - 1);
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[j + r * stride];
+    for (int r = 0; r < R; ++r) {
+        const int n = j + r * stride;
+        v[r] = src[SW_IN ? swz(n) : n];
+    }
     if constexpr (Ns > 1) {
         const float2 *tws = tw + tw_offset(P, Ns) + k;
 #pragma unroll
@@ -140,36 +153,41 @@ __device__ __forceinline__ void stockham_stage(const float2 *__restrict__ src, f
     dftR<R, INV>(v);
     const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
-    for (int s = 0; s < R; ++s) dst[base + s * Ns] = epi(base + s * Ns, v[s]);
+    for (int s = 0; s < R; ++s) {
+        const int n = base + s * Ns;
+        dst[SW_OUT ? swz(n) : n] = epi(n, v[s]);
+    }
 }
 
 // Stages for P = 2^LG: radix 8 while three or more bits remain, then one
 // radix-4 or radix-2 stage. Thread j of T = P/8 runs one butterfly per
 // radix-8 stage, two per radix-4 stage, four per radix-2 stage. epi is applied
-// to the values of the last stage as they are stored.
+// to the values of the last stage as they are stored. The stage at Ns = 1
+// reads natural order, later stages swizzled; the last stage writes natural.
 template <int P, int Ns, bool INV, class Epi = NoEpi>
 __device__ __forceinline__ float2 *fft_stages(float2 *a, float2 *b, int j, const float2 *__restrict__ tw,
                                               Epi epi = Epi())
 {
     constexpr int T = P / 8;
+    constexpr bool SW_IN = Ns > 1;
     if constexpr (Ns == P) {
         return a;
     } else if constexpr (P / Ns >= 8) {
         if constexpr (P / Ns == 8)
-            stockham_stage<P, Ns, 8, INV>(a, b, j, tw, epi);
+            stockham_stage<P, Ns, 8, INV, SW_IN, false>(a, b, j, tw, epi);
         else
-            stockham_stage<P, Ns, 8, INV>(a, b, j, tw);
+            stockham_stage<P, Ns, 8, INV, SW_IN, true>(a, b, j, tw);
         __syncthreads();
         return fft_stages<P, Ns * 8, INV>(b, a, j, tw, epi);
     } else if constexpr (P / Ns == 4) {
-        stockham_stage<P, Ns, 4, INV>(a, b, j, tw, epi);
-        stockham_stage<P, Ns, 4, INV>(a, b, j + T, tw, epi);
+        stockham_stage<P, Ns, 4, INV, SW_IN, false>(a, b, j, tw, epi);
+        stockham_stage<P, Ns, 4, INV, SW_IN, false>(a, b, j + T, tw, epi);
         __syncthreads();
         return b;
     } else {
         static_assert(P / Ns == 2, "radix plan");
 #pragma unroll
-        for (int u = 0; u < 4; ++u) stockham_stage<P, Ns, 2, INV>(a, b, j + u * T, tw, epi);
+        for (int u = 0; u < 4; ++u) stockham_stage<P, Ns, 2, INV, SW_IN, false>(a, b, j + u * T, tw, epi);
         __syncthreads();
         return b;
     }
@@ -193,7 +211,7 @@ __device__ __forceinline__ float2 *fft_complex_regs(float2 (&z)[8], float2 *a, f
     static_assert(P >= 16, "a radix-8 first stage and at least one stage after it");
     dftR<8, INV>(z);
 #pragma unroll
-    for (int s = 0; s < 8; ++s) b[j * 8 + s] = z[s];   // stage Ns = 1: dst (j * 8 + s)
+    for (int s = 0; s < 8; ++s) b[swz(j * 8 + s)] = z[s];   // stage Ns = 1: dst (j * 8 + s), swizzled
     __syncthreads();
     return fft_stages<P, 8, INV>(b, a, j, tw, epi);
 }
