@@ -241,6 +241,19 @@ def test_mac_staging_variants_agree_bitwise(L, n_slots, interp):
     _assert_close(y0, _ref(wl), "variants")
 
 
+def test_staging_option_range():
+    """TVOLAP_OPT_MAC_STAGING takes 0 .. 4; other values and options are refused."""
+    from paper_2310_00319_gb300 import TvolapError
+    dev = _dev()
+    wl = W.random_case(3, L=64, ir_len=300, N=2000, n_slots=2)
+    plan = _plan(wl, dev)
+    for v in range(5):
+        plan.set_option(1, v)
+    for opt, v in [(1, -1), (1, 5), (2, 0)]:
+        with pytest.raises(TvolapError):
+            plan.set_option(opt, v)
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 8])
 def test_mac_four_filter_groups(k):
     """Staging option 2 stages up to four filters per group of 64 blocks: a
