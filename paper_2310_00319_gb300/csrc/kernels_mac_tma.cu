@@ -615,8 +615,10 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
 // loader keeps up to PSTAGE chunks in flight. The loader fills context k for
 // group i as soon as the consumers have released it (group i - 2 done:
 // barrier 'freed'), publishes it ('ready'), issues its window, then its chunks
-// as stages come free; the next group's work index and schedule entries are
-// fetched while the current group's chunks are issued. Consumer warps without
+// as stages come free; the next group's schedule entries load while the
+// current group's chunks are issued, and one work-counter request is always in
+// flight. Taking groups in counter order keeps the CTAs on neighbouring groups,
+// whose X rows and filter rows overlap in L2. Consumer warps without
 // a run in a group (past the output's last block) still take part in every
 // chunk's barriers, so the empty barriers always count four arrivals.
 //
@@ -741,8 +743,7 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
     __syncthreads();
 
     if (w == GW) {                                     // ---- loader
-        // next work index (uniform); stops once a wait anywhere gave up
-        // work indices come from a counter, one request kept in flight (lane 0)
+        // work indices (uniform) come from a counter, one request kept in flight (lane 0)
         // so that its latency hides behind a group; none once a wait anywhere
         // gave up
         int pend = lane == 0 ? atomicAdd(count + 1, 1) : 0;
