@@ -965,6 +965,149 @@ def _oracle_sample(wl, n_samples, channel=0, start=None, values=False):
     return (dt, y) if values else dt
 
 
+def run_mixdown(args):
+    """Binaural mixdown: S = channels / 2 sources, each rendered to two ears
+    through its own time-variant responses (plan output 2s + e reads source s),
+    the ears' spectra summed before one inverse transform per ear. A step is
+    the bank transform, the forward transforms of the S sources, the MAC of
+    the 2S paths, the mixdown and the two inverse transforms with the
+    overlap-add; beside it the same step with 2S inverse transforms and no
+    mixdown."""
+    import torch
+    import oracle
+    from paper_2310_00319_gb300 import Plan, costmodel, _lib as L_
+    from paper_2310_00319_gb300.tvolap import n_blocks_for, _ptr
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    base = workload(args)                                   # 2S paths of the default recipe
+    S = base.n_out // 2
+    L, M, P, N = base.L, base.M, 2 * base.L, base.N
+    nb = n_blocks_for(base.out_len, L)
+    o2i = [o // 2 for o in range(2 * S)]
+    mix = [o % 2 for o in range(2 * S)]
+    stream = torch.cuda.current_stream(dev)
+    plan = Plan(L, M, n_in=S, n_out=2 * S, out_to_in=o2i, n_slots=base.irs.shape[0], device=dev)
+    plan.set_mix(mix)
+    ears = Plan(L, M, n_in=2, n_out=2, n_slots=1, device=dev)   # inverse of the two mixed rows
+    x = torch.from_numpy(np.ascontiguousarray(base.x[:S])).to(dev)
+    irs = torch.from_numpy(base.irs).to(dev)
+    sa, sb, sal = (torch.from_numpy(a).to(dev) for a in (base.sched_a, base.sched_b,
+                                                           base.sched_alpha))
+    X = torch.empty((S, nb, P), dtype=torch.complex64, device=dev)
+    Y = torch.empty((2 * S, nb, P), dtype=torch.complex64, device=dev)
+    Ym = torch.empty((2, nb, P), dtype=torch.complex64, device=dev)
+    y2 = torch.empty((2, base.out_len), dtype=torch.float32, device=dev)
+    yall = torch.empty((2 * S, base.out_len), dtype=torch.float32, device=dev)
+    lib, h = plan.lib, plan.h
+
+    def step(mixdown, ev=None):
+        rec = (lambda i: ev[i].record(stream)) if ev else (lambda i: None)
+        rec(0)
+        L_.check(lib.tvolap_load_bank(h, 0, irs.shape[0], _ptr(irs), irs.shape[1], irs.shape[1]),
+                 "load_bank")
+        L_.check(lib.tvolap_forward_spectra(h, _ptr(x), N, N, nb, _ptr(X)), "forward")
+        rec(1)
+        L_.check(lib.tvolap_mac(h, _ptr(X), nb, _ptr(sa), _ptr(sb), _ptr(sal), sa.shape[1],
+                                _ptr(Y)), "mac")
+        rec(2)
+        if mixdown:
+            L_.check(lib.tvolap_mix(h, _ptr(Y), nb, _ptr(Ym)), "mix")
+            rec(3)
+            L_.check(lib.tvolap_inverse_ola(ears.h, _ptr(Ym), nb, _ptr(y2), base.out_len,
+                                            base.out_len), "inverse")
+        else:
+            rec(3)
+            L_.check(lib.tvolap_inverse_ola(h, _ptr(Y), nb, _ptr(yall), base.out_len,
+                                            base.out_len), "inverse")
+        rec(4)
+
+    def timed(mixdown):
+        for _ in range(args.warmup):
+            step(mixdown)
+        plan.check()
+        torch.cuda.synchronize(dev)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev.index) as clk:
+            t0.record(stream)
+            for i in range(args.steps):
+                step(mixdown, evs[i])
+            t1.record(stream)
+            torch.cuda.synchronize(dev)
+        plan.check()
+        st = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in evs]).mean(0)
+        return t0.elapsed_time(t1) / args.steps, st, clk.summary()
+
+    ms_mix, st_mix, clocks = timed(True)
+    ms_plain, st_plain, _ = timed(False)
+    # the user call for the whole signal (forward, MAC, mixdown, two inverses)
+    for _ in range(2):
+        plan.process_signal_mix(x, sa, sb, sal, out_len=base.out_len)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        ym = plan.process_signal_mix(x, sa, sb, sal, out_len=base.out_len)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    plan.check()
+    ms_call = a.elapsed_time(b) / args.steps
+    units = 2 * S * base.out_len                            # path-samples per step
+    flops = mac_terms(nb, M) * P * 2 * S * costmodel.mac_flops_per_block_bin_partition(True)
+    peak = fp32_peak_tflops(_peaks()[0].get("sm_max_mhz", 2070.0))
+    achieved = flops / (st_mix[1] * 1e-3) / 1e12
+    hbm = _peaks()[0].get("hbm_gbs", 6800.0)
+    mix_bytes = 8.0 * P * nb * (2 * S + 2)
+    out = {
+        "metric": METRIC, "value": round(units / (ms_mix * 1e-3), 1), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_mix, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"binaural_mixdown_{S}src_L{L}_N{N}_ir{base.ir_len}",
+                   "sources": S, "ears": 2, "paths": 2 * S, "L": L, "M": M,
+                   "samples_per_path": base.out_len, "per_gpu_units": units,
+                   "unit_note": "path-samples (sources x ears x output samples)",
+                   "l2": "working set ~1.3 GB >> 129 MB L2; no flush"},
+        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
+                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": "k_mac_signal_persist"},
+        "stages": {"bank_and_forward": {"ms": round(float(st_mix[0]), 4)},
+                   "mac": {"ms": round(float(st_mix[1]), 4), "tflops": round(achieved, 3)},
+                   "mix": {"ms": round(float(st_mix[2]), 4),
+                           "gbs": round(mix_bytes / (st_mix[2] * 1e-3) / 1e9, 1),
+                           "of_hbm": round(mix_bytes / (st_mix[2] * 1e-3) / 1e9 / hbm, 3)},
+                   "inverse_2_ears": {"ms": round(float(st_mix[3]), 4)}},
+        "without_mixdown": {"ms_per_step": round(ms_plain, 4),
+                            "inverse_all_paths_ms": round(float(st_plain[3]), 4),
+                            "speedup": round(ms_plain / ms_mix, 3),
+                            "note": f"{2 * S} inverse transforms and {2 * S} output rows; the "
+                                    "ears would still need a sum"},
+        "process_signal_mix_ms": round(ms_call, 4),
+        "clocks": clocks, "gpu_launches": 6 * args.steps,
+    }
+    if not args.no_cpu:
+        # ear e at 128 samples in the steady state: the sum of its paths' oracle outputs
+        n_idx = np.arange(base.out_len // 2, base.out_len // 2 + 128, dtype=np.int64)
+        x64 = np.ascontiguousarray(base.x[:S], np.float64)
+        irs64 = np.ascontiguousarray(base.irs, np.float64)
+        al64 = np.ascontiguousarray(base.sched_alpha, np.float64)
+        oc = np.repeat(np.arange(2 * S, dtype=np.int32), n_idx.size)
+        t = time.perf_counter()
+        per_path = oracle.tvolap_samples(x64, irs64, L, base.sched_a, base.sched_b, al64, oc,
+                                         np.tile(n_idx, 2 * S), out_to_in=o2i)
+        dt = time.perf_counter() - t
+        ref = oracle.mixdown(per_path.reshape(2 * S, n_idx.size), mix)
+        got = ym[:, n_idx.min():n_idx.max() + 1].cpu().numpy()
+        out["accuracy"] = accuracy(got, ref)
+        out["cpu_baseline"] = {"value": round(oc.size / dt, 1), "unit": UNIT,
+                               "cores": oracle.num_threads(), "kind": "oracle",
+                               "sample": f"{n_idx.size} samples of both ears: {oc.size} path "
+                                         "samples of the FP64 time-domain oracle, summed"}
+    plan.close()
+    ears.close()
+    return out
+
+
 def accuracy_plain_mono(dev):
     """The mono configuration (L = 128, 96000 samples, 4 responses of 4096 taps
     switched every 16 blocks) through process_signal, against the FP64 oracle
@@ -1054,7 +1197,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain_at_scale",
-                    choices=["plain_at_scale", "adjoint", "batched", "serve"])
+                    choices=["plain_at_scale", "adjoint", "batched", "serve", "mixdown"])
     ap.add_argument("--channels", type=int, default=64)
     ap.add_argument("--samples", type=int, default=480000)
     ap.add_argument("--ir-len", type=int, default=48000,
@@ -1085,6 +1228,8 @@ def main():
         out = run_batched(args)
     elif args.workload == "serve":
         out = run_serve(args)
+    elif args.workload == "mixdown":
+        out = run_mixdown(args)
     else:
         out = run_ours(args)
     if out is not None:

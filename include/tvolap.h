@@ -339,6 +339,59 @@ TVOLAP_API int tvolap_process_signal_static(tvolap_t h, const float *x_dev, int6
                                             int64_t sched_stride, float *y_dev, int64_t out_len,
                                             int64_t y_stride);
 
+/* ========================================================================
+ * Frequency-domain mixdown of several outputs (an extension of Section 2's
+ * c parallel channels for multi-channel binaural rendering, Section 5): the
+ * inverse transform (Eq. 8) and the overlap-add (Eqs. 9-12) are linear, so
+ * the sum of several outputs equals one inverse transform of the sum of
+ * their spectra Y. A renderer with S sources and E ears makes S*E plan
+ * outputs (output o reads source out_to_in[o] through its own filters) and
+ * E mix outputs, and runs E inverse transforms per block instead of S*E.
+ * ======================================================================== */
+
+/*
+ * Define the mixdown: n_mix mix outputs, 1 <= n_mix <= n_out; mix_of_out
+ * (host int32 [n_out]) gives each plan output's mix output in [0, n_mix);
+ * a mix output with no member is silent. n_mix = 0 removes the mixdown.
+ * Synchronises the plan's stream (allocates), clears the mix outputs'
+ * streaming overlap-add state; the plan's own streaming state is kept.
+ * Returns TVOLAP_ERR_ARG for an invalid map.
+ */
+TVOLAP_API int tvolap_set_mix(tvolap_t h, int n_mix, const int32_t *mix_of_out);
+
+/*
+ * Mixdown stage: Ymix[e][t][k] = sum of Y[o][t][k] over the outputs o of mix
+ * output e, added in increasing o (a single member is copied exactly).
+ *   Y_dev     device complex64 [n_out][n_blocks][2L] (tvolap_mac's layout)
+ *   Ymix_dev  device complex64 [n_mix][n_blocks][2L]
+ * Both 16-byte aligned. TVOLAP_ERR_ARG without a mixdown.
+ */
+TVOLAP_API int tvolap_mix(tvolap_t h, const void *Y_dev, int n_blocks, void *Ymix_dev);
+
+/*
+ * tvolap_process_signal with the mixdown: forward transforms, the partition
+ * MAC of every plan output, the mixdown, then n_mix inverse transforms with
+ * the overlap-add.
+ *   y_dev   device float [n_mix][y_stride]; samples [0, out_len) of each
+ *           mix output written
+ * Other arguments as tvolap_process_signal; the workspace grows by
+ * 8 * P * n_blocks * n_mix bytes.
+ */
+TVOLAP_API int tvolap_process_signal_mix(tvolap_t h, const float *x_dev, int64_t N, int64_t x_stride,
+                                         const int32_t *sched_a, const int32_t *sched_b,
+                                         const float *sched_alpha, int64_t sched_stride,
+                                         float *y_dev, int64_t out_len, int64_t y_stride);
+
+/*
+ * tvolap_process_block with the mixdown: out_dev is device float [n_mix][L],
+ * delayed by L samples like tvolap_process_block. The mix outputs keep their
+ * own overlap-add state, so a stream is run with one of the two calls (after
+ * tvolap_reset or tvolap_set_mix).
+ */
+TVOLAP_API int tvolap_process_block_mix(tvolap_t h, const float *in_dev, float *out_dev,
+                                        const int32_t *sel_a, const int32_t *sel_b,
+                                        const float *sel_alpha);
+
 /* Options of tvolap_set_option. */
 typedef enum tvolap_option {
     /* Staging of the offline multiply-accumulate: 0 = tiled bulk tensor copies

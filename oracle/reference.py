@@ -33,6 +33,10 @@ Functions and the passages of arxiv 2310.00319 they follow:
                               tests/test_oracle_grad_pins.py.
 * ``params_grad_sampled``  -- chosen entries of the same gradients, each from
                               the definitions on its own (full-size checks).
+* ``mixdown``              -- the sum of the outputs routed to each mix output
+                              (Section 2's c channels summed per ear for the
+                              binaural rendering of Section 5; by linearity of
+                              Eq. 8 and Eqs. 9-12 the library sums spectra).
 
 Readings of the paper that these functions take (each is pinned by a test in
 tests/test_oracle_pins.py):
@@ -195,6 +199,26 @@ def tvolap_direct(x, irs, L, sched_a, sched_b=None, sched_alpha=None, out_len=No
                              _ptr(a, ctypes.c_int), _ptr(b, ctypes.c_int),
                              _ptr(al, ctypes.c_double), int(out_len), _ptr(y, ctypes.c_double))
     return y[0] if (squeeze and n_out == 1) else y
+
+
+def mixdown(y, mix_of_out, n_mix=None):
+    """Mix outputs as sums of plan outputs (FP64): row e of the result is the
+    sum of the rows o of y with mix_of_out[o] == e, added in increasing o.
+
+    y          [n_out, n] outputs (any float dtype, upcast to FP64)
+    mix_of_out [n_out] mix output of each plan output, in [0, n_mix)
+    n_mix      mix outputs (default max(mix_of_out) + 1)
+    returns    [n_mix, n] FP64
+    """
+    y = _f64(y)
+    m = np.asarray(mix_of_out, dtype=np.int64)
+    if m.shape != (y.shape[0],):
+        raise ValueError("mix_of_out must have one entry per output")
+    n_mix = int(m.max()) + 1 if n_mix is None else int(n_mix)
+    out = np.zeros((n_mix, y.shape[1]), np.float64)
+    for o in range(y.shape[0]):
+        out[m[o]] += y[o]
+    return out
 
 
 def tvolap_samples(x, irs, L, sched_a, sched_b, sched_alpha, out_ch, n_idx, M=None,

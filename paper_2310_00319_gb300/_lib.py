@@ -47,6 +47,13 @@ SIGNATURES = {
     "tvolap_bank_spectra": (c_int, [c_void_p, c_int, c_void_p]),
     "tvolap_check": (c_int, [c_void_p]),
     "tvolap_set_option": (c_int, [c_void_p, c_int, c_int]),
+    "tvolap_set_mix": (c_int, [c_void_p, c_int, c_void_p]),
+    "tvolap_mix": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
+    "tvolap_process_signal_mix": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p,
+                                          c_void_p, c_void_p, c_int64, c_void_p, c_int64,
+                                          c_int64]),
+    "tvolap_process_block_mix": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_void_p]),
     "tvolap_block_spectra": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int,
                                      c_void_p]),
     "tvolap_mac_params": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int64,

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "internal.h"
 
@@ -38,7 +39,8 @@ void free_plan(tvolap_plan *h)
     if (!h) return;
     void *ptrs[] = {h->tw,   h->rot,  h->post, h->win,     h->bank, h->out_to_in,
                     h->sel_a, h->sel_b, h->sel_alpha, h->err, h->ring, h->hist,
-                    h->ola,  h->Ystream, h->ws,  h->ovf_list, h->ovf_count};
+                    h->ola,  h->Ystream, h->ws,  h->ovf_list, h->ovf_count,
+                    h->mix_off, h->mix_members, h->mix_ola, h->Ymix_stream};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -49,10 +51,11 @@ int64_t blocks_for(const tvolap_plan *h, int64_t out_len)
     return out_len <= 0 ? 0 : (out_len - 1) / h->L + 2;
 }
 
-// Device memory for process_signal: X [n_in][nb][P] then Y [n_out][nb][P].
+// Device memory for process_signal: X [n_in][nb][P], Y [n_out][nb][P], then
+// (with a mixdown) Ymix [n_mix][nb][P].
 int64_t workspace_bytes(const tvolap_plan *h, int64_t nb)
 {
-    return (int64_t)sizeof(float2) * h->P * nb * (h->n_in + h->n_out);
+    return (int64_t)sizeof(float2) * h->P * nb * (h->n_in + h->n_out + h->n_mix);
 }
 
 int ensure_workspace(tvolap_plan *h, size_t bytes)
@@ -82,6 +85,8 @@ int reset_state(tvolap_plan *h)
     if ((e = cudaMemsetAsync(h->ring, 0, sizeof(float2) * h->n_in * 2 * h->M * P, h->stream)) ||
         (e = cudaMemsetAsync(h->hist, 0, sizeof(float) * h->n_in * h->L, h->stream)) ||
         (e = cudaMemsetAsync(h->ola, 0, sizeof(float) * h->n_out * 3 * h->L, h->stream)) ||
+        (h->n_mix > 0 &&
+         (e = cudaMemsetAsync(h->mix_ola, 0, sizeof(float) * h->n_mix * 3 * h->L, h->stream))) ||
         (e = cudaMemsetAsync(h->sel_alpha, 0, sizeof(float) * h->n_out, h->stream)))
         return cuda_status(e);
     // every output starts on its private (zero) slot
@@ -509,6 +514,97 @@ int tvolap_adjoint_input(tvolap_t h, const float *dX_dev, int64_t q_first, int q
     if (!dX_dev || !dx_dev) return TVOLAP_ERR_ARG;
     return cuda_status(launch_adjoint_input(h, reinterpret_cast<const float2 *>(dX_dev), q_first,
                                             q_count, dx_dev, N, x_stride));
+}
+
+int tvolap_set_mix(tvolap_t h, int n_mix, const int32_t *mix_of_out)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (n_mix < 0 || n_mix > h->n_out || (n_mix > 0 && !mix_of_out)) return TVOLAP_ERR_ARG;
+    for (int o = 0; n_mix > 0 && o < h->n_out; ++o)
+        if (mix_of_out[o] < 0 || mix_of_out[o] >= n_mix) return TVOLAP_ERR_ARG;
+    // members of each mix output in increasing output order (CSR)
+    std::vector<int32_t> off(n_mix + 1, 0), members(n_mix > 0 ? h->n_out : 0);
+    for (int o = 0; n_mix > 0 && o < h->n_out; ++o) ++off[mix_of_out[o] + 1];
+    for (int e = 0; e < n_mix; ++e) off[e + 1] += off[e];
+    {
+        std::vector<int32_t> fill(off.begin(), off.end() - (n_mix > 0 ? 1 : 0));
+        for (int o = 0; n_mix > 0 && o < h->n_out; ++o) members[fill[mix_of_out[o]]++] = o;
+    }
+    cudaError_t e = cudaStreamSynchronize(h->stream);          // the old arrays may be in use
+    if (e != cudaSuccess) return cuda_status(e);
+    void *old[] = {h->mix_off, h->mix_members, h->mix_ola, h->Ymix_stream};
+    for (void *p : old)
+        if (p) cudaFree(p);
+    h->mix_off = h->mix_members = nullptr;
+    h->mix_ola = nullptr;
+    h->Ymix_stream = nullptr;
+    h->n_mix = 0;
+    if (n_mix == 0) return TVOLAP_OK;
+    if ((e = dalloc(&h->mix_off, (size_t)n_mix + 1)) || (e = dalloc(&h->mix_members, (size_t)h->n_out)) ||
+        (e = dalloc(&h->mix_ola, (size_t)n_mix * 3 * h->L)) ||
+        (e = dalloc(&h->Ymix_stream, (size_t)n_mix * h->P)))
+        return cuda_status(e);
+    if ((e = cudaMemcpy(h->mix_off, off.data(), sizeof(int32_t) * (n_mix + 1), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(h->mix_members, members.data(), sizeof(int32_t) * h->n_out,
+                        cudaMemcpyHostToDevice)) ||
+        (e = cudaMemsetAsync(h->mix_ola, 0, sizeof(float) * n_mix * 3 * h->L, h->stream)) ||
+        (e = cudaStreamSynchronize(h->stream)))
+        return cuda_status(e);
+    h->n_mix = n_mix;
+    return TVOLAP_OK;
+}
+
+int tvolap_mix(tvolap_t h, const void *Y_dev, int n_blocks, void *Ymix_dev)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (h->n_mix == 0 || n_blocks < 0) return TVOLAP_ERR_ARG;
+    if (n_blocks == 0) return TVOLAP_OK;
+    if (!Y_dev || !Ymix_dev || (reinterpret_cast<uintptr_t>(Y_dev) & 15u) ||
+        (reinterpret_cast<uintptr_t>(Ymix_dev) & 15u))
+        return TVOLAP_ERR_ARG;
+    return cuda_status(launch_mix_spectra(h, reinterpret_cast<const float2 *>(Y_dev), n_blocks,
+                                          reinterpret_cast<float2 *>(Ymix_dev)));
+}
+
+int tvolap_process_signal_mix(tvolap_t h, const float *x_dev, int64_t N, int64_t x_stride,
+                              const int32_t *sched_a, const int32_t *sched_b,
+                              const float *sched_alpha, int64_t sched_stride, float *y_dev,
+                              int64_t out_len, int64_t y_stride)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (h->n_mix == 0) return TVOLAP_ERR_ARG;
+    if (N < 0 || out_len < 0 || x_stride < N || y_stride < out_len) return TVOLAP_ERR_ARG;
+    if (out_len == 0) return TVOLAP_OK;
+    if ((N > 0 && !x_dev) || !y_dev || !sched_a) return TVOLAP_ERR_ARG;
+    const int64_t nb = blocks_for(h, out_len);
+    if (nb > (int64_t)0x7fffffff / 2 || sched_stride < nb) return TVOLAP_ERR_ARG;
+    int st = ensure_workspace(h, (size_t)workspace_bytes(h, nb));
+    if (st != TVOLAP_OK) return st;
+    float2 *X = reinterpret_cast<float2 *>(h->ws);
+    float2 *Y = X + (int64_t)h->n_in * nb * h->P;
+    float2 *Ym = Y + (int64_t)h->n_out * nb * h->P;
+    cudaError_t e = launch_forward_signal(h, x_dev, N, x_stride, (int)nb, X);
+    if (e == cudaSuccess)
+        e = launch_mac_signal(h, X, (int)nb, sched_a, sched_b, sched_alpha, sched_stride, Y);
+    if (e == cudaSuccess) e = launch_mix_spectra(h, Y, (int)nb, Ym);
+    if (e == cudaSuccess)
+        e = launch_inverse_ola(h, Ym, (int)nb, y_dev, out_len, y_stride, Ragged{}, h->n_mix);
+    return cuda_status(e);
+}
+
+int tvolap_process_block_mix(tvolap_t h, const float *in_dev, float *out_dev, const int32_t *sel_a,
+                             const int32_t *sel_b, const float *sel_alpha)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (h->n_mix == 0 || !in_dev || !out_dev) return TVOLAP_ERR_ARG;
+    if (!sel_a && (sel_b || sel_alpha)) return TVOLAP_ERR_ARG;
+    cudaError_t e = launch_forward_stream(h, in_dev);
+    if (e == cudaSuccess) e = launch_mac_stream(h, sel_a, sel_b, sel_alpha);
+    if (e == cudaSuccess) e = launch_mix_spectra(h, h->Ystream, 1, h->Ymix_stream);
+    if (e == cudaSuccess) e = launch_inverse_stream(h, out_dev, h->Ymix_stream, h->mix_ola, h->n_mix);
+    if (e != cudaSuccess) return cuda_status(e);
+    h->tick += 1;
+    return TVOLAP_OK;
 }
 
 int tvolap_set_option(tvolap_t h, int option, int value)

@@ -46,6 +46,14 @@ struct tvolap_plan {
     // process_signal workspace
     void *ws;
     size_t ws_bytes;
+
+    // frequency-domain mixdown (tvolap_set_mix): mix output e sums the spectra
+    // of plan outputs mix_members[mix_off[e] .. mix_off[e + 1]), in increasing order
+    int n_mix;
+    int32_t *mix_off;             // [n_mix + 1]
+    int32_t *mix_members;         // [n_out]
+    float *mix_ola;               // [n_mix][3L] pending overlap-add sums (streaming)
+    float2 *Ymix_stream;          // [n_mix][P] this tick's mixed spectra
 };
 
 namespace tvolap {
@@ -77,10 +85,16 @@ cudaError_t launch_adjoint_input(tvolap_plan *h, const float2 *dX, int64_t q_fir
                                  float *dx, int64_t N, int64_t x_stride);
 cudaError_t launch_bank(tvolap_plan *h, int first_slot, int count, const float *ir, int ir_len,
                         int64_t ir_stride);
+// n_outputs: spectra rows of Y and output rows of y (-1: the plan's n_out)
 cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, float *y,
-                               int64_t out_len, int64_t y_stride, Ragged rg = Ragged{});
+                               int64_t out_len, int64_t y_stride, Ragged rg = Ragged{},
+                               int n_outputs = -1);
 cudaError_t launch_forward_stream(tvolap_plan *h, const float *in);
-cudaError_t launch_inverse_stream(tvolap_plan *h, float *out);
+// Ys, ola, n_outputs: this tick's spectra and pending sums (null, -1: the plan's outputs)
+cudaError_t launch_inverse_stream(tvolap_plan *h, float *out, const float2 *Ys = nullptr,
+                                  float *ola = nullptr, int n_outputs = -1);
+// Ymix[e][t] = sum over the members of mix output e of Y[o][t], t < n_blocks
+cudaError_t launch_mix_spectra(tvolap_plan *h, const float2 *Y, int n_blocks, float2 *Ymix);
 // tables and bank transform for a hop L (P = 2L = 1 << lgP) outside a plan
 cudaError_t launch_tables_raw(float2 *tw, float2 *rot, float2 *post, float *win, int L,
                               cudaStream_t st);

@@ -360,6 +360,32 @@ int inverse_seg(int L)
     return seg;
 }
 
+// Frequency-domain mixdown: by linearity of Eq. 8 and of the overlap-add of
+// Eqs. 9-12, one inverse transform of the sum of several outputs' spectra
+// equals the sum of their outputs. Thread i of the grid-stride loop takes bin
+// pair i of mix output e and adds the members' values in increasing output
+// order (two bins per 16-byte load).
+__global__ void __launch_bounds__(256)
+k_mix_spectra(const float4 *__restrict__ Y, float4 *__restrict__ Ymix, int64_t per_out, int n_mix,
+              const int32_t *__restrict__ off, const int32_t *__restrict__ members)
+{
+    const int64_t total = per_out * n_mix;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i / per_out);
+        const int64_t r = i - (int64_t)e * per_out;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int m = __ldg(off + e), m_end = __ldg(off + e + 1); m < m_end; ++m) {
+            const float4 v = __ldg(Y + (int64_t)__ldg(members + m) * per_out + r);
+            acc.x += v.x;
+            acc.y += v.y;
+            acc.z += v.z;
+            acc.w += v.w;
+        }
+        Ymix[i] = acc;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_tables(tvolap_plan *h)
@@ -436,9 +462,11 @@ cudaError_t launch_bank_raw(int lgP, int L, int M, int64_t count, const float *i
 }
 
 cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, float *y,
-                               int64_t out_len, int64_t y_stride, Ragged rg)
+                               int64_t out_len, int64_t y_stride, Ragged rg, int n_outputs)
 {
     if (out_len <= 0) return cudaSuccess;
+    if (n_outputs < 0) n_outputs = h->n_out;
+    if (n_outputs == 0) return cudaSuccess;
     const int seg = OLA_SEG;
     const int64_t n_seg = (out_len + (int64_t)seg * h->L - 1) / ((int64_t)seg * h->L);
     TVOLAP_DISPATCH(h->lgP, {
@@ -446,7 +474,7 @@ cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, fl
         const size_t sm = smem_fft<LG>() + (size_t)6 * h->L * sizeof(float);
         cudaError_t e = set_smem(k_inverse_ola<LG>, sm);
         if (e != cudaSuccess) return e;
-        dim3 grid((unsigned)n_seg, (unsigned)h->n_out);
+        dim3 grid((unsigned)n_seg, (unsigned)n_outputs);
         k_inverse_ola<LG><<<grid, Geo<P>::THREADS, sm, h->stream>>>(
             Y, n_blocks, h->L, seg, y, out_len, y_stride, h->rot, h->post, h->tw, rg);
     });
@@ -510,17 +538,37 @@ cudaError_t launch_forward_stream(tvolap_plan *h, const float *in)
     return cudaGetLastError();
 }
 
-cudaError_t launch_inverse_stream(tvolap_plan *h, float *out)
+cudaError_t launch_inverse_stream(tvolap_plan *h, float *out, const float2 *Ys, float *ola,
+                                  int n_outputs)
 {
+    if (!Ys) Ys = h->Ystream;
+    if (!ola) ola = h->ola;
+    if (n_outputs < 0) n_outputs = h->n_out;
+    if (n_outputs == 0) return cudaSuccess;
     TVOLAP_DISPATCH(h->lgP, {
         constexpr int P = 1 << LG;
-        const int grid = (h->n_out + Geo<P>::F - 1) / Geo<P>::F;
+        const int grid = (n_outputs + Geo<P>::F - 1) / Geo<P>::F;
         const size_t sm = smem_fft<LG>();
         cudaError_t e = set_smem(k_inverse_stream<LG>, sm);
         if (e != cudaSuccess) return e;
         k_inverse_stream<LG><<<grid, Geo<P>::THREADS, sm, h->stream>>>(
-            h->Ystream, h->ola, out, h->L, h->n_out, h->rot, h->post, h->tw);
+            Ys, ola, out, h->L, n_outputs, h->rot, h->post, h->tw);
     });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mix_spectra(tvolap_plan *h, const float2 *Y, int n_blocks, float2 *Ymix)
+{
+    const int64_t per_out = (int64_t)n_blocks * h->P / 2;      // bin pairs of one output
+    const int64_t total = per_out * h->n_mix;
+    if (total == 0) return cudaSuccess;
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    int64_t grid = (total + 255) / 256;
+    if (grid > (int64_t)sms * 16) grid = (int64_t)sms * 16;
+    k_mix_spectra<<<(unsigned)grid, 256, 0, h->stream>>>(reinterpret_cast<const float4 *>(Y),
+                                                         reinterpret_cast<float4 *>(Ymix), per_out,
+                                                         h->n_mix, h->mix_off, h->mix_members);
     return cudaGetLastError();
 }
 

@@ -70,6 +70,7 @@ class Plan:
             _lib.check(st, "tvolap_create")
         self.h = h
         self.out_to_in = list(out_to_in) if out_to_in is not None else list(range(n_out))
+        self.n_mix = 0
 
     # ------------------------------------------------------------------ lifetime
     def close(self):
@@ -149,6 +150,68 @@ class Plan:
                 if t.shape[0] != self.n_out:
                     raise ValueError(f"{nm} must have n_out entries")
         self._call("tvolap_process_block", _ptr(x), _ptr(out), _ptr(sel_a), _ptr(sel_b),
+                   _ptr(sel_alpha))
+        return out
+
+    # ------------------------------------------------------------------ mixdown
+    def set_mix(self, mix_of_out, n_mix: int | None = None):
+        """Sum plan outputs into n_mix mix outputs before the inverse transform:
+        mix_of_out[o] in [0, n_mix) (sequence of n_out ints); None removes it."""
+        if mix_of_out is None:
+            self._call("tvolap_set_mix", 0, None)
+            self.n_mix = 0
+            return
+        vals = [int(v) for v in mix_of_out]
+        if len(vals) != self.n_out:
+            raise ValueError(f"mix_of_out must have {self.n_out} entries")
+        n_mix = max(vals) + 1 if n_mix is None else int(n_mix)
+        self._call("tvolap_set_mix", n_mix, (ctypes.c_int32 * self.n_out)(*vals))
+        self.n_mix = n_mix
+
+    def mix(self, Y: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Mixdown stage: Y complex64 [n_out, n_blocks, 2L] -> [n_mix, n_blocks, 2L]."""
+        Y = _need(Y, torch.complex64, self.device, "Y", 3)
+        nb = Y.shape[1]
+        if out is None:
+            out = torch.empty((self.n_mix, nb, self.P), dtype=torch.complex64, device=self.device)
+        self._call("tvolap_mix", _ptr(Y), nb, _ptr(out))
+        return out
+
+    def process_signal_mix(self, x: torch.Tensor, sched_a, sched_b=None, sched_alpha=None,
+                           out_len: int | None = None, out: torch.Tensor | None = None):
+        """Offline TVOLAP with the mixdown: x [n_in, N] -> y [n_mix, out_len]."""
+        x = _need(x, torch.float32, self.device, "x", 2)
+        if x.shape[0] != self.n_in:
+            raise ValueError(f"x must have {self.n_in} rows")
+        N = x.shape[1]
+        out_len = N if out_len is None else int(out_len)
+        nb = n_blocks_for(out_len, self.L)
+        sa, sb, sal, stride = self._sched(sched_a, sched_b, sched_alpha, nb)
+        if out is None:
+            out = torch.empty((self.n_mix, out_len), dtype=torch.float32, device=self.device)
+        _need(out, torch.float32, self.device, "out", 2)
+        if out.shape[0] != self.n_mix or out.shape[1] < out_len:
+            raise ValueError("out too small")
+        self._call("tvolap_process_signal_mix", _ptr(x), N, N, _ptr(sa), _ptr(sb), _ptr(sal),
+                   stride, _ptr(out), out_len, out.shape[1])
+        return out
+
+    def process_block_mix(self, x: torch.Tensor, out: torch.Tensor | None = None, sel_a=None,
+                          sel_b=None, sel_alpha=None) -> torch.Tensor:
+        """One hop with the mixdown: x [n_in, L] -> [n_mix, L] (delayed by L)."""
+        x = _need(x, torch.float32, self.device, "x", 2)
+        if tuple(x.shape) != (self.n_in, self.L):
+            raise ValueError(f"x must be [{self.n_in}, {self.L}]")
+        if out is None:
+            out = torch.empty((self.n_mix, self.L), dtype=torch.float32, device=self.device)
+        _need(out, torch.float32, self.device, "out", 2)
+        for t, nm, dt in ((sel_a, "sel_a", torch.int32), (sel_b, "sel_b", torch.int32),
+                          (sel_alpha, "sel_alpha", torch.float32)):
+            if t is not None:
+                _need(t, dt, self.device, nm, 1)
+                if t.shape[0] != self.n_out:
+                    raise ValueError(f"{nm} must have n_out entries")
+        self._call("tvolap_process_block_mix", _ptr(x), _ptr(out), _ptr(sel_a), _ptr(sel_b),
                    _ptr(sel_alpha))
         return out
 

@@ -78,6 +78,11 @@ def test_null_handle_calls(lib):
     assert lib.tvolap_check(None) == -4
     assert lib.tvolap_reset(None) == -4
     assert lib.tvolap_process_block(None, None, None, None, None, None) == -4
+    # the mixdown entry points
+    assert lib.tvolap_set_mix(None, 0, None) == -4
+    assert lib.tvolap_mix(None, None, 0, None) == -4
+    assert lib.tvolap_process_signal_mix(None, None, 0, 0, None, None, None, 0, None, 0, 0) == -4
+    assert lib.tvolap_process_block_mix(None, None, None, None, None, None) == -4
 
 
 @pytest.mark.parametrize("args", [

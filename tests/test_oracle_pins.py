@@ -106,6 +106,29 @@ def test_channels_are_independent():
         np.testing.assert_array_equal(y[o], ym)
 
 
+def test_mixdown_of_paths_equals_one_path_with_summed_taps():
+    """Mixdown (the sum of outputs per mix output): two paths reading the same
+    input through fixed responses h1 and h2 and mixed together equal one path
+    with the response h1 + h2 (linearity of convolution), and paths with h and
+    -h cancel exactly; each is checked against numpy.convolve as well."""
+    rng = np.random.default_rng(31)
+    L, N, ir_len = 8, 150, 40
+    x = rng.standard_normal(N)
+    h1, h2 = rng.standard_normal(ir_len), rng.standard_normal(ir_len)
+    irs = np.stack([h1, h2, -h1])
+    nb = oracle.n_out_blocks(N, L)
+    sched = np.array([[0] * nb, [1] * nb, [2] * nb], np.int32)
+    y = oracle.tvolap_direct(x, irs, L, sched, out_to_in=[0, 0, 0])
+    mixed = oracle.mixdown(y, [0, 0, 1], n_mix=3)
+    ref = np.convolve(x, h1 + h2)[:N]
+    assert _rel(mixed[0], ref) < 1e-12
+    assert _rel(mixed[1], -np.convolve(x, h1)[:N]) < 1e-12
+    assert not mixed[2].any()                                   # no member: silent
+    # h and -h routed to one mix output cancel to rounding
+    cancel = oracle.mixdown(y[[0, 2]], [0, 0])
+    assert np.max(np.abs(cancel)) <= 1e-12 * np.max(np.abs(y[0]))
+
+
 # --------------------------------------------------------------------- closed form, Fig. 3
 @pytest.mark.parametrize("L,M,d,A", [(8, 4, 3, 10), (8, 4, 21, 12), (16, 2, 40, 9), (4, 3, 17, 15)])
 def test_polarity_switch_closed_form(L, M, d, A):
