@@ -392,6 +392,34 @@ TVOLAP_API int tvolap_process_block_mix(tvolap_t h, const float *in_dev, float *
                                         const int32_t *sel_a, const int32_t *sel_b,
                                         const float *sel_alpha);
 
+/* ========================================================================
+ * Streaming-state snapshot (serving resilience: checkpoint a stream, resume
+ * it later or on another plan of the same shape). The state is what
+ * tvolap_process_block / tvolap_process_block_mix carry from tick to tick:
+ * the frequency-domain delay line, the input history, the pending
+ * overlap-add sums (of the outputs and of the mix outputs), the current
+ * selection and the block counter. The filter bank is not part of it.
+ * ======================================================================== */
+
+/* Bytes of a snapshot of this plan (a 256-byte aligned layout: a header
+   with the plan's shape and block counter, then the arrays). */
+TVOLAP_API int64_t tvolap_state_bytes(tvolap_t h);
+
+/*
+ * Copy the streaming state into buf (host or device memory, cap bytes >=
+ * tvolap_state_bytes), ordered after the work already on the plan's stream;
+ * returns when the copy is complete (synchronises the stream).
+ */
+TVOLAP_API int tvolap_get_state(tvolap_t h, void *buf, int64_t cap);
+
+/*
+ * Restore a snapshot (host or device memory) taken from a plan with the same
+ * L, M, n_in, n_out and number of mix outputs; TVOLAP_ERR_ARG if the shape
+ * or the format differs (the plan is then unchanged). Synchronises the
+ * stream. The next tick continues exactly where the snapshot was taken.
+ */
+TVOLAP_API int tvolap_set_state(tvolap_t h, const void *buf, int64_t bytes);
+
 /* Options of tvolap_set_option. */
 typedef enum tvolap_option {
     /* Staging of the offline multiply-accumulate: 0 = tiled bulk tensor copies

@@ -48,6 +48,9 @@ SIGNATURES = {
     "tvolap_check": (c_int, [c_void_p]),
     "tvolap_set_option": (c_int, [c_void_p, c_int, c_int]),
     "tvolap_set_mix": (c_int, [c_void_p, c_int, c_void_p]),
+    "tvolap_state_bytes": (c_int64, [c_void_p]),
+    "tvolap_get_state": (c_int, [c_void_p, c_void_p, c_int64]),
+    "tvolap_set_state": (c_int, [c_void_p, c_void_p, c_int64]),
     "tvolap_mix": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
     "tvolap_process_signal_mix": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p,
                                           c_void_p, c_void_p, c_int64, c_void_p, c_int64,

@@ -129,6 +129,48 @@ cudaError_t ensure_overflow(tvolap_plan *h, int64_t entries)
 
 }  // namespace tvolap
 
+// Streaming-state snapshot: a header, then each array at a 256-byte aligned
+// offset (delay line, input history, pending sums, selection, mix pending sums).
+namespace {
+
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t L, M, n_in, n_out, n_mix, pad;
+    int64_t tick;
+};
+constexpr uint32_t STATE_MAGIC = 0x54535654u;   // "TVST"
+constexpr uint32_t STATE_VERSION = 1;
+
+struct StatePart {
+    void *dev;
+    int64_t bytes;
+};
+
+int state_parts(tvolap_plan *h, StatePart (&p)[7])
+{
+    const int64_t P = h->P, L = h->L;
+    p[0] = {h->ring, (int64_t)sizeof(float2) * h->n_in * 2 * h->M * P};
+    p[1] = {h->hist, (int64_t)sizeof(float) * h->n_in * L};
+    p[2] = {h->ola, (int64_t)sizeof(float) * h->n_out * 3 * L};
+    p[3] = {h->sel_a, (int64_t)sizeof(int32_t) * h->n_out};
+    p[4] = {h->sel_b, (int64_t)sizeof(int32_t) * h->n_out};
+    p[5] = {h->sel_alpha, (int64_t)sizeof(float) * h->n_out};
+    p[6] = {h->mix_ola, (int64_t)sizeof(float) * h->n_mix * 3 * L};
+    return 7;
+}
+
+int64_t align256(int64_t v) { return (v + 255) & ~(int64_t)255; }
+
+int64_t state_bytes(tvolap_plan *h)
+{
+    StatePart p[7];
+    int64_t off = align256(sizeof(StateHeader));
+    for (int i = 0, n = state_parts(h, p); i < n; ++i) off += align256(p[i].bytes);
+    return off;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *tvolap_strerror(int status)
@@ -604,6 +646,57 @@ int tvolap_process_block_mix(tvolap_t h, const float *in_dev, float *out_dev, co
     if (e == cudaSuccess) e = launch_inverse_stream(h, out_dev, h->Ymix_stream, h->mix_ola, h->n_mix);
     if (e != cudaSuccess) return cuda_status(e);
     h->tick += 1;
+    return TVOLAP_OK;
+}
+
+int64_t tvolap_state_bytes(tvolap_t h)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    return state_bytes(h);
+}
+
+int tvolap_get_state(tvolap_t h, void *buf, int64_t cap)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (!buf || cap < state_bytes(h)) return TVOLAP_ERR_ARG;
+    const StateHeader hd{STATE_MAGIC, STATE_VERSION, h->L, h->M, h->n_in, h->n_out, h->n_mix, 0,
+                         h->tick};
+    char *dst = static_cast<char *>(buf);
+    cudaError_t e = cudaMemcpyAsync(dst, &hd, sizeof(hd), cudaMemcpyDefault, h->stream);
+    StatePart p[7];
+    int64_t off = align256(sizeof(StateHeader));
+    for (int i = 0, n = state_parts(h, p); i < n && e == cudaSuccess; ++i) {
+        if (p[i].bytes)
+            e = cudaMemcpyAsync(dst + off, p[i].dev, (size_t)p[i].bytes, cudaMemcpyDefault, h->stream);
+        off += align256(p[i].bytes);
+    }
+    // the header is read from this stack frame: wait for the copies
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_status(e);
+}
+
+int tvolap_set_state(tvolap_t h, const void *buf, int64_t bytes)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (!buf || bytes < state_bytes(h)) return TVOLAP_ERR_ARG;
+    StateHeader hd;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&hd, buf, sizeof(hd), cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (hd.magic != STATE_MAGIC || hd.version != STATE_VERSION || hd.L != h->L || hd.M != h->M ||
+        hd.n_in != h->n_in || hd.n_out != h->n_out || hd.n_mix != h->n_mix || hd.tick < 0)
+        return TVOLAP_ERR_ARG;
+    const char *src = static_cast<const char *>(buf);
+    StatePart p[7];
+    int64_t off = align256(sizeof(StateHeader));
+    for (int i = 0, n = state_parts(h, p); i < n && e == cudaSuccess; ++i) {
+        if (p[i].bytes)
+            e = cudaMemcpyAsync(p[i].dev, src + off, (size_t)p[i].bytes, cudaMemcpyDefault, h->stream);
+        off += align256(p[i].bytes);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    h->tick = hd.tick;
     return TVOLAP_OK;
 }
 

@@ -153,6 +153,30 @@ class Plan:
                    _ptr(sel_alpha))
         return out
 
+    # ------------------------------------------------------------------ state
+    def state_bytes(self) -> int:
+        n = int(self.lib.tvolap_state_bytes(self.h))
+        if n < 0:
+            _lib.check(n, "tvolap_state_bytes")
+        return n
+
+    def get_state(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Snapshot of the streaming state into a uint8 tensor (device by
+        default; a CPU tensor works too)."""
+        n = self.state_bytes()
+        if out is None:
+            out = torch.empty(n, dtype=torch.uint8, device=self.device)
+        if out.dtype != torch.uint8 or not out.is_contiguous() or out.numel() < n:
+            raise ValueError(f"out must be a contiguous uint8 tensor of >= {n} bytes")
+        self._call("tvolap_get_state", ctypes.c_void_p(out.data_ptr()), out.numel())
+        return out
+
+    def set_state(self, state: torch.Tensor):
+        """Restore a snapshot from get_state (same plan shape)."""
+        if state.dtype != torch.uint8 or not state.is_contiguous():
+            raise ValueError("state must be a contiguous uint8 tensor")
+        self._call("tvolap_set_state", ctypes.c_void_p(state.data_ptr()), state.numel())
+
     # ------------------------------------------------------------------ mixdown
     def set_mix(self, mix_of_out, n_mix: int | None = None):
         """Sum plan outputs into n_mix mix outputs before the inverse transform:

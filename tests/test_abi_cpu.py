@@ -83,6 +83,10 @@ def test_null_handle_calls(lib):
     assert lib.tvolap_mix(None, None, 0, None) == -4
     assert lib.tvolap_process_signal_mix(None, None, 0, 0, None, None, None, 0, None, 0, 0) == -4
     assert lib.tvolap_process_block_mix(None, None, None, None, None, None) == -4
+    # the streaming-state snapshot
+    assert lib.tvolap_state_bytes(None) == -4
+    assert lib.tvolap_get_state(None, None, 0) == -4
+    assert lib.tvolap_set_state(None, None, 0) == -4
 
 
 @pytest.mark.parametrize("args", [

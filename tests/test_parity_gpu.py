@@ -350,3 +350,46 @@ def test_streaming_set_filter_and_select():
     sa[0, 20:], sb[0, 20:], al[0, 20:] = 0, 1, 0.25
     ref = oracle.tvolap_direct(x, irs_o, L, sa, sb, al)
     _assert_close(y, ref, "set_filter/select")
+
+
+# ------------------------------------------------------------------ state snapshot
+@pytest.mark.parametrize("where", ["cuda", "cpu"])
+def test_state_snapshot_resumes_bitwise(where):
+    """A snapshot taken after some ticks and restored, into the same plan and
+    into a fresh plan of the same shape, continues with the same outputs bit
+    for bit (host or device snapshot buffer); a plan of another shape refuses it."""
+    from paper_2310_00319_gb300 import TvolapError
+    dev = _dev()
+    L = 128
+    N = 30 * L
+    wl = W.random_case(80, L=L, ir_len=1500, N=N, n_in=2, n_out=3, n_slots=3,
+                       out_to_in=[0, 1, 1])
+    plan = _plan(wl, dev)
+    xd = _t(wl.x, dev)
+    sa, sb, sal = _t(wl.sched_a.T.copy(), dev), _t(wl.sched_b.T.copy(), dev), \
+        _t(wl.sched_alpha.T.copy(), dev)
+
+    def tick(p, t):
+        return p.process_block(xd[:, t * L:(t + 1) * L].contiguous(), None, sa[t], sb[t],
+                               sal[t]).clone()
+
+    for t in range(12):
+        tick(plan, t)
+    buf = torch.empty(plan.state_bytes(), dtype=torch.uint8,
+                      device=dev if where == "cuda" else "cpu")
+    if where == "cpu":
+        buf = buf.pin_memory()
+    plan.get_state(buf)
+    first = torch.cat([tick(plan, t) for t in range(12, 20)], dim=1).cpu().numpy()
+    plan.set_state(buf)
+    again = torch.cat([tick(plan, t) for t in range(12, 20)], dim=1).cpu().numpy()
+    np.testing.assert_array_equal(again, first)
+    other = _plan(wl, dev)
+    other.set_state(buf)
+    moved = torch.cat([tick(other, t) for t in range(12, 20)], dim=1).cpu().numpy()
+    np.testing.assert_array_equal(moved, first)
+    plan.check()
+    from paper_2310_00319_gb300 import Plan
+    wrong = Plan(L, wl.M + 1, n_in=2, n_out=3, out_to_in=[0, 1, 1], n_slots=3, device=dev)
+    with pytest.raises(TvolapError):
+        wrong.set_state(buf)
