@@ -620,6 +620,24 @@ TVOLAP_API int tvolap_server_footprint(tvolap_server_t s, int L, int M, int n_ou
 TVOLAP_API int tvolap_server_admit(tvolap_server_t s, int L, int M, int n_out, int n_filters,
                                    const float *ir_dev, int ir_len, int64_t ir_stride, int *id);
 
+/*
+ * Stream snapshots (serving resilience, migration between slots or servers):
+ * tvolap_server_stream_bytes gives the bytes of stream id's snapshot (a
+ * 256-byte header, then its arena piece: transformed filters, delay line,
+ * pending overlap-add sums, input history). tvolap_server_snapshot completes
+ * the ticks in flight (as tvolap_server_wait, whose status it returns) and
+ * copies the stream into buf (host or device memory, cap bytes).
+ * tvolap_server_restore admits a new stream from a snapshot taken on a
+ * server with the same hop range: a new slot and piece (TVOLAP_ERR_CAPACITY
+ * when none is free), the piece copied on the admission stream, the block
+ * counter and the selected filter restored; it becomes live like an admitted
+ * stream and continues exactly where the snapshot was taken. Migrating a
+ * stream: snapshot, retire, restore.
+ */
+TVOLAP_API int tvolap_server_stream_bytes(tvolap_server_t s, int id, int64_t *bytes);
+TVOLAP_API int tvolap_server_snapshot(tvolap_server_t s, int id, void *buf, int64_t cap);
+TVOLAP_API int tvolap_server_restore(tvolap_server_t s, const void *buf, int64_t bytes, int *id);
+
 /* Retire a stream: it is never due again and its slot and memory are free. */
 TVOLAP_API int tvolap_server_retire(tvolap_server_t s, int id);
 

@@ -98,6 +98,9 @@ SIGNATURES = {
     "tvolap_server_admit": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_int64,
                                     P_int]),
     "tvolap_server_retire": (c_int, [c_void_p, c_int]),
+    "tvolap_server_stream_bytes": (c_int, [c_void_p, c_int, P_int64]),
+    "tvolap_server_snapshot": (c_int, [c_void_p, c_int, c_void_p, c_int64]),
+    "tvolap_server_restore": (c_int, [c_void_p, c_void_p, c_int64, P_int]),
     "tvolap_server_state": (c_int, [c_void_p, c_int, P_int, P_int64, P_int]),
     "tvolap_server_staging": (c_int, [c_void_p, c_int, ctypes.POINTER(c_void_p), P_int64,
                                       ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), P_int64]),

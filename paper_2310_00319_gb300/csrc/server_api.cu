@@ -399,20 +399,18 @@ int tvolap_server_footprint(tvolap_server_t s, int L, int M, int n_out, int n_fi
     return TVOLAP_OK;
 }
 
-int tvolap_server_admit(tvolap_server_t s, int L, int M, int n_out, int n_filters,
-                        const float *ir_dev, int ir_len, int64_t ir_stride, int *id)
+}  // extern "C"
+
+namespace {
+
+// A slot and an arena piece for a new stream (admission or restore): its
+// descriptor, its admission event, and the admission stream ordered after
+// the last enqueued tick (the piece may have belonged to a retired stream
+// those ticks still read).
+int take_slot(tvolap_server *s, int L, int M, int n_out, int n_filters, int c, int *id)
 {
-    if (!s) return TVOLAP_ERR_STATE;
-    if (!id || ir_len < 0 || (int64_t)ir_len > 2 * (int64_t)L * M || (ir_len > 0 && !ir_dev) ||
-        ir_stride < ir_len)
-        return TVOLAP_ERR_ARG;
-    if (ir_dev && (reinterpret_cast<uintptr_t>(ir_dev) & 3u)) return TVOLAP_ERR_ARG;
-    int e = s->sch.check_stream_args(L, M, n_out, n_filters);
-    if (e != TVOLAP_OK) return e;
-    const int c = class_of(s, L);
-    if (c < 0) return TVOLAP_ERR_ARG;
     int i = -1;
-    e = s->sch.admit(L, M, n_out, n_filters, &i);
+    int e = s->sch.admit(L, M, n_out, n_filters, &i);
     if (e != TVOLAP_OK) return e;
     const SchedStream &ss = s->sch.st[i];
     char *base = s->arena + ss.offset;
@@ -427,17 +425,52 @@ int tvolap_server_admit(tvolap_server_t s, int L, int M, int n_out, int n_filter
     d.n_filters = n_filters;
     d.lgP = s->cls[c].lgP;
     s->desc_h[i] = d;
+    if ((!s->adm_ev[i] && cudaEventCreateWithFlags(&s->adm_ev[i], cudaEventDisableTiming) != cudaSuccess) ||
+        (s->seq > 0 && cudaStreamWaitEvent(s->adm, s->tick_ev[(s->seq - 1) & 1], 0) != cudaSuccess)) {
+        s->sch.retire(i);
+        return TVOLAP_ERR_CUDA;
+    }
+    *id = i;
+    return TVOLAP_OK;
+}
+
+// Stream snapshot: this header, then the stream's arena piece (transformed
+// filters, delay line, pending sums, input history) at byte 256.
+struct StreamSnapHeader {
+    uint32_t magic, version;
+    int32_t L, M, n_out, n_filters, sel, pad;
+    int64_t blocks, piece;
+};
+constexpr uint32_t SNAP_MAGIC = 0x53535654u;   // "TVSS"
+constexpr int64_t SNAP_DATA = 256;
+static_assert(sizeof(StreamSnapHeader) <= SNAP_DATA, "snapshot header");
+
+}  // namespace
+
+extern "C" {
+
+int tvolap_server_admit(tvolap_server_t s, int L, int M, int n_out, int n_filters,
+                        const float *ir_dev, int ir_len, int64_t ir_stride, int *id)
+{
+    if (!s) return TVOLAP_ERR_STATE;
+    if (!id || ir_len < 0 || (int64_t)ir_len > 2 * (int64_t)L * M || (ir_len > 0 && !ir_dev) ||
+        ir_stride < ir_len)
+        return TVOLAP_ERR_ARG;
+    if (ir_dev && (reinterpret_cast<uintptr_t>(ir_dev) & 3u)) return TVOLAP_ERR_ARG;
+    int e = s->sch.check_stream_args(L, M, n_out, n_filters);
+    if (e != TVOLAP_OK) return e;
+    const int c = class_of(s, L);
+    if (c < 0) return TVOLAP_ERR_ARG;
+    int i = -1;
+    e = take_slot(s, L, M, n_out, n_filters, c, &i);
+    if (e != TVOLAP_OK) return e;
+    const SchedStream &ss = s->sch.st[i];
+    char *base = s->arena + ss.offset;
+    const SrvDesc &d = s->desc_h[i];
     auto undo = [&](int code) {
         s->sch.retire(i);
         return code;
     };
-    if (!s->adm_ev[i] && cudaEventCreateWithFlags(&s->adm_ev[i], cudaEventDisableTiming) != cudaSuccess)
-        return undo(TVOLAP_ERR_CUDA);
-    // the piece may have belonged to a retired stream still read by enqueued ticks
-    if (s->seq > 0) {
-        const int lb = (int)((s->seq - 1) & 1);
-        if (cudaStreamWaitEvent(s->adm, s->tick_ev[lb], 0) != cudaSuccess) return undo(TVOLAP_ERR_CUDA);
-    }
     if (cudaMemsetAsync(base + ss.lay.ring, 0, ss.lay.total - ss.lay.ring, s->adm) != cudaSuccess)
         return undo(TVOLAP_ERR_CUDA);
     const int64_t count = (int64_t)n_filters * n_out;
@@ -449,6 +482,63 @@ int tvolap_server_admit(tvolap_server_t s, int L, int M, int n_out, int n_filter
         ce = cudaMemsetAsync(d.bank, 0, ss.lay.ring, s->adm);
     if (ce != cudaSuccess) return undo(TVOLAP_ERR_CUDA);
     if (cudaEventRecord(s->adm_ev[i], s->adm) != cudaSuccess) return undo(TVOLAP_ERR_CUDA);
+    s->pending.push_back(i);
+    *id = i;
+    return TVOLAP_OK;
+}
+
+int tvolap_server_stream_bytes(tvolap_server_t s, int id, int64_t *bytes)
+{
+    if (!s) return TVOLAP_ERR_STATE;
+    if (!bytes || !s->sch.valid_id(id)) return TVOLAP_ERR_ARG;
+    *bytes = SNAP_DATA + s->sch.st[id].lay.total;
+    return TVOLAP_OK;
+}
+
+int tvolap_server_snapshot(tvolap_server_t s, int id, void *buf, int64_t cap)
+{
+    if (!s) return TVOLAP_ERR_STATE;
+    if (!buf || !s->sch.valid_id(id)) return TVOLAP_ERR_ARG;
+    const SchedStream &ss = s->sch.st[id];
+    if (cap < SNAP_DATA + ss.lay.total) return TVOLAP_ERR_ARG;
+    const int e = finish(s);                // ticks in flight and admissions complete
+    if (e != TVOLAP_OK) return e;
+    const StreamSnapHeader hd{SNAP_MAGIC, 1, ss.L, ss.M, ss.n_out, ss.n_filters, s->sel_h[id], 0,
+                              ss.blocks, ss.lay.total};
+    char *dst = static_cast<char *>(buf);
+    if (cudaMemcpy(dst, &hd, sizeof(hd), cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(dst + SNAP_DATA, s->arena + ss.offset, (size_t)ss.lay.total, cudaMemcpyDefault) !=
+            cudaSuccess)
+        return TVOLAP_ERR_CUDA;
+    return TVOLAP_OK;
+}
+
+int tvolap_server_restore(tvolap_server_t s, const void *buf, int64_t bytes, int *id)
+{
+    if (!s) return TVOLAP_ERR_STATE;
+    if (!buf || !id || bytes < SNAP_DATA) return TVOLAP_ERR_ARG;
+    StreamSnapHeader hd;
+    if (cudaMemcpy(&hd, buf, sizeof(hd), cudaMemcpyDefault) != cudaSuccess) return TVOLAP_ERR_CUDA;
+    if (hd.magic != SNAP_MAGIC || hd.version != 1 || hd.blocks < 0) return TVOLAP_ERR_ARG;
+    int e = s->sch.check_stream_args(hd.L, hd.M, hd.n_out, hd.n_filters);
+    if (e != TVOLAP_OK) return e;
+    const int c = class_of(s, hd.L);
+    if (c < 0 || hd.sel < 0 || hd.sel >= hd.n_filters) return TVOLAP_ERR_ARG;
+    if (stream_layout(hd.L, hd.M, hd.n_out, hd.n_filters).total != hd.piece ||
+        bytes < SNAP_DATA + hd.piece)
+        return TVOLAP_ERR_ARG;
+    int i = -1;
+    e = take_slot(s, hd.L, hd.M, hd.n_out, hd.n_filters, c, &i);
+    if (e != TVOLAP_OK) return e;
+    const SchedStream &ss = s->sch.st[i];
+    if (cudaMemcpyAsync(s->arena + ss.offset, static_cast<const char *>(buf) + SNAP_DATA,
+                        (size_t)hd.piece, cudaMemcpyDefault, s->adm) != cudaSuccess ||
+        cudaEventRecord(s->adm_ev[i], s->adm) != cudaSuccess) {
+        s->sch.retire(i);
+        return TVOLAP_ERR_CUDA;
+    }
+    s->sch.st[i].blocks = hd.blocks;
+    s->sel_h[i] = hd.sel;
     s->pending.push_back(i);
     *id = i;
     return TVOLAP_OK;

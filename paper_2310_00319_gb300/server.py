@@ -116,6 +116,27 @@ class Server:
     def retire(self, i: int):
         self._call("tvolap_server_retire", int(i))
 
+    def snapshot(self, i: int, out=None):
+        """Stream i's transformed filters and streaming state (after the ticks
+        in flight) as a uint8 tensor (device by default, or into out)."""
+        import torch
+        n = ctypes.c_int64()
+        self._call("tvolap_server_stream_bytes", int(i), ctypes.byref(n))
+        if out is None:
+            out = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+        if out.dtype != torch.uint8 or not out.is_contiguous() or out.numel() < n.value:
+            raise ValueError(f"out must be a contiguous uint8 tensor of >= {n.value} bytes")
+        self._call("tvolap_server_snapshot", int(i), ctypes.c_void_p(out.data_ptr()), out.numel())
+        return out
+
+    def restore(self, snap) -> int:
+        """Admit a stream from a snapshot (this or another server with the
+        same hops); it continues where the snapshot was taken. Returns its id."""
+        i = ctypes.c_int()
+        self._call("tvolap_server_restore", ctypes.c_void_p(snap.data_ptr()), snap.numel(),
+                   ctypes.byref(i))
+        return i.value
+
     def state(self, i: int):
         st, bl, ph = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
         self._call("tvolap_server_state", int(i), ctypes.byref(st), ctypes.byref(bl),

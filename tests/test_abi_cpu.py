@@ -87,6 +87,9 @@ def test_null_handle_calls(lib):
     assert lib.tvolap_state_bytes(None) == -4
     assert lib.tvolap_get_state(None, None, 0) == -4
     assert lib.tvolap_set_state(None, None, 0) == -4
+    assert lib.tvolap_server_stream_bytes(None, 0, None) == -4
+    assert lib.tvolap_server_snapshot(None, 0, None, 0) == -4
+    assert lib.tvolap_server_restore(None, None, 0, None) == -4
 
 
 @pytest.mark.parametrize("args", [

@@ -312,3 +312,73 @@ def test_pipelined_ticks_equal_one_at_a_time():
     srv.close()
     for a, b in zip(ref, outs):
         np.testing.assert_array_equal(a, b)
+
+
+def _feed(srv, sid, s, b0, b1, extra=()):
+    """Feed stream s's blocks b0 .. b1-1 to stream id sid (and silence with
+    filter 0 to the extra stream ids); returns sid's output blocks [2, b1-b0, L]."""
+    outs, b = [], b0
+    for _ in range(100 * (b1 - b0) + 100):
+        if b == b1:
+            break
+        due = [int(v) for v in srv.due()]
+        for x in due:
+            if x == sid:
+                assert srv.state(sid)[1] == b
+                srv.inp[x, :s.L] = s.x[b * s.L:(b + 1) * s.L]
+                srv.sel[x] = s.sel[b]
+            else:
+                assert x in extra
+                srv.inp[x, :] = 0.0
+                srv.sel[x] = 0
+        srv.tick()
+        srv.wait()
+        if sid in due:
+            outs.append(np.array(srv.out[sid, :2, :s.L]))
+            b += 1
+    assert b == b1, "stream did not run"
+    return np.stack(outs, 1)
+
+
+@pytest.mark.parametrize("where", ["cuda", "cpu"])
+def test_snapshot_restore_and_migration_bitwise(where):
+    """A stream snapshotted after some blocks continues bit for bit when
+    restored: into another slot of the same server after retiring it
+    (migration), and into a fresh server with other streams around it."""
+    dev = _dev()
+    A = W.serving_streams(90, 1, hops=(32,), blocks=(50, 50))[0]
+    B = W.serving_streams(91, 2, hops=(16, 64), blocks=(50, 50))
+    srv = _server(dev)
+    other = srv.admit(B[0].L, _irs(B[0], 2, dev))          # takes the first slot and piece
+    sid = srv.admit(A.L, _irs(A, 2, dev))
+    _feed(srv, sid, A, 0, 20, extra=(other,))
+    if where == "cuda":
+        snap = srv.snapshot(sid)
+    else:
+        n = srv.snapshot(sid).numel()
+        snap = srv.snapshot(sid, torch.empty(n, dtype=torch.uint8).pin_memory())
+    ref = _feed(srv, sid, A, 20, 50, extra=(other,))
+    # migration: retire, then restore into the same server (another slot / piece)
+    srv.retire(sid)
+    srv.retire(other)
+    late = [srv.admit(b.L, _irs(b, 2, dev)) for b in B]    # take the old slots first
+    sid2 = srv.restore(snap)
+    assert sid2 not in (sid, other)
+    got = _feed(srv, sid2, A, 20, 50, extra=tuple(late))
+    np.testing.assert_array_equal(got, ref)
+    srv.close()
+    # a fresh server
+    srv2 = _server(dev)
+    sid3 = srv2.restore(snap)
+    got2 = _feed(srv2, sid3, A, 20, 50)
+    np.testing.assert_array_equal(got2, ref)
+    srv2.close()
+
+
+def test_restore_rejects_a_foreign_buffer():
+    from paper_2310_00319_gb300 import TvolapError
+    dev = _dev()
+    srv = _server(dev)
+    with pytest.raises(TvolapError):
+        srv.restore(torch.zeros(4096, dtype=torch.uint8, device=dev))
+    srv.close()
