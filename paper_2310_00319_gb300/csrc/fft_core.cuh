@@ -113,13 +113,20 @@ __host__ __device__ constexpr int tw_offset(int P, int Ns)
 __host__ __device__ constexpr int tw_size(int P) { return tw_offset(P, P); }
 
 // Between stages the transform lives in shared memory in a swizzled order:
-// value n sits at swz(n), which permutes the 16 values of each 128-byte row by
-// XOR with the row index. The butterflies' scattered stores (index 8j + s at
-// the first stage, (j/8) 64 + j mod 8 + 8s at the second) then spread over all
-// banks instead of hitting every second or eighth row's banks; the strided
-// loads stay one row per half warp. A transform's input (filled by the caller)
-// and output are in natural order.
-__device__ __forceinline__ int swz(int n) { return n ^ ((n >> 4) & 15); }
+// value n sits at swz(n), which permutes the 16 values of each 128-byte row r
+// by XOR with g(r) = (r mod 8) + 8 * (bit 2 of r). A 64-bit shared access is
+// served half a warp at a time, so the scattered stores of the first stage
+// (index 8j + s: rows j/2, positions 8 (j mod 2) + s) and of the second
+// ((j/8) 64 + j mod 8 + 8s: rows 4 (j/8) + s/2) must put each half warp's 16
+// values on 16 different positions: the first needs g mod 8 distinct over 8
+// consecutive rows, the second different bit 3 in rows r and r + 4. The
+// strided loads stay one row per half warp. A transform's input (filled by
+// the caller) and output are in natural order.
+__device__ __forceinline__ int swz(int n)
+{
+    const int r = n >> 4;
+    return n ^ ((r & 7) | ((r & 4) << 1));
+}
 
 // One Stockham stage of radix R on a P-point transform: butterfly j reads
 // src[j + r P/R], rotates input r by the twiddle r * (j mod Ns) / (Ns R) of a
