@@ -1212,7 +1212,7 @@ def main():
                     help="serve: ticks of the latency run (throughput run: 3/4 of it)")
     ap.add_argument("--adj-channels", type=int, default=16,
                     help="adjoint: channels of the differentiable workload")
-    ap.add_argument("--staging", type=int, default=None, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--staging", type=int, default=None, choices=[0, 1, 2, 3, 4, 5],
                     help="multiply-accumulate staging (default workload: instead of the default; "
                          "batched: instead of the autotuner)")
     ap.add_argument("--skip-extras", action="store_true")

@@ -429,9 +429,10 @@ typedef enum tvolap_option {
        group per CTA, up to four distinct filters per group (for schedules that
        cycle four filters; fewer resident groups per SM); 3 = TMA, one group
        per CTA, up to three filters; 4 = as 3 with two adjacent bins per thread
-       when 2L is a multiple of 64 (fastest for slowly changing filters).
-       0, 1, 3 and 4 give identical results; 2 differs from them only in the
-       rounding of blocks whose group holds four filters. */
+       when 2L is a multiple of 64 (fastest for slowly changing filters);
+       5 = as 0 with up to four filters per group. 0, 1, 3 and 4 give
+       identical results, and so do 2 and 5; 2 and 5 differ from the others
+       only in the rounding of blocks whose group holds four filters. */
     TVOLAP_OPT_MAC_STAGING = 1
 } tvolap_option;
 
@@ -516,7 +517,7 @@ TVOLAP_API int tvolap_batch_run(tvolap_batch_t b);
 TVOLAP_API int tvolap_batch_capture(tvolap_batch_t b);
 
 /*
- * For every hop group, time each multiply-accumulate staging (0 .. 4) over
+ * For every hop group, time each multiply-accumulate staging (0 .. 5) over
  * reps runs on the batch itself and keep the fastest; drops a captured graph.
  * chosen (may be NULL): host int [number of groups], the staging per group in
  * increasing hop order. Synchronises.

@@ -704,7 +704,7 @@ int tvolap_set_option(tvolap_t h, int option, int value)
 {
     if (!h) return TVOLAP_ERR_STATE;
     if (option == TVOLAP_OPT_MAC_STAGING) {
-        if (value < 0 || value > 4) return TVOLAP_ERR_ARG;
+        if (value < 0 || value > 5) return TVOLAP_ERR_ARG;
         h->mac_variant = value;
         return TVOLAP_OK;
     }

@@ -300,7 +300,7 @@ int tvolap_batch_autotune(tvolap_batch_t b, int reps, int *chosen)
         BatchGroup &g = b->groups[gi];
         float best = -1.f;
         int best_opt = 0;
-        for (int opt = 0; opt <= 4 && status == TVOLAP_OK; ++opt) {
+        for (int opt = 0; opt <= 5 && status == TVOLAP_OK; ++opt) {
             status = tvolap_set_option(g.plan, TVOLAP_OPT_MAC_STAGING, opt);
             if (status != TVOLAP_OK || g.max_out == 0) break;
             auto one = [&]() {
@@ -335,7 +335,7 @@ int tvolap_batch_autotune(tvolap_batch_t b, int reps, int *chosen)
 int tvolap_batch_set_staging(tvolap_batch_t b, int g, int staging)
 {
     if (!b) return TVOLAP_ERR_STATE;
-    if (g < -1 || g >= (int)b->groups.size() || staging < 0 || staging > 4) return TVOLAP_ERR_ARG;
+    if (g < -1 || g >= (int)b->groups.size() || staging < 0 || staging > 5) return TVOLAP_ERR_ARG;
     for (int k = 0; k < (int)b->groups.size(); ++k) {
         if (g != -1 && k != g) continue;
         const int e = tvolap_set_option(b->groups[k].plan, TVOLAP_OPT_MAC_STAGING, staging);

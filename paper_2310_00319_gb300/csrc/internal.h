@@ -38,7 +38,8 @@ struct tvolap_plan {
     int mac_variant;              // 0: TMA staging, persistent groups of <= 3 slots (when
                                   // the buffers allow TMA), 1: cp.async staging, 2: TMA,
                                   // groups of <= 4 slots, 3: TMA, one group of <= 3 slots
-                                  // per CTA, 4: as 3 with two bins per thread
+                                  // per CTA, 4: as 3 with two bins per thread,
+                                  // 5: as 0 with groups of <= 4 slots
     int4 *ovf_list;               // groups the group kernel hands to the per-warp kernel
     int *ovf_count;
     int64_t ovf_cap;

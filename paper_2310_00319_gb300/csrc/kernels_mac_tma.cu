@@ -1095,9 +1095,12 @@ cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, con
     e = cudaMemsetAsync(h->ovf_count, 0, 2 * sizeof(int), h->stream);   // overflow count, work counter
     if (e != cudaSuccess) return e;
     // 0: persistent groups; 2: groups of up to four filters; 3: one group per
-    // CTA; 4: as 3 with two bins per thread where the bins split into 64-bin tiles
+    // CTA; 4: as 3 with two bins per thread where the bins split into 64-bin
+    // tiles; 5: persistent groups of up to four filters
     if (h->mac_variant == 0)
         e = launch_persist<3, 1, 3, 4>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
+    else if (h->mac_variant == 5)
+        e = launch_persist<4, 1, 4, 3>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
     else if (h->mac_variant == 2)
         e = launch_group<4, 1>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
     else if (h->mac_variant == 4 && h->P % 64 == 0)

@@ -105,7 +105,8 @@ class Plan:
     def set_option(self, option: int, value: int):
         """TVOLAP_OPT_MAC_STAGING (1): 0 = persistent TMA groups (default),
         1 = cp.async, 2 = TMA groups of up to four filters, 3 = one TMA group
-        per CTA, 4 = as 3 with two bins per thread."""
+        per CTA, 4 = as 3 with two bins per thread, 5 = as 0 with up to four
+        filters per group."""
         self._call("tvolap_set_option", int(option), int(value))
 
     def check(self):

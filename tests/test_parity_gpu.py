@@ -242,14 +242,14 @@ def test_mac_staging_variants_agree_bitwise(L, n_slots, interp):
 
 
 def test_staging_option_range():
-    """TVOLAP_OPT_MAC_STAGING takes 0 .. 4; other values and options are refused."""
+    """TVOLAP_OPT_MAC_STAGING takes 0 .. 5; other values and options are refused."""
     from paper_2310_00319_gb300 import TvolapError
     dev = _dev()
     wl = W.random_case(3, L=64, ir_len=300, N=2000, n_slots=2)
     plan = _plan(wl, dev)
-    for v in range(5):
+    for v in range(6):
         plan.set_option(1, v)
-    for opt, v in [(1, -1), (1, 5), (2, 0)]:
+    for opt, v in [(1, -1), (1, 6), (2, 0)]:
         with pytest.raises(TvolapError):
             plan.set_option(opt, v)
 
@@ -272,6 +272,8 @@ def test_mac_four_filter_groups(k):
     y0 = _run_signal(wl, dev, plan)
     plan.set_option(1, 2)
     y2 = _run_signal(wl, dev, plan)
+    plan.set_option(1, 5)                                    # persistent, four filters
+    np.testing.assert_array_equal(_run_signal(wl, dev, plan), y2)
     _assert_close(y2, _ref(wl), f"four-filter groups k={k}")
     rel = np.linalg.norm(y2 - y0) / np.linalg.norm(y0)
     assert rel <= 1e-6, rel
