@@ -1108,6 +1108,104 @@ def run_mixdown(args):
     return out
 
 
+def run_nonuniform(args):
+    """Two-level non-uniform partitions for long responses at a short hop:
+    16 channels, responses of 96000 taps (2 s at 48 kHz), head hop 64 (latency
+    128 samples) with 15 partitions, tail hop 1024 with 46 partitions, against
+    one uniform plan at hop 64 (750 partitions, the same latency). Offline:
+    one process_signal of 480000 samples per channel; streaming: mean time of
+    a hop-64 tick (every 16th also runs the tail's hop)."""
+    import torch
+    import oracle
+    from synth import workloads as W
+    from paper_2310_00319_gb300 import Plan
+    from paper_2310_00319_gb300.nonuniform import NonUniform
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    La, Ma, ratio, Mb, n_ch, ir_len = 64, 15, 16, 46, 16, 96000
+    wl = W.plain_at_scale(n_ch=n_ch, N=args.samples, L=La, ir_len=ir_len)
+    nb = wl.sched_a.shape[1]
+    stream = torch.cuda.current_stream(dev)
+    nu = NonUniform(La, Ma, ratio, Mb, n_in=n_ch, n_slots=wl.irs.shape[0], device=dev)
+    uni = Plan(La, wl.M, n_in=n_ch, n_slots=wl.irs.shape[0], device=dev)
+    irs = torch.from_numpy(wl.irs).to(dev)
+    nu.load_bank(0, irs)
+    uni.load_bank(0, irs)
+    x = torch.from_numpy(wl.x).to(dev)
+    sa, sb, sal = (torch.from_numpy(a).to(dev) for a in (wl.sched_a, wl.sched_b, wl.sched_alpha))
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / steps
+
+    with ClockSampler(dev.index) as clk:
+        ms_nu = timed(lambda: nu.process_signal(x, sa, sb, sal, out_len=wl.out_len), args.steps)
+    clocks = clk.summary()
+    ms_uni = timed(lambda: uni.process_signal(x, sa, sb, sal, out_len=wl.out_len), max(3, args.steps // 4))
+    nu.check()
+    uni.check()
+    # streaming ticks (hop 64): 1600 ticks = 100 tail hops
+    n_ticks = 1600
+    xs = x[:, :n_ticks * La].contiguous()
+    blocks = [xs[:, t * La:(t + 1) * La].contiguous() for t in range(n_ticks)]
+    out = torch.empty((n_ch, La), dtype=torch.float32, device=dev)
+    sat = sa.t().contiguous()
+
+    def ticks(obj):
+        obj.reset()
+        for t in range(n_ticks):
+            obj.process_block(blocks[t], out, sat[t])
+
+    tick_nu = timed(lambda: ticks(nu), 2) / n_ticks
+    tick_uni = timed(lambda: ticks(uni), 2) / n_ticks
+    units = n_ch * wl.out_len
+    res = {
+        "metric": METRIC, "value": round(units / (ms_nu * 1e-3), 1), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_nu, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"nonuniform_{n_ch}ch_La{La}x{ratio}_ir{ir_len}_N{wl.N}",
+                   "channels": n_ch, "head": {"hop": La, "partitions": Ma, "taps": 2 * La * Ma},
+                   "tail": {"hop": La * ratio, "partitions": Mb}, "ir_len": ir_len,
+                   "latency_samples": 2 * La, "per_gpu_units": units,
+                   "l2": "working set > 129 MB L2; no flush"},
+        "uniform_hop64": {"partitions": wl.M, "ms_per_step": round(ms_uni, 4),
+                          "speedup": round(ms_uni / ms_nu, 2)},
+        "stream_tick_ms": {"nonuniform": round(tick_nu, 4), "uniform_hop64": round(tick_uni, 4),
+                           "deadline_ms": round(La / 48.0, 4)},
+        "clocks": clocks,
+        # per process_signal: two plans' forward, MAC (+ overflow), inverse, the
+        # tail schedule and the shifted add
+        "gpu_launches": 10 * args.steps,
+    }
+    if not args.no_cpu:
+        # the oracle's two-level definition on the first 6000 samples of channel 0
+        n = 6000
+        nb_n = oracle.n_out_blocks(n, La)
+        t = time.perf_counter()
+        ref = oracle.tvolap_nonuniform(wl.x[0, :n], wl.irs, La, Ma, ratio, Mb,
+                                       wl.sched_a[:1, :nb_n], wl.sched_b[:1, :nb_n],
+                                       wl.sched_alpha[:1, :nb_n], out_len=n)
+        dt = time.perf_counter() - t
+        y = nu.process_signal(x[:, :n].contiguous(), sa[:, :nb_n].contiguous(),
+                              sb[:, :nb_n].contiguous(), sal[:, :nb_n].contiguous(),
+                              out_len=n)[:1].cpu().numpy()
+        res["accuracy"] = accuracy(y, ref)
+        res["cpu_baseline"] = {"value": round(n / dt, 1), "unit": UNIT, "cores": oracle.num_threads(),
+                               "kind": "oracle", "sample": f"{n} samples of channel 0 (both levels)"}
+    nu.close()
+    uni.close()
+    return res
+
+
 def accuracy_plain_mono(dev):
     """The mono configuration (L = 128, 96000 samples, 4 responses of 4096 taps
     switched every 16 blocks) through process_signal, against the FP64 oracle
@@ -1197,7 +1295,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain_at_scale",
-                    choices=["plain_at_scale", "adjoint", "batched", "serve", "mixdown"])
+                    choices=["plain_at_scale", "adjoint", "batched", "serve", "mixdown",
+                             "nonuniform"])
     ap.add_argument("--channels", type=int, default=64)
     ap.add_argument("--samples", type=int, default=480000)
     ap.add_argument("--ir-len", type=int, default=48000,
@@ -1230,6 +1329,8 @@ def main():
         out = run_serve(args)
     elif args.workload == "mixdown":
         out = run_mixdown(args)
+    elif args.workload == "nonuniform":
+        out = run_nonuniform(args)
     else:
         out = run_ours(args)
     if out is not None:

@@ -420,6 +420,50 @@ TVOLAP_API int tvolap_get_state(tvolap_t h, void *buf, int64_t cap);
  */
 TVOLAP_API int tvolap_set_state(tvolap_t h, const void *buf, int64_t bytes);
 
+/* ========================================================================
+ * Two-level non-uniform partitions (small first partitions, larger later
+ * ones: the partitioned-convolution lineage the paper builds on, Section 1).
+ * A head plan (hop La, Ma partitions) convolves with taps [0, D), D = 2 La Ma,
+ * at the small hop's latency; a tail plan (hop Lb = ratio * La, Mb
+ * partitions) convolves with taps [D, D + 2 Lb Mb) at a fraction of the cost
+ * per sample, and its aligned output is added D samples later. A fixed
+ * response gives exactly its full convolution (linearity and time invariance
+ * of each level); a switch crossfades in each level at that level's block
+ * boundaries. The tail's schedule entry tb is the head's entry
+ * (tb + 1) * ratio - 1 (in streaming: the head's selection when the tail's
+ * hop completes). Streaming needs Ma >= ratio - 1, so that every tail sample
+ * has been produced when the head output that adds it is emitted.
+ * ======================================================================== */
+typedef struct tvolap_nu *tvolap_nu_t;
+
+/* ratio: a power of two in [2, 64] with La * ratio <= 1024; Ma >= ratio - 1;
+   other arguments as tvolap_create (the same for both levels). */
+TVOLAP_API int tvolap_nu_create(tvolap_nu_t *out, int La, int Ma, int ratio, int Mb, int n_in,
+                                int n_out, const int32_t *out_to_in, int n_slots, void *stream);
+TVOLAP_API int tvolap_nu_destroy(tvolap_nu_t h);
+/* Zero both levels' streaming state and the tail's delay line of outputs. */
+TVOLAP_API int tvolap_nu_reset(tvolap_nu_t h);
+/* Hops, head taps D and the longest response (D + 2 Lb Mb). */
+TVOLAP_API int tvolap_nu_dims(tvolap_nu_t h, int *La, int *Lb, int64_t *head_taps,
+                              int64_t *max_taps);
+/* Stored responses of up to D + 2 Lb Mb taps: taps [0, D) go to the head's
+   slots, the rest to the tail's (as tvolap_load_bank). */
+TVOLAP_API int tvolap_nu_load_bank(tvolap_nu_t h, int first_slot, int count, const float *ir_dev,
+                                   int ir_len, int64_t ir_stride);
+/* Offline, as tvolap_process_signal; schedules are per head block (hop La). */
+TVOLAP_API int tvolap_nu_process_signal(tvolap_nu_t h, const float *x_dev, int64_t N,
+                                        int64_t x_stride, const int32_t *sched_a,
+                                        const int32_t *sched_b, const float *sched_alpha,
+                                        int64_t sched_stride, float *y_dev, int64_t out_len,
+                                        int64_t y_stride);
+/* One head hop, as tvolap_process_block (La samples in and out, output
+   delayed by La); every ratio-th call also runs the tail's hop. */
+TVOLAP_API int tvolap_nu_process_block(tvolap_nu_t h, const float *in_dev, float *out_dev,
+                                       const int32_t *sel_a, const int32_t *sel_b,
+                                       const float *sel_alpha);
+/* Deferred device errors of both levels (as tvolap_check). */
+TVOLAP_API int tvolap_nu_check(tvolap_nu_t h);
+
 /* Options of tvolap_set_option. */
 typedef enum tvolap_option {
     /* Staging of the offline multiply-accumulate: 0 = tiled bulk tensor copies

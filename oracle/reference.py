@@ -33,6 +33,12 @@ Functions and the passages of arxiv 2310.00319 they follow:
                               tests/test_oracle_grad_pins.py.
 * ``params_grad_sampled``  -- chosen entries of the same gradients, each from
                               the definitions on its own (full-size checks).
+* ``tvolap_nonuniform``    -- two-level non-uniform partitions: TVOLAP of the
+                              first D = 2 La Ma taps at hop La plus TVOLAP of
+                              the remaining taps at hop ratio * La, added D
+                              samples later (the tail's schedule entry t is
+                              the head's entry (t + 1) ratio - 1); each level is
+                              ``tvolap_direct``.
 * ``mixdown``              -- the sum of the outputs routed to each mix output
                               (Section 2's c channels summed per ear for the
                               binaural rendering of Section 5; by linearity of
@@ -199,6 +205,41 @@ def tvolap_direct(x, irs, L, sched_a, sched_b=None, sched_alpha=None, out_len=No
                              _ptr(a, ctypes.c_int), _ptr(b, ctypes.c_int),
                              _ptr(al, ctypes.c_double), int(out_len), _ptr(y, ctypes.c_double))
     return y[0] if (squeeze and n_out == 1) else y
+
+
+def tvolap_nonuniform(x, irs, La, Ma, ratio, Mb, sched_a, sched_b=None, sched_alpha=None,
+                      out_len=None, out_to_in=None):
+    """Two-level non-uniform partitioned TVOLAP (FP64).
+
+    Head: taps [0, D), D = 2 La Ma, TVOLAP at hop La with Ma partitions and the
+    given schedules (per head block). Tail: taps [D, D + 2 Lb Mb), Lb = ratio La,
+    TVOLAP at hop Lb with Mb partitions; its schedule entry t is the head's
+    entry min((t + 1) ratio - 1, last); its aligned output is added at n + D.
+    A fixed response gives its full linear convolution.
+    """
+    irs = _f64(irs).reshape(-1, np.asarray(irs).shape[-1])
+    x = _f64(x)
+    N = x.reshape(-1, x.shape[-1]).shape[1]
+    out_len = N if out_len is None else int(out_len)
+    D, Lb = 2 * La * Ma, ratio * La
+    if irs.shape[1] > D + 2 * Lb * Mb:
+        raise ValueError("responses longer than D + 2 Lb Mb")
+    head = np.zeros((irs.shape[0], D))
+    head[:, :min(D, irs.shape[1])] = irs[:, :D]
+    sa = np.atleast_2d(_i32(sched_a))
+    sb = sa if sched_b is None else np.atleast_2d(_i32(sched_b))
+    sal = np.zeros(sa.shape) if sched_alpha is None else np.atleast_2d(_f64(sched_alpha))
+    y = tvolap_direct(x, head, La, sa, sb, sal, out_len=out_len, M=Ma, out_to_in=out_to_in)
+    y = np.atleast_2d(y)
+    if irs.shape[1] > D and out_len > D:
+        tail = irs[:, D:]
+        nb_head = n_out_blocks(out_len, La)
+        tail_len = out_len - D
+        idx = np.minimum((np.arange(n_out_blocks(tail_len, Lb)) + 1) * ratio - 1, nb_head - 1)
+        yt = tvolap_direct(x, tail, Lb, sa[:, idx], sb[:, idx], sal[:, idx], out_len=tail_len,
+                           M=Mb, out_to_in=out_to_in)
+        y[:, D:] += np.atleast_2d(yt)
+    return y
 
 
 def mixdown(y, mix_of_out, n_mix=None):

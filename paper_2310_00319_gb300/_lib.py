@@ -48,6 +48,19 @@ SIGNATURES = {
     "tvolap_check": (c_int, [c_void_p]),
     "tvolap_set_option": (c_int, [c_void_p, c_int, c_int]),
     "tvolap_set_mix": (c_int, [c_void_p, c_int, c_void_p]),
+    "tvolap_nu_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int, c_int,
+                                 c_int, c_void_p,
+                                 c_int, c_void_p]),
+    "tvolap_nu_destroy": (c_int, [c_void_p]),
+    "tvolap_nu_reset": (c_int, [c_void_p]),
+    "tvolap_nu_dims": (c_int, [c_void_p, P_int, P_int, P_int64, P_int64]),
+    "tvolap_nu_load_bank": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int64]),
+    "tvolap_nu_process_signal": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p,
+                                         c_void_p, c_void_p, c_int64, c_void_p, c_int64,
+                                         c_int64]),
+    "tvolap_nu_process_block": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                        c_void_p]),
+    "tvolap_nu_check": (c_int, [c_void_p]),
     "tvolap_state_bytes": (c_int64, [c_void_p]),
     "tvolap_get_state": (c_int, [c_void_p, c_void_p, c_int64]),
     "tvolap_set_state": (c_int, [c_void_p, c_void_p, c_int64]),

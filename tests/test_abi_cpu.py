@@ -90,6 +90,12 @@ def test_null_handle_calls(lib):
     assert lib.tvolap_server_stream_bytes(None, 0, None) == -4
     assert lib.tvolap_server_snapshot(None, 0, None, 0) == -4
     assert lib.tvolap_server_restore(None, None, 0, None) == -4
+    # two-level non-uniform partitions
+    assert lib.tvolap_nu_destroy(None) == 0
+    assert lib.tvolap_nu_reset(None) == -4
+    assert lib.tvolap_nu_check(None) == -4
+    assert lib.tvolap_nu_process_block(None, None, None, None, None, None) == -4
+    assert lib.tvolap_nu_create(None, 32, 4, 4, 2, 1, 1, None, 1, None) == -1
 
 
 @pytest.mark.parametrize("args", [

@@ -129,6 +129,56 @@ def test_mixdown_of_paths_equals_one_path_with_summed_taps():
     assert np.max(np.abs(cancel)) <= 1e-12 * np.max(np.abs(y[0]))
 
 
+def test_nonuniform_fixed_response_is_full_convolution():
+    """Two-level non-uniform partitions with one fixed response: head (small
+    hop) plus tail (hop ratio * La, added D samples later) equal numpy's full
+    linear convolution; a response no longer than D leaves the tail silent."""
+    rng = np.random.default_rng(33)
+    La, Ma, ratio, Mb = 4, 3, 4, 2
+    D, Lb = 2 * La * Ma, ratio * La
+    N = 300
+    x = rng.standard_normal(N)
+    h = rng.standard_normal(D + 2 * Lb * Mb - 5)
+    nb = oracle.n_out_blocks(N, La)
+    y = oracle.tvolap_nonuniform(x, h[None], La, Ma, ratio, Mb, _const_sched(nb), out_len=N)
+    assert _rel(y[0], np.convolve(x, h)[:N]) < 1e-12
+    short = h[:D - 3]
+    ys = oracle.tvolap_nonuniform(x, short[None], La, Ma, ratio, Mb, _const_sched(nb), out_len=N)
+    yp = oracle.tvolap_direct(x, short[None], La, _const_sched(nb), out_len=N, M=Ma)
+    np.testing.assert_array_equal(ys, np.atleast_2d(yp))
+
+
+def test_nonuniform_tail_takes_the_head_entry_of_its_hop():
+    """The filter switches from response 0 to 1 at head block ts; an input
+    that starts at sample (ts + 1) La meets response 1 in every block of both
+    levels only if the tail's entry t maps to head entry (t + 1) ratio - 1 or
+    later: the output is then exactly x * h1. A tail reading the entry at the
+    start of its hop instead would still use response 0 and is caught."""
+    rng = np.random.default_rng(34)
+    La, Ma, ratio, Mb = 4, 3, 4, 2
+    D, Lb = 2 * La * Ma, ratio * La
+    N = 400
+    h = rng.standard_normal((2, D + 2 * Lb * Mb))
+    ts = 37
+    x = np.zeros(N)
+    S = (ts + 1) * La
+    x[S:] = rng.standard_normal(N - S)
+    nb = oracle.n_out_blocks(N, La)
+    sched = np.zeros((1, nb), np.int32)
+    sched[0, ts:] = 1
+    y = oracle.tvolap_nonuniform(x, h, La, Ma, ratio, Mb, sched, out_len=N)
+    assert _rel(y[0], np.convolve(x, h[1])[:N]) < 1e-12
+    # planted: the tail reading the head entry t * ratio (start of its hop)
+    tail_len = N - D
+    idx = np.arange(oracle.n_out_blocks(tail_len, Lb)) * ratio
+    yt = oracle.tvolap_direct(x, h[:, D:], Lb, sched[:, np.minimum(idx, nb - 1)],
+                              out_len=tail_len, M=Mb)
+    yh = oracle.tvolap_direct(x, h[:, :D], La, sched, out_len=N, M=Ma)
+    wrong = np.atleast_2d(yh).copy()
+    wrong[:, D:] += np.atleast_2d(yt)
+    assert _rel(wrong[0], np.convolve(x, h[1])[:N]) > 1e-3
+
+
 # --------------------------------------------------------------------- closed form, Fig. 3
 @pytest.mark.parametrize("L,M,d,A", [(8, 4, 3, 10), (8, 4, 21, 12), (16, 2, 40, 9), (4, 3, 17, 15)])
 def test_polarity_switch_closed_form(L, M, d, A):
