@@ -461,6 +461,10 @@ TVOLAP_API int tvolap_nu_process_signal(tvolap_nu_t h, const float *x_dev, int64
 TVOLAP_API int tvolap_nu_process_block(tvolap_nu_t h, const float *in_dev, float *out_dev,
                                        const int32_t *sel_a, const int32_t *sel_b,
                                        const float *sel_alpha);
+/* tvolap_set_option for the head (level 0), the tail (1) or both (-1): the
+   tail's filters change by larger steps per block, so another MAC staging
+   may suit it better. */
+TVOLAP_API int tvolap_nu_set_option(tvolap_nu_t h, int level, int option, int value);
 /* Deferred device errors of both levels (as tvolap_check). */
 TVOLAP_API int tvolap_nu_check(tvolap_nu_t h);
 

@@ -61,6 +61,7 @@ SIGNATURES = {
     "tvolap_nu_process_block": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                         c_void_p]),
     "tvolap_nu_check": (c_int, [c_void_p]),
+    "tvolap_nu_set_option": (c_int, [c_void_p, c_int, c_int, c_int]),
     "tvolap_state_bytes": (c_int64, [c_void_p]),
     "tvolap_get_state": (c_int, [c_void_p, c_void_p, c_int64]),
     "tvolap_set_state": (c_int, [c_void_p, c_void_p, c_int64]),

@@ -297,6 +297,16 @@ int tvolap_nu_process_block(tvolap_nu_t h, const float *in_dev, float *out_dev, 
     return TVOLAP_OK;
 }
 
+int tvolap_nu_set_option(tvolap_nu_t h, int level, int option, int value)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (level < -1 || level > 1) return TVOLAP_ERR_ARG;
+    int st = TVOLAP_OK;
+    if (level != 1) st = tvolap_set_option(h->head, option, value);
+    if (st == TVOLAP_OK && level != 0) st = tvolap_set_option(h->tail, option, value);
+    return st;
+}
+
 int tvolap_nu_check(tvolap_nu_t h)
 {
     if (!h) return TVOLAP_ERR_STATE;

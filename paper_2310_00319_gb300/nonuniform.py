@@ -64,6 +64,10 @@ class NonUniform:
     def check(self):
         self._call("tvolap_nu_check")
 
+    def set_option(self, option: int, value: int, level: int = -1):
+        """tvolap_set_option for the head (0), the tail (1) or both (-1)."""
+        self._call("tvolap_nu_set_option", int(level), int(option), int(value))
+
     def load_bank(self, first_slot: int, irs: torch.Tensor):
         """irs: device float32 [count, ir_len], ir_len <= head_taps + 2 Lb Mb."""
         irs = _need(irs, torch.float32, self.device, "irs", 2)

@@ -94,6 +94,7 @@ def test_null_handle_calls(lib):
     assert lib.tvolap_nu_destroy(None) == 0
     assert lib.tvolap_nu_reset(None) == -4
     assert lib.tvolap_nu_check(None) == -4
+    assert lib.tvolap_nu_set_option(None, -1, 1, 0) == -4
     assert lib.tvolap_nu_process_block(None, None, None, None, None, None) == -4
     assert lib.tvolap_nu_create(None, 32, 4, 4, 2, 1, 1, None, 1, None) == -1
 
