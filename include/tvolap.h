@@ -678,10 +678,12 @@ TVOLAP_API int tvolap_server_admit(tvolap_server_t s, int L, int M, int n_out, i
  * copies the stream into buf (host or device memory, cap bytes).
  * tvolap_server_restore admits a new stream from a snapshot taken on a
  * server with the same hop range: a new slot and piece (TVOLAP_ERR_CAPACITY
- * when none is free), the piece copied on the admission stream, the block
- * counter and the selected filter restored; it becomes live like an admitted
- * stream and continues exactly where the snapshot was taken. Migrating a
- * stream: snapshot, retire, restore.
+ * when none is free), the piece copied on the admission stream (buf stays
+ * valid until the stream is live or the server is waited on, as an
+ * admission's responses), the block counter and the selected filter
+ * restored; it becomes live like an admitted stream and continues exactly
+ * where the snapshot was taken. Migrating a stream: snapshot, retire,
+ * restore.
  */
 TVOLAP_API int tvolap_server_stream_bytes(tvolap_server_t s, int id, int64_t *bytes);
 TVOLAP_API int tvolap_server_snapshot(tvolap_server_t s, int id, void *buf, int64_t cap);
