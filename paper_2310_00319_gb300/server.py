@@ -135,6 +135,7 @@ class Server:
         i = ctypes.c_int()
         self._call("tvolap_server_restore", ctypes.c_void_p(snap.data_ptr()), snap.numel(),
                    ctypes.byref(i))
+        self._keep[i.value] = snap           # read by the admission copy until the stream is live
         return i.value
 
     def state(self, i: int):
