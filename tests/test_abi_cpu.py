@@ -112,6 +112,24 @@ def test_server_create_rejects_bad_arguments_without_gpu(lib, args):
     assert not h.value
 
 
+@pytest.mark.parametrize("args", [
+    (32, 4, 3, 2, 1, 1),         # ratio not a power of two
+    (32, 4, 1, 2, 1, 1),         # ratio below two
+    (16, 64, 128, 2, 1, 1),      # ratio above 64
+    (32, 2, 4, 2, 1, 1),         # head shorter than ratio - 1 partitions
+    (32, 4, 4, 0, 1, 1),         # no tail partitions
+    (512, 4, 4, 2, 1, 1),        # tail hop above 1024
+    (24, 4, 4, 2, 1, 1),         # head hop not a power of two
+    (8, 4, 4, 2, 1, 1),          # head hop below 16
+    (32, 4, 4, 2, 2, 3),         # n_in != n_out without routing
+])
+def test_nu_create_rejects_bad_arguments_without_gpu(lib, args):
+    La, Ma, r, Mb, ni, no = args
+    h = ctypes.c_void_p()
+    assert lib.tvolap_nu_create(ctypes.byref(h), La, Ma, r, Mb, ni, no, None, 1, None) == -1
+    assert not h.value
+
+
 class _BSrc(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("M", ctypes.c_int), ("n_filters", ctypes.c_int),
                 ("N", ctypes.c_int64), ("out_len", ctypes.c_int64)]
