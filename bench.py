@@ -17,11 +17,13 @@ bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -62,52 +64,124 @@ def fp32_peak_tflops(mhz: float) -> float:
     return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
 
 
+def _is_num(v: str) -> bool:
+    try:
+        float(v)
+        return True
+    except ValueError:
+        return False
+
+
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock / throttle sampling during a timed region.
+
+    ``start(prime)`` launches nvidia-smi (a row every PERIOD_MS) and, given
+    ``prime`` (one untimed step, synchronised), keeps the GPU busy with it until
+    the sampler's first row has arrived (at most ``wait_s``), so that sampling
+    is live and the clocks are those under load when the region opens. The
+    region is the ``with`` block. Every row carries nvidia-smi's own timestamp
+    (else the time it was read) and only rows stamped inside the region are
+    summarised; a region shorter than the sampling period reports the row
+    nearest to it, with its distance.
+    """
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    PERIOD_MS = 25
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.reader = None
+        self.lines = []
+        self.first = threading.Event()
+        self.primed = 0
+        self.t_open = self.t_close = None
 
-    def __enter__(self):
+    def start(self, prime=None, wait_s: float = 3.0):
+        if self.proc is not None:
+            return self
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.proc = subprocess.Popen(self.command(), stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return self
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+        deadline = time.time() + wait_s
+        while prime is not None and not self.first.is_set() and time.time() < deadline:
+            prime()
+            self.primed += 1
+        return self
+
+    def command(self):
+        return ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)]
+
+    def _read(self):
+        try:
+            for line in self.proc.stdout:
+                self.lines.append((time.time(), line))
+                self.first.set()
+        except (OSError, ValueError):
+            pass
+
+    def __enter__(self):
+        self.start()
+        self.t_open = time.time()
         return self
 
     def __exit__(self, *exc):
-        self.rows = []
+        self.t_close = time.time()
         if self.proc is None:
             return
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
-        for line in out.splitlines():
-            p = [s.strip() for s in line.split(",")]
-            if len(p) >= 9:
-                self.rows.append(p)
+            self.proc.wait()
+        self.reader.join(timeout=5)
+
+    def _rows(self):
+        rows = []
+        for arrived, line in list(self.lines):
+            p = [v.strip() for v in line.split(",")]
+            if len(p) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = arrived                 # unparsed stamp: the time the row was read
+            rows.append((ts, p))
+        return rows
 
     def summary(self):
-        if not getattr(self, "rows", None):
+        rows = self._rows()
+        if not rows or self.t_open is None or self.t_close is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        mhz = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4)
-                          if r[5 + i].lower().startswith("active")})
-        return {"sm_mhz": statistics.median(mhz) if mhz else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.rows)}
+        inside = [p for ts, p in rows if self.t_open <= ts <= self.t_close]
+        res = {}
+        if inside:
+            res["samples"] = len(inside)
+        else:
+            mid = 0.5 * (self.t_open + self.t_close)
+            ts, p = min(rows, key=lambda r: abs(r[0] - mid))
+            inside = [p]
+            res["samples"] = 0
+            res["nearest_ms"] = round(1e3 * max(self.t_open - ts, ts - self.t_close, 0.0), 1)
+        mhz = [float(p[2]) for p in inside if _is_num(p[2])]
+        mx = [float(p[3]) for p in inside if _is_num(p[3])]
+        reasons = sorted({self.REASONS[i] for p in inside for i in range(4)
+                          if p[6 + i].lower().startswith("active")})
+        res.update({"sm_mhz": statistics.median(mhz) if mhz else None,
+                    "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                    "region_ms": round(1e3 * (self.t_close - self.t_open), 1)})
+        if self.primed:
+            res["prime_steps"] = self.primed
+        return res
 
 
 def workload(args):
@@ -196,10 +270,11 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(dev.index).start(prime=lambda: (step(), torch.cuda.synchronize(dev)))
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    with ClockSampler(dev.index) as clk:
+    with clk:
         t0.record(stream)
         for i in range(args.steps):
             step(evs[i])
@@ -492,7 +567,8 @@ def run_adjoint(args):
     torch.cuda.synchronize(dev)
     evs = []
     t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clk:
+    with ClockSampler(dev.index).start(prime=lambda: (step([]), torch.cuda.synchronize(dev))) \
+            as clk:
         t0e.record(stream)
         for _ in range(args.steps):
             step(evs)
@@ -591,7 +667,8 @@ def run_batched(args):
         B.replay()
     torch.cuda.synchronize(dev)
     t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clk:
+    with ClockSampler(dev.index).start(prime=lambda: (B.replay(), torch.cuda.synchronize(dev))) \
+            as clk:
         t0e.record(B.stream)
         for _ in range(args.steps):
             B.replay()
@@ -1028,7 +1105,8 @@ def run_mixdown(args):
         torch.cuda.synchronize(dev)
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(dev.index) as clk:
+        prime = lambda: (step(mixdown), torch.cuda.synchronize(dev))  # noqa: E731
+        with ClockSampler(dev.index).start(prime=prime) as clk:
             t0.record(stream)
             for i in range(args.steps):
                 step(mixdown, evs[i])
@@ -1155,8 +1233,10 @@ def run_nonuniform(args):
         tail_ms[stg] = timed(lambda: nu.process_signal(x, sa, sb, sal, out_len=wl.out_len), 3)
     tail_staging = min(tail_ms, key=tail_ms.get)
     nu.set_option(1, tail_staging, level=1)
-    with ClockSampler(dev.index) as clk:
-        ms_nu = timed(lambda: nu.process_signal(x, sa, sb, sal, out_len=wl.out_len), args.steps)
+    run_nu = lambda: nu.process_signal(x, sa, sb, sal, out_len=wl.out_len)  # noqa: E731
+    with ClockSampler(dev.index).start(prime=lambda: (run_nu(), torch.cuda.synchronize(dev))) \
+            as clk:
+        ms_nu = timed(run_nu, args.steps)
     clocks = clk.summary()
     ms_uni = timed(lambda: uni.process_signal(x, sa, sb, sal, out_len=wl.out_len), max(3, args.steps // 4))
     nu.check()
