@@ -1409,6 +1409,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.impl != "reference" and args.workload != "plain_at_scale" and _dist()[0] > 1:
+        # the other workloads are single-GPU measurements on cuda:0
+        sys.exit(f"bench.py: --workload {args.workload} runs on one GPU; launch it without torchrun")
     if args.impl == "reference":
         out = run_reference(args)
     elif args.workload == "adjoint":
