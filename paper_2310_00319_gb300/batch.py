@@ -68,6 +68,19 @@ class BatchedTvolap:
         replays read them."""
         x = x.contiguous()
         sched = sched.to(torch.int32).contiguous()
+        if not 0 <= int(i) < len(self.sources):
+            raise IndexError(f"source {i} out of range")
+        src = self.sources[i]
+        N, out_len, L = src.x.shape[0], int(src.out_len), int(src.L)
+        nb = 0 if out_len <= 0 else (out_len - 1) // L + 2
+        for t, nm in ((x, "x"), (sched, "sched")):
+            if t.device.type != "cuda" or (self.device.index is not None
+                                           and t.device.index != self.device.index):
+                raise ValueError(f"{nm} must be on {self.device}")
+        if x.dtype != torch.float32 or x.dim() != 1 or x.numel() != N:
+            raise ValueError(f"x must be float32 [{N}] (source {i}'s length)")
+        if sched.dim() != 1 or sched.numel() < nb:
+            raise ValueError(f"sched must be int32 [>= {nb}] (source {i}'s blocks)")
         self.stream.wait_stream(torch.cuda.current_stream(self.device))
         self._call("tvolap_batch_set_source", int(i), _ptr(x) if x.numel() else None,
                    _ptr(sched) if sched.numel() else None)

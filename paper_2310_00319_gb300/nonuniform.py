@@ -10,7 +10,7 @@ import ctypes
 import torch
 
 from . import _lib
-from .tvolap import _need, _ptr, n_blocks_for
+from .tvolap import _dims, _need, _ptr, n_blocks_for
 
 
 class NonUniform:
@@ -77,7 +77,7 @@ class NonUniform:
     def process_signal(self, x: torch.Tensor, sched_a, sched_b=None, sched_alpha=None,
                        out_len: int | None = None) -> torch.Tensor:
         """Offline: x [n_in, N] -> y [n_out, out_len]; schedules per head block."""
-        x = _need(x, torch.float32, self.device, "x", 2)
+        x = _dims(_need(x, torch.float32, self.device, "x", 2), "x", self.n_in, None)
         N = x.shape[1]
         out_len = N if out_len is None else int(out_len)
         nb = n_blocks_for(out_len, self.La)
@@ -103,6 +103,11 @@ class NonUniform:
             raise ValueError(f"x must be [{self.n_in}, {self.La}]")
         if out is None:
             out = torch.empty((self.n_out, self.La), dtype=torch.float32, device=self.device)
+        _dims(_need(out, torch.float32, self.device, "out", 2), "out", self.n_out, self.La)
+        for t, nm, dt in ((sel_a, "sel_a", torch.int32), (sel_b, "sel_b", torch.int32),
+                          (sel_alpha, "sel_alpha", torch.float32)):
+            if t is not None:
+                _dims(_need(t, dt, self.device, nm, 1), nm, self.n_out)
         self._call("tvolap_nu_process_block", _ptr(x), _ptr(out), _ptr(sel_a), _ptr(sel_b),
                    _ptr(sel_alpha))
         return out

@@ -132,6 +132,10 @@ class Server:
     def restore(self, snap) -> int:
         """Admit a stream from a snapshot (this or another server with the
         same hops); it continues where the snapshot was taken. Returns its id."""
+        import torch
+        if not isinstance(snap, torch.Tensor) or snap.dtype != torch.uint8 or \
+                not snap.is_contiguous():
+            raise ValueError("snap must be a contiguous uint8 tensor (from snapshot())")
         i = ctypes.c_int()
         self._call("tvolap_server_restore", ctypes.c_void_p(snap.data_ptr()), snap.numel(),
                    ctypes.byref(i))

@@ -33,6 +33,15 @@ def _need(t, dtype, device, name, ndim=None):
     return t
 
 
+def _dims(t, name, *dims):
+    """t.shape must be dims (None: any extent); the kernels index every listed
+    extent, so a smaller tensor would be read or written out of bounds."""
+    if t.dim() != len(dims) or any(d is not None and n != d for n, d in zip(t.shape, dims)):
+        want = ", ".join("*" if d is None else str(d) for d in dims)
+        raise ValueError(f"{name} must be [{want}], got {list(t.shape)}")
+    return t
+
+
 def n_blocks_for(out_len: int, L: int) -> int:
     """Schedule entries for output samples [0, out_len): t = l + 1, l = -1 ..
     floor((out_len - 1) / L)."""
@@ -143,7 +152,7 @@ class Plan:
             raise ValueError(f"x must be [{self.n_in}, {self.L}]")
         if out is None:
             out = torch.empty((self.n_out, self.L), dtype=torch.float32, device=self.device)
-        _need(out, torch.float32, self.device, "out", 2)
+        _dims(_need(out, torch.float32, self.device, "out", 2), "out", self.n_out, self.L)
         for t, nm, dt in ((sel_a, "sel_a", torch.int32), (sel_b, "sel_b", torch.int32),
                           (sel_alpha, "sel_alpha", torch.float32)):
             if t is not None:
@@ -195,10 +204,11 @@ class Plan:
 
     def mix(self, Y: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         """Mixdown stage: Y complex64 [n_out, n_blocks, 2L] -> [n_mix, n_blocks, 2L]."""
-        Y = _need(Y, torch.complex64, self.device, "Y", 3)
+        Y = _dims(_need(Y, torch.complex64, self.device, "Y", 3), "Y", self.n_out, None, self.P)
         nb = Y.shape[1]
         if out is None:
             out = torch.empty((self.n_mix, nb, self.P), dtype=torch.complex64, device=self.device)
+        _dims(_need(out, torch.complex64, self.device, "out", 3), "out", self.n_mix, nb, self.P)
         self._call("tvolap_mix", _ptr(Y), nb, _ptr(out))
         return out
 
@@ -229,7 +239,7 @@ class Plan:
             raise ValueError(f"x must be [{self.n_in}, {self.L}]")
         if out is None:
             out = torch.empty((self.n_mix, self.L), dtype=torch.float32, device=self.device)
-        _need(out, torch.float32, self.device, "out", 2)
+        _dims(_need(out, torch.float32, self.device, "out", 2), "out", self.n_mix, self.L)
         for t, nm, dt in ((sel_a, "sel_a", torch.int32), (sel_b, "sel_b", torch.int32),
                           (sel_alpha, "sel_alpha", torch.float32)):
             if t is not None:
@@ -280,15 +290,15 @@ class Plan:
         x [C, x_stride] (channel c holds n[c] samples), n/out_len int64 [C],
         parts int32 [C]; returns y [C, max_out_len] (channel c valid up to
         out_len[c])."""
-        x = _need(x, torch.float32, self.device, "x", 2)
-        _need(n, torch.int64, self.device, "n", 1)
-        _need(out_len, torch.int64, self.device, "out_len", 1)
-        _need(parts, torch.int32, self.device, "parts", 1)
+        x = _dims(_need(x, torch.float32, self.device, "x", 2), "x", self.n_in, None)
+        _dims(_need(n, torch.int64, self.device, "n", 1), "n", self.n_in)
+        _dims(_need(out_len, torch.int64, self.device, "out_len", 1), "out_len", self.n_out)
+        _dims(_need(parts, torch.int32, self.device, "parts", 1), "parts", self.n_out)
         nb = n_blocks_for(max_out_len, self.L)
         sa, sb, sal, stride = self._sched(sched_a, sched_b, sched_alpha, nb)
         if out is None:
             out = torch.empty((self.n_out, max_out_len), dtype=torch.float32, device=self.device)
-        _need(out, torch.float32, self.device, "out", 2)
+        _dims(_need(out, torch.float32, self.device, "out", 2), "out", self.n_out, None)
         self._call("tvolap_process_ragged", _ptr(x), x.shape[1], _ptr(n), _ptr(out_len),
                    _ptr(parts), int(max_out_len), _ptr(sa), _ptr(sb), _ptr(sal), stride,
                    _ptr(out), out.shape[1])
@@ -299,14 +309,14 @@ class Plan:
 
     def forward_spectra(self, x: torch.Tensor, n_blocks: int) -> torch.Tensor:
         """X [n_in, n_blocks, P] of input blocks l = -1 .. n_blocks - 2."""
-        x = _need(x, torch.float32, self.device, "x", 2)
+        x = _dims(_need(x, torch.float32, self.device, "x", 2), "x", self.n_in, None)
         X = torch.empty((self.n_in, n_blocks, self.P), dtype=torch.complex64, device=self.device)
         self._call("tvolap_forward_spectra", _ptr(x), x.shape[1], x.shape[1], int(n_blocks),
                    _ptr(X))
         return X
 
     def mac(self, X: torch.Tensor, sched_a, sched_b=None, sched_alpha=None) -> torch.Tensor:
-        X = _need(X, torch.complex64, self.device, "X", 3)
+        X = _dims(_need(X, torch.complex64, self.device, "X", 3), "X", self.n_in, None, self.P)
         nb = X.shape[1]
         sa, sb, sal, stride = self._sched(sched_a, sched_b, sched_alpha, nb)
         Y = torch.empty((self.n_out, nb, self.P), dtype=torch.complex64, device=self.device)
@@ -314,7 +324,7 @@ class Plan:
         return Y
 
     def inverse_ola(self, Y: torch.Tensor, out_len: int) -> torch.Tensor:
-        Y = _need(Y, torch.complex64, self.device, "Y", 3)
+        Y = _dims(_need(Y, torch.complex64, self.device, "Y", 3), "Y", self.n_out, None, self.P)
         y = torch.empty((self.n_out, out_len), dtype=torch.float32, device=self.device)
         self._call("tvolap_inverse_ola", _ptr(Y), Y.shape[1], _ptr(y), int(out_len), int(out_len))
         return y
@@ -322,7 +332,7 @@ class Plan:
     # ------------------------------------------------------------------ differentiable model
     def block_spectra(self, x: torch.Tensor, t_first: int, t_count: int) -> torch.Tensor:
         """X [n_in, t_count, P]: spectra of blocks t_first .. t_first + t_count - 1."""
-        x = _need(x, torch.float32, self.device, "x", 2)
+        x = _dims(_need(x, torch.float32, self.device, "x", 2), "x", self.n_in, None)
         X = torch.empty((self.n_in, t_count, self.P), dtype=torch.complex64, device=self.device)
         self._call("tvolap_block_spectra", _ptr(x), x.shape[1], x.shape[1], int(t_first),
                    int(t_count), _ptr(X))
@@ -333,12 +343,13 @@ class Plan:
         """Eq. 7 with per-block parameter spectra Pspec [n_out, p_blocks, M, P] for
         blocks t_first .. t_first + t_count - 1, written to rows out_row .. of
         out [n_out, rows, P] (default: a new [n_out, t_count, P])."""
-        X = _need(X, torch.complex64, self.device, "X", 3)
-        Pspec = _need(Pspec, torch.complex64, self.device, "Pspec", 4)
+        X = _dims(_need(X, torch.complex64, self.device, "X", 3), "X", self.n_in, None, self.P)
+        Pspec = _dims(_need(Pspec, torch.complex64, self.device, "Pspec", 4), "Pspec", self.n_out,
+                      None, self.M, self.P)
         if out is None:
             out = torch.empty((self.n_out, t_count, self.P), dtype=torch.complex64,
                               device=self.device)
-        _need(out, torch.complex64, self.device, "out", 3)
+        _dims(_need(out, torch.complex64, self.device, "out", 3), "out", self.n_out, None, self.P)
         if out_row < 0 or out_row + t_count > out.shape[1]:
             raise ValueError("out rows out of range")
         ptr = ctypes.c_void_p(out.data_ptr() + out_row * self.P * 8)
@@ -348,20 +359,30 @@ class Plan:
 
     def adjoint_output(self, g: torch.Tensor, t_first: int, t_count: int) -> torch.Tensor:
         """G [n_out, t_count, P] = dL/dY of blocks t_first .. from g = dL/dy."""
-        g = _need(g, torch.float32, self.device, "g", 2)
+        g = _dims(_need(g, torch.float32, self.device, "g", 2), "g", self.n_out, None)
         G = torch.empty((self.n_out, t_count, self.P), dtype=torch.complex64, device=self.device)
         self._call("tvolap_adjoint_output", _ptr(g), g.shape[1], g.shape[1], int(t_first),
                    int(t_count), _ptr(G))
         return G
+
+    def _adjoint_operands(self, G, Pspec, dP):
+        G = _dims(_need(G, torch.complex64, self.device, "G", 3), "G", self.n_out, None, self.P)
+        Pspec = _dims(_need(Pspec, torch.complex64, self.device, "Pspec", 4), "Pspec", self.n_out,
+                      None, self.M, self.P)
+        dP = _dims(_need(dP, torch.complex64, self.device, "dP", 4), "dP", *Pspec.shape)
+        return G, Pspec, dP
 
     def adjoint_mac(self, G, g_first, X, x_first, Pspec, q_first, q_count, dP, dX=None,
                     dx_row=0):
         """dP (written in place for t - 2m in the q range) and the input-block
         gradients, written to rows dx_row .. of dX [n_out, rows, P] (default: a
         new [n_out, q_count, P])."""
+        G, Pspec, dP = self._adjoint_operands(G, Pspec, dP)
+        X = _dims(_need(X, torch.complex64, self.device, "X", 3), "X", self.n_in, None, self.P)
         if dX is None:
             dX = torch.empty((self.n_out, q_count, self.P), dtype=torch.complex64,
                              device=self.device)
+        _dims(_need(dX, torch.complex64, self.device, "dX", 3), "dX", self.n_out, None, self.P)
         if dx_row < 0 or dx_row + q_count > dX.shape[1]:
             raise ValueError("dX rows out of range")
         ptr = ctypes.c_void_p(dX.data_ptr() + dx_row * self.P * 8)
@@ -373,12 +394,14 @@ class Plan:
     def adjoint_mac_x(self, G, g_first, x, Pspec, q_first, q_count, dP, dX=None, dx_row=0):
         """adjoint_mac with the input spectra recomputed inside the kernel from
         x [n_in, N] (nothing stored between forward and backward)."""
+        G, Pspec, dP = self._adjoint_operands(G, Pspec, dP)
+        x = _dims(_need(x.contiguous(), torch.float32, self.device, "x", 2), "x", self.n_in, None)
         if dX is None:
             dX = torch.empty((self.n_out, q_count, self.P), dtype=torch.complex64,
                              device=self.device)
+        _dims(_need(dX, torch.complex64, self.device, "dX", 3), "dX", self.n_out, None, self.P)
         if dx_row < 0 or dx_row + q_count > dX.shape[1]:
             raise ValueError("dX rows out of range")
-        x = x.contiguous()
         ptr = ctypes.c_void_p(dX.data_ptr() + dx_row * self.P * 8)
         self._call("tvolap_adjoint_mac_x", _ptr(G), int(g_first), G.shape[1], _ptr(x), x.shape[1],
                    x.shape[1], _ptr(Pspec), Pspec.shape[1], int(q_first), int(q_count), _ptr(dP),
@@ -387,6 +410,8 @@ class Plan:
 
     def adjoint_input(self, dX: torch.Tensor, q_first: int, dx: torch.Tensor):
         """dx [n_in, N] += the input gradient of blocks q_first .. + dX.shape[1] - 1."""
+        _dims(_need(dX, torch.complex64, self.device, "dX", 3), "dX", self.n_out, None, self.P)
+        _dims(_need(dx, torch.float32, self.device, "dx", 2), "dx", self.n_in, None)
         self._call("tvolap_adjoint_input", _ptr(dX), int(q_first), dX.shape[1], _ptr(dx),
                    dx.shape[1], dx.shape[1])
         return dx
