@@ -72,6 +72,35 @@ def _is_num(v: str) -> bool:
         return False
 
 
+def smi_index_of(uuid: str, listing: str, fallback: str) -> str:
+    """nvidia-smi's index of the GPU whose UUID is ``uuid``, from the lines
+    ``index, uuid`` of ``listing``; ``fallback`` when none matches."""
+    want = uuid.strip().lower()
+    want = want[4:] if want.startswith("gpu-") else want
+    for line in listing.splitlines():
+        p = [v.strip() for v in line.split(",")]
+        if len(p) == 2:
+            u = p[1].lower()
+            if (u[4:] if u.startswith("gpu-") else u) == want and want:
+                return p[0]
+    return fallback
+
+
+def smi_index(dev) -> str:
+    """nvidia-smi's id of torch device ``dev``. CUDA's device order and
+    CUDA_VISIBLE_DEVICES need not follow nvidia-smi's numbering, so the device
+    is found by its UUID; the CUDA index is the fallback."""
+    fallback = str(dev.index if dev.index is not None else 0)
+    try:
+        import torch
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        listing = subprocess.run(["nvidia-smi", "--query-gpu=index,uuid", "--format=csv,noheader"],
+                                 capture_output=True, text=True, timeout=20).stdout
+    except Exception:
+        return fallback
+    return smi_index_of(uuid, listing, fallback)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during a timed region.
 
@@ -90,8 +119,8 @@ class ClockSampler:
     REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
     PERIOD_MS = 25
 
-    def __init__(self, index: int):
-        self.index = index
+    def __init__(self, index):
+        self.index = index               # nvidia-smi's id of the GPU (see smi_index)
         self.proc = None
         self.reader = None
         self.lines = []
@@ -178,7 +207,8 @@ class ClockSampler:
                           if p[6 + i].lower().startswith("active")})
         res.update({"sm_mhz": statistics.median(mhz) if mhz else None,
                     "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                    "region_ms": round(1e3 * (self.t_close - self.t_open), 1)})
+                    "region_ms": round(1e3 * (self.t_close - self.t_open), 1),
+                    "smi_id": str(self.index)})
         if self.primed:
             res["prime_steps"] = self.primed
         return res
@@ -270,7 +300,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clk = ClockSampler(dev.index).start(prime=lambda: (step(), torch.cuda.synchronize(dev)))
+    clk = ClockSampler(smi_index(dev)).start(prime=lambda: (step(), torch.cuda.synchronize(dev)))
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -567,7 +597,7 @@ def run_adjoint(args):
     torch.cuda.synchronize(dev)
     evs = []
     t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(dev.index).start(prime=lambda: (step([]), torch.cuda.synchronize(dev))) \
+    with ClockSampler(smi_index(dev)).start(prime=lambda: (step([]), torch.cuda.synchronize(dev))) \
             as clk:
         t0e.record(stream)
         for _ in range(args.steps):
@@ -667,7 +697,7 @@ def run_batched(args):
         B.replay()
     torch.cuda.synchronize(dev)
     t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(dev.index).start(prime=lambda: (B.replay(), torch.cuda.synchronize(dev))) \
+    with ClockSampler(smi_index(dev)).start(prime=lambda: (B.replay(), torch.cuda.synchronize(dev))) \
             as clk:
         t0e.record(B.stream)
         for _ in range(args.steps):
@@ -895,7 +925,7 @@ def run_serve(args):
     e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
          for _ in range(lat_ticks)]
     s0 = srv.stats()
-    with ClockSampler(0) as clk:
+    with ClockSampler(smi_index(dev)) as clk:
         for k in range(lat_ticks):
             arrivals(tick)
             ids = srv.due()
@@ -1106,7 +1136,7 @@ def run_mixdown(args):
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         prime = lambda: (step(mixdown), torch.cuda.synchronize(dev))  # noqa: E731
-        with ClockSampler(dev.index).start(prime=prime) as clk:
+        with ClockSampler(smi_index(dev)).start(prime=prime) as clk:
             t0.record(stream)
             for i in range(args.steps):
                 step(mixdown, evs[i])
@@ -1234,7 +1264,7 @@ def run_nonuniform(args):
     tail_staging = min(tail_ms, key=tail_ms.get)
     nu.set_option(1, tail_staging, level=1)
     run_nu = lambda: nu.process_signal(x, sa, sb, sal, out_len=wl.out_len)  # noqa: E731
-    with ClockSampler(dev.index).start(prime=lambda: (run_nu(), torch.cuda.synchronize(dev))) \
+    with ClockSampler(smi_index(dev)).start(prime=lambda: (run_nu(), torch.cuda.synchronize(dev))) \
             as clk:
         ms_nu = timed(run_nu, args.steps)
     clocks = clk.summary()

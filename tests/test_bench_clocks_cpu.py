@@ -97,3 +97,21 @@ def test_unparsed_stamps_fall_back_to_arrival_time():
     clk.lines = [(t, "garbled" + line[line.index(","):]) for t, line in clk.lines]
     res = clk.summary()
     assert res["samples"] >= 3
+
+
+def test_gpu_found_by_uuid_not_by_cuda_index():
+    listing = ("0, GPU-11111111-aaaa-bbbb-cccc-000000000000\n"
+               "1, GPU-22222222-aaaa-bbbb-cccc-000000000000\n")
+    # the process sees one GPU (CUDA index 0) that nvidia-smi numbers 1
+    assert bench.smi_index_of("22222222-AAAA-bbbb-cccc-000000000000", listing, "0") == "1"
+    assert bench.smi_index_of("GPU-11111111-aaaa-bbbb-cccc-000000000000", listing, "5") == "0"
+    assert bench.smi_index_of("33333333-aaaa-bbbb-cccc-000000000000", listing, "0") == "0"
+    assert bench.smi_index_of("", listing, "2") == "2"
+    assert bench.smi_index_of("x", "garbled", "3") == "3"
+
+
+def test_smi_index_falls_back_without_a_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("needs a machine without a GPU")
+    assert bench.smi_index(torch.device("cuda", 3)) == "3"
