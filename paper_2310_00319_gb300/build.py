@@ -25,6 +25,11 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibilit
               "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
 
 
+# TVOLAP_NO_NVTX=1 in the environment builds the library without its NVTX ranges
+if os.environ.get("TVOLAP_NO_NVTX") == "1":
+    NVCC_FLAGS = NVCC_FLAGS + ["-DTVOLAP_NO_NVTX"]
+
+
 def nvcc() -> str:
     cand = os.environ.get("NVCC") or shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(cand):

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "trace.h"
 
 using namespace tvolap;
 
@@ -299,6 +300,7 @@ int tvolap_reset(tvolap_t h)
 int tvolap_load_bank(tvolap_t h, int first_slot, int count, const float *ir_dev, int ir_len,
                      int64_t ir_stride)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (first_slot < 0 || count < 0 || (int64_t)first_slot + count > h->n_user_slots)
         return TVOLAP_ERR_ARG;
@@ -310,6 +312,7 @@ int tvolap_load_bank(tvolap_t h, int first_slot, int count, const float *ir_dev,
 
 int tvolap_set_filter(tvolap_t h, int out_ch, const float *ir_dev, int ir_len)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (out_ch < 0 || out_ch >= h->n_out || !ir_dev || ir_len < 1 ||
         (int64_t)ir_len > 2LL * h->L * h->M)
@@ -332,6 +335,7 @@ int tvolap_select(tvolap_t h, int out_ch, int slot_a, int slot_b, float alpha)
 int tvolap_process_block(tvolap_t h, const float *in_dev, float *out_dev, const int32_t *sel_a,
                          const int32_t *sel_b, const float *sel_alpha)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (!in_dev || !out_dev) return TVOLAP_ERR_ARG;
     if (!sel_a && (sel_b || sel_alpha)) return TVOLAP_ERR_ARG;
@@ -355,6 +359,7 @@ int tvolap_process_signal(tvolap_t h, const float *x_dev, int64_t N, int64_t x_s
                           const float *sched_alpha, int64_t sched_stride, float *y_dev,
                           int64_t out_len, int64_t y_stride)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (N < 0 || out_len < 0 || x_stride < N || y_stride < out_len) return TVOLAP_ERR_ARG;
     if (out_len == 0) return TVOLAP_OK;
@@ -377,6 +382,7 @@ int tvolap_process_ragged(tvolap_t h, const float *x_dev, int64_t x_stride, cons
                           const int32_t *sched_a, const int32_t *sched_b, const float *sched_alpha,
                           int64_t sched_stride, float *y_dev, int64_t y_stride)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (!h->identity_routing) return TVOLAP_ERR_ARG;
     if (max_out_len < 0 || x_stride < 0 || y_stride < max_out_len) return TVOLAP_ERR_ARG;
@@ -399,6 +405,7 @@ int tvolap_process_ragged(tvolap_t h, const float *x_dev, int64_t x_stride, cons
 int tvolap_forward_spectra(tvolap_t h, const float *x_dev, int64_t N, int64_t x_stride,
                            int n_blocks, float *X_dev)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (N < 0 || x_stride < N || n_blocks < 0 || (N > 0 && !x_dev) || (n_blocks > 0 && !X_dev))
         return TVOLAP_ERR_ARG;
@@ -410,6 +417,7 @@ int tvolap_mac(tvolap_t h, const float *X_dev, int n_blocks, const int32_t *sche
                const int32_t *sched_b, const float *sched_alpha, int64_t sched_stride,
                float *Y_dev)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (n_blocks < 0 || sched_stride < n_blocks) return TVOLAP_ERR_ARG;
     if (n_blocks == 0) return TVOLAP_OK;
@@ -422,6 +430,7 @@ int tvolap_mac(tvolap_t h, const float *X_dev, int n_blocks, const int32_t *sche
 int tvolap_inverse_ola(tvolap_t h, const float *Y_dev, int n_blocks, float *y_dev,
                        int64_t out_len, int64_t y_stride)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (out_len < 0 || y_stride < out_len || n_blocks != blocks_for(h, out_len))
         return TVOLAP_ERR_ARG;
@@ -461,6 +470,7 @@ static bool a16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) =
 int tvolap_block_spectra(tvolap_t h, const float *x_dev, int64_t N, int64_t x_stride,
                          int64_t t_first, int t_count, float *X_dev)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (N < 0 || x_stride < N || t_first < 0 || t_count < 0 || (N > 0 && !x_dev) ||
         (t_count > 0 && !X_dev))
@@ -473,6 +483,7 @@ int tvolap_mac_params(tvolap_t h, const float *X_dev, int64_t x_first, int x_cou
                       const float *P_dev, int64_t p_blocks, int64_t t_first, int t_count,
                       float *Y_dev, int64_t y_rows)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (t_count < 0 || t_first < 0 || x_first < 0 || x_count < 0) return TVOLAP_ERR_ARG;
     if (t_count == 0) return TVOLAP_OK;
@@ -489,6 +500,7 @@ int tvolap_mac_params(tvolap_t h, const float *X_dev, int64_t x_first, int x_cou
 int tvolap_adjoint_output(tvolap_t h, const float *g_dev, int64_t g_len, int64_t g_stride,
                           int64_t t_first, int t_count, float *G_dev)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (g_len < 0 || g_stride < g_len || t_first < 0 || t_count < 0 || (g_len > 0 && !g_dev) ||
         (t_count > 0 && !G_dev))
@@ -502,6 +514,7 @@ int tvolap_adjoint_mac(tvolap_t h, const float *G_dev, int64_t g_first, int g_co
                        int64_t p_blocks, int64_t q_first, int q_count, float *dP_dev, float *dX_dev,
                        int64_t dx_rows)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (!h->identity_routing) return TVOLAP_ERR_ARG;
     if (q_count < 0 || q_first < 0 || g_first < 0 || x_first < 0 || g_count < 0 || x_count < 0)
@@ -527,6 +540,7 @@ int tvolap_adjoint_mac_x(tvolap_t h, const float *G_dev, int64_t g_first, int g_
                          int64_t p_blocks, int64_t q_first, int q_count, float *dP_dev,
                          float *dX_dev, int64_t dx_rows)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (!h->identity_routing) return TVOLAP_ERR_ARG;
     if (q_count < 0 || q_first < 0 || g_first < 0 || g_count < 0 || N < 0 || x_stride < N)
@@ -549,6 +563,7 @@ int tvolap_adjoint_mac_x(tvolap_t h, const float *G_dev, int64_t g_first, int g_
 int tvolap_adjoint_input(tvolap_t h, const float *dX_dev, int64_t q_first, int q_count,
                          float *dx_dev, int64_t N, int64_t x_stride)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (!h->identity_routing) return TVOLAP_ERR_ARG;
     if (q_first < 0 || q_count < 0 || N < 0 || x_stride < N) return TVOLAP_ERR_ARG;
@@ -598,6 +613,7 @@ int tvolap_set_mix(tvolap_t h, int n_mix, const int32_t *mix_of_out)
 
 int tvolap_mix(tvolap_t h, const void *Y_dev, int n_blocks, void *Ymix_dev)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (h->n_mix == 0 || n_blocks < 0) return TVOLAP_ERR_ARG;
     if (n_blocks == 0) return TVOLAP_OK;
@@ -613,6 +629,7 @@ int tvolap_process_signal_mix(tvolap_t h, const float *x_dev, int64_t N, int64_t
                               const float *sched_alpha, int64_t sched_stride, float *y_dev,
                               int64_t out_len, int64_t y_stride)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (h->n_mix == 0) return TVOLAP_ERR_ARG;
     if (N < 0 || out_len < 0 || x_stride < N || y_stride < out_len) return TVOLAP_ERR_ARG;
@@ -637,6 +654,7 @@ int tvolap_process_signal_mix(tvolap_t h, const float *x_dev, int64_t N, int64_t
 int tvolap_process_block_mix(tvolap_t h, const float *in_dev, float *out_dev, const int32_t *sel_a,
                              const int32_t *sel_b, const float *sel_alpha)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (h->n_mix == 0 || !in_dev || !out_dev) return TVOLAP_ERR_ARG;
     if (!sel_a && (sel_b || sel_alpha)) return TVOLAP_ERR_ARG;
@@ -657,6 +675,7 @@ int64_t tvolap_state_bytes(tvolap_t h)
 
 int tvolap_get_state(tvolap_t h, void *buf, int64_t cap)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (!buf || cap < state_bytes(h)) return TVOLAP_ERR_ARG;
     const StateHeader hd{STATE_MAGIC, STATE_VERSION, h->L, h->M, h->n_in, h->n_out, h->n_mix, 0,
@@ -677,6 +696,7 @@ int tvolap_get_state(tvolap_t h, void *buf, int64_t cap)
 
 int tvolap_set_state(tvolap_t h, const void *buf, int64_t bytes)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (!buf || bytes < state_bytes(h)) return TVOLAP_ERR_ARG;
     StateHeader hd;

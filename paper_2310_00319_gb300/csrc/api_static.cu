@@ -11,6 +11,7 @@
 #include <mutex>
 
 #include "internal.h"
+#include "trace.h"
 
 using namespace tvolap;
 
@@ -56,6 +57,7 @@ extern "C" int tvolap_process_signal_static(tvolap_t h, const float *x_dev, int6
                                             int64_t sched_stride, float *y_dev, int64_t out_len,
                                             int64_t y_stride)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (N < 0 || out_len < 0 || x_stride < N || y_stride < out_len) return TVOLAP_ERR_ARG;
     if (out_len == 0) return TVOLAP_OK;

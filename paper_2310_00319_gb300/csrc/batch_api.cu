@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/tvolap.h"
+#include "trace.h"
 
 namespace {
 
@@ -253,6 +254,7 @@ int tvolap_batch_load_filters(tvolap_batch_t b, int i, const float *ir_dev, int 
 
 int tvolap_batch_run(tvolap_batch_t b)
 {
+    TVOLAP_TRACE();
     if (!b) return TVOLAP_ERR_STATE;
     if (b->graph) return cuda_status(cudaGraphLaunch(b->graph, b->stream));
     return run_direct(b);
@@ -260,6 +262,7 @@ int tvolap_batch_run(tvolap_batch_t b)
 
 int tvolap_batch_capture(tvolap_batch_t b)
 {
+    TVOLAP_TRACE();
     if (!b) return TVOLAP_ERR_STATE;
     int e = run_direct(b);                 // sizes every workspace before the capture
     if (e != TVOLAP_OK) return e;
@@ -284,6 +287,7 @@ int tvolap_batch_capture(tvolap_batch_t b)
 
 int tvolap_batch_autotune(tvolap_batch_t b, int reps, int *chosen)
 {
+    TVOLAP_TRACE();
     if (!b) return TVOLAP_ERR_STATE;
     if (reps < 1) return TVOLAP_ERR_ARG;
     if (b->graph) {

@@ -11,6 +11,7 @@
 #include <new>
 
 #include "internal.h"
+#include "trace.h"
 
 struct tvolap_nu {
     tvolap_t head = nullptr, tail = nullptr;
@@ -194,6 +195,7 @@ int tvolap_nu_dims(tvolap_nu_t h, int *La, int *Lb, int64_t *head_taps, int64_t 
 int tvolap_nu_load_bank(tvolap_nu_t h, int first_slot, int count, const float *ir_dev, int ir_len,
                         int64_t ir_stride)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (count < 0 || ir_len < 1 || ir_stride < ir_len || (count > 0 && !ir_dev) ||
         (int64_t)ir_len > h->D + 2LL * h->Lb * h->Mb)
@@ -222,6 +224,7 @@ int tvolap_nu_process_signal(tvolap_nu_t h, const float *x_dev, int64_t N, int64
                              const int32_t *sched_a, const int32_t *sched_b, const float *sched_alpha,
                              int64_t sched_stride, float *y_dev, int64_t out_len, int64_t y_stride)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     int st = tvolap_process_signal(h->head, x_dev, N, x_stride, sched_a, sched_b, sched_alpha,
                                    sched_stride, y_dev, out_len, y_stride);
@@ -270,6 +273,7 @@ int tvolap_nu_process_signal(tvolap_nu_t h, const float *x_dev, int64_t N, int64
 int tvolap_nu_process_block(tvolap_nu_t h, const float *in_dev, float *out_dev, const int32_t *sel_a,
                             const int32_t *sel_b, const float *sel_alpha)
 {
+    TVOLAP_TRACE();
     if (!h) return TVOLAP_ERR_STATE;
     if (!in_dev || !out_dev) return TVOLAP_ERR_ARG;
     int st = tvolap_process_block(h->head, in_dev, out_dev, sel_a, sel_b, sel_alpha);

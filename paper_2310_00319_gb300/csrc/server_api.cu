@@ -11,6 +11,7 @@
 #include "internal.h"
 #include "server_dev.h"
 #include "server_sched.h"
+#include "trace.h"
 
 using namespace tvolap;
 
@@ -452,6 +453,7 @@ extern "C" {
 int tvolap_server_admit(tvolap_server_t s, int L, int M, int n_out, int n_filters,
                         const float *ir_dev, int ir_len, int64_t ir_stride, int *id)
 {
+    TVOLAP_TRACE();
     if (!s) return TVOLAP_ERR_STATE;
     if (!id || ir_len < 0 || (int64_t)ir_len > 2 * (int64_t)L * M || (ir_len > 0 && !ir_dev) ||
         ir_stride < ir_len)
@@ -497,6 +499,7 @@ int tvolap_server_stream_bytes(tvolap_server_t s, int id, int64_t *bytes)
 
 int tvolap_server_snapshot(tvolap_server_t s, int id, void *buf, int64_t cap)
 {
+    TVOLAP_TRACE();
     if (!s) return TVOLAP_ERR_STATE;
     if (!buf || !s->sch.valid_id(id)) return TVOLAP_ERR_ARG;
     const SchedStream &ss = s->sch.st[id];
@@ -515,6 +518,7 @@ int tvolap_server_snapshot(tvolap_server_t s, int id, void *buf, int64_t cap)
 
 int tvolap_server_restore(tvolap_server_t s, const void *buf, int64_t bytes, int *id)
 {
+    TVOLAP_TRACE();
     if (!s) return TVOLAP_ERR_STATE;
     if (!buf || !id || bytes < SNAP_DATA) return TVOLAP_ERR_ARG;
     StreamSnapHeader hd;
@@ -596,6 +600,7 @@ int tvolap_server_due(tvolap_server_t s, int32_t *ids_host, int cap, int *count,
 
 int tvolap_server_tick(tvolap_server_t s)
 {
+    TVOLAP_TRACE();
     if (!s) return TVOLAP_ERR_STATE;
     if (s->wait_us > 0) {                      // one tick in flight
         const int e = finish(s);
@@ -690,6 +695,7 @@ int tvolap_server_tick(tvolap_server_t s)
 
 int tvolap_server_wait(tvolap_server_t s)
 {
+    TVOLAP_TRACE();
     if (!s) return TVOLAP_ERR_STATE;
     return finish(s);
 }
