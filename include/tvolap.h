@@ -759,7 +759,11 @@ typedef enum tvolap_server_option {
     TVOLAP_SERVER_OPT_WAIT_US = 2,
     /* 1: direct launches with CUDA events around the three stages; their
        times accumulate into tvolap_server_stats. 0 (default): off. */
-    TVOLAP_SERVER_OPT_TIMING = 3
+    TVOLAP_SERVER_OPT_TIMING = 3,
+    /* Fault injection on the host: the next `value` admissions (admit and
+       restore) with valid arguments return TVOLAP_ERR_CAPACITY as if no arena
+       piece were free, and change nothing. 0 (default): none. */
+    TVOLAP_SERVER_OPT_FAIL_ADMITS = 4
 } tvolap_server_option;
 
 TVOLAP_API int tvolap_server_set_option(tvolap_server_t s, int option, int64_t value);
@@ -795,6 +799,9 @@ TVOLAP_API int tvolap_sched_footprint(int L, int M, int n_out, int n_filters, in
 /* Admit: receives the id, the arena offset and the phase. */
 TVOLAP_API int tvolap_sched_admit(tvolap_sched_t s, int L, int M, int n_out, int n_filters,
                                   int *id, int64_t *offset, int *phase);
+/* Fault injection (as TVOLAP_SERVER_OPT_FAIL_ADMITS): the next n admissions
+   with valid arguments return TVOLAP_ERR_CAPACITY and change nothing. */
+TVOLAP_API int tvolap_sched_fail_admits(tvolap_sched_t s, int64_t n);
 TVOLAP_API int tvolap_sched_activate(tvolap_sched_t s, int id);
 TVOLAP_API int tvolap_sched_retire(tvolap_sched_t s, int id);
 /* Due ids at the next tick (live streams only), as tvolap_server_due. */

@@ -129,6 +129,7 @@ SIGNATURES = {
     "tvolap_sched_destroy": (c_int, [c_void_p]),
     "tvolap_sched_footprint": (c_int, [c_int, c_int, c_int, c_int, P_int64]),
     "tvolap_sched_admit": (c_int, [c_void_p, c_int, c_int, c_int, c_int, P_int, P_int64, P_int]),
+    "tvolap_sched_fail_admits": (c_int, [c_void_p, c_int64]),
     "tvolap_sched_activate": (c_int, [c_void_p, c_int]),
     "tvolap_sched_retire": (c_int, [c_void_p, c_int]),
     "tvolap_sched_due": (c_int, [c_void_p, P_int32, c_int, P_int]),

@@ -730,6 +730,10 @@ int tvolap_server_set_option(tvolap_server_t s, int option, int64_t value)
         if (value != 0 && value != 1) return TVOLAP_ERR_ARG;
         s->timing = (int)value;
         return TVOLAP_OK;
+    case TVOLAP_SERVER_OPT_FAIL_ADMITS:
+        if (value < 0) return TVOLAP_ERR_ARG;
+        s->sch.fail_admits = value;
+        return TVOLAP_OK;
     default:
         return TVOLAP_ERR_ARG;
     }

@@ -105,6 +105,10 @@ int Scheduler::admit(int L, int M, int n_out, int n_filters, int *id)
 {
     int e = check_stream_args(L, M, n_out, n_filters);
     if (e != TVOLAP_OK) return e;
+    if (fail_admits > 0) {
+        --fail_admits;
+        return TVOLAP_ERR_CAPACITY;
+    }
     if (free_ids_.empty()) return TVOLAP_ERR_CAPACITY;
     const StreamLayout lay = stream_layout(L, M, n_out, n_filters);
     const int64_t off = take(lay.total);
@@ -237,6 +241,14 @@ int tvolap_sched_admit(tvolap_sched_t s, int L, int M, int n_out, int n_filters,
     if (e != TVOLAP_OK) return e;
     if (offset) *offset = s->s.st[*id].offset;
     if (phase) *phase = s->s.st[*id].phase;
+    return TVOLAP_OK;
+}
+
+int tvolap_sched_fail_admits(tvolap_sched_t s, int64_t n)
+{
+    if (!s) return TVOLAP_ERR_STATE;
+    if (n < 0) return TVOLAP_ERR_ARG;
+    s->s.fail_admits = n;
     return TVOLAP_OK;
 }
 

@@ -57,6 +57,10 @@ public:
 
     int base_hop = 0, max_hop = 0, capacity = 0, max_out = 0, n_phase = 1;
     int64_t arena_bytes = 0, used = 0, tick = 0;
+    // Fault injection on the host: the next fail_admits admissions with valid
+    // arguments are refused with TVOLAP_ERR_CAPACITY as if no arena piece were
+    // free, changing nothing else.
+    int64_t fail_admits = 0;
     std::vector<SchedStream> st;
     std::vector<int64_t> phase_load;     // per base tick mod n_phase
 

@@ -18,7 +18,7 @@ import numpy as np
 from . import _lib
 
 STATE_FREE, STATE_PENDING, STATE_LIVE = 0, 1, 2
-OPT_GRAPH, OPT_WAIT_US, OPT_TIMING = 1, 2, 3
+OPT_GRAPH, OPT_WAIT_US, OPT_TIMING, OPT_FAIL_ADMITS = 1, 2, 3, 4
 
 
 class _Stats(ctypes.Structure):
@@ -232,6 +232,11 @@ class Scheduler:
         self._call("tvolap_sched_admit", L, M, n_out, n_filters, ctypes.byref(i),
                    ctypes.byref(off), ctypes.byref(ph))
         return i.value, off.value, ph.value
+
+    def fail_admits(self, n: int):
+        """Fault injection: the next n admissions with valid arguments are
+        refused (TVOLAP_ERR_CAPACITY) and change nothing."""
+        self._call("tvolap_sched_fail_admits", int(n))
 
     def activate(self, i):
         self._call("tvolap_sched_activate", int(i))

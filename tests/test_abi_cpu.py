@@ -97,6 +97,9 @@ def test_null_handle_calls(lib):
     assert lib.tvolap_nu_set_option(None, -1, 1, 0) == -4
     assert lib.tvolap_nu_process_block(None, None, None, None, None, None) == -4
     assert lib.tvolap_nu_create(None, 32, 4, 4, 2, 1, 1, None, 1, None) == -1
+    # host-side fault injection
+    assert lib.tvolap_sched_fail_admits(None, 1) == -4
+    assert lib.tvolap_server_set_option(None, 4, 1) == -4
 
 
 @pytest.mark.parametrize("args", [

@@ -114,6 +114,38 @@ def test_slot_limit_and_failed_admit_changes_nothing():
     assert sch.arena() == (0, (1 << 30))
 
 
+def test_injected_admission_failures_change_nothing():
+    """Fault injection on the host: the next n valid admissions are refused
+    with TVOLAP_ERR_CAPACITY and leave the slots, the arena, the phase loads
+    and the due lists as they were; invalid arguments are still reported as
+    such and do not use up an injected failure; then admission resumes with
+    the same placement it would have had."""
+    ref = Scheduler(16, 64, 4, 2, 1 << 24)
+    sch = Scheduler(16, 64, 4, 2, 1 << 24)
+    for s in (ref, sch):
+        a = s.admit(32, 3, 2, 4)
+        s.activate(a[0])
+        s.advance()
+    state = (sch.arena(), sch.phase_loads().tolist(), sch.due().tolist())
+    sch.fail_admits(2)
+    for _ in range(2):
+        with pytest.raises(TvolapError) as ei:
+            sch.admit(64, 5, 2, 4)
+        assert ei.value.status == CAPACITY
+        with pytest.raises(TvolapError) as ei:
+            sch.admit(48, 5, 2, 4)                       # bad hop: not an injected failure
+        assert ei.value.status == ARG
+        assert (sch.arena(), sch.phase_loads().tolist(), sch.due().tolist()) == state
+    sch.fail_admits(0)                                   # clearing works too
+    sch.fail_admits(1)
+    with pytest.raises(TvolapError):
+        sch.admit(64, 5, 2, 4)
+    assert sch.admit(64, 5, 2, 4) == ref.admit(64, 5, 2, 4)
+    with pytest.raises(TvolapError) as ei:
+        sch.fail_admits(-1)
+    assert ei.value.status == ARG
+
+
 @pytest.mark.parametrize("args", [(48, 1, 1, 1), (8, 1, 1, 1), (128, 1, 1, 1), (32, 0, 1, 1),
                                   (32, 1, 3, 1), (32, 1, 1, 0)])
 def test_bad_stream_arguments(args):
