@@ -60,7 +60,6 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
-import sys
 import threading
 
 import numpy as np
