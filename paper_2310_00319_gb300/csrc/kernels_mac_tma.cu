@@ -338,7 +338,6 @@ constexpr int XRING = 64;                             // rows; chunk c writes sl
 // four filters); groups with more go to the overflow list.
 template <int NSM, int BPL>
 struct GroupGeo {
-    static constexpr int ROWB = 32 * BPL;              // float2 per staged row
     static constexpr int HSTAGE_ROWS = NSM * TMA_D;
     static constexpr int BYTES = 256 + (XRING + NSTAGE * HSTAGE_ROWS) * ROW_BYTES * BPL;
     // CTAs per SM the registers must allow
@@ -647,7 +646,6 @@ static_assert(sizeof(PersistSmem) <= PERSIST_HEAD, "persistent header must fit i
 template <int NSM, int BPL, int PST>
 struct PersistGeo {
     static_assert(PST >= 2 && PST <= 5, "stages");
-    static constexpr int ROWB = 32 * BPL;
     static constexpr int PSTAGE = PST;
     static constexpr int PRING = PST <= 4 ? 64 : 8 * (PST + 4);   // >= 8 (PST + 4)
     static constexpr int HSTAGE_ROWS = NSM * TMA_D;
