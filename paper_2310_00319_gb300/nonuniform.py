@@ -75,8 +75,9 @@ class NonUniform:
                    irs.shape[1])
 
     def process_signal(self, x: torch.Tensor, sched_a, sched_b=None, sched_alpha=None,
-                       out_len: int | None = None) -> torch.Tensor:
-        """Offline: x [n_in, N] -> y [n_out, out_len]; schedules per head block."""
+                       out_len: int | None = None, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Offline: x [n_in, N] -> y [n_out, out_len] (into out [n_out, >= out_len]
+        when given); schedules per head block."""
         x = _dims(_need(x, torch.float32, self.device, "x", 2), "x", self.n_in, None)
         N = x.shape[1]
         out_len = N if out_len is None else int(out_len)
@@ -90,10 +91,14 @@ class NonUniform:
         sb = None if sched_b is None else _need(sched_b, torch.int32, self.device, "sched_b", 2)
         sal = None if sched_alpha is None else _need(sched_alpha, torch.float32, self.device,
                                                      "sched_alpha", 2)
-        y = torch.empty((self.n_out, out_len), dtype=torch.float32, device=self.device)
+        if out is None:
+            out = torch.empty((self.n_out, out_len), dtype=torch.float32, device=self.device)
+        _dims(_need(out, torch.float32, self.device, "out", 2), "out", self.n_out, None)
+        if out.shape[1] < out_len:
+            raise ValueError(f"out must have >= {out_len} columns")
         self._call("tvolap_nu_process_signal", _ptr(x), N, N, _ptr(sa), _ptr(sb), _ptr(sal),
-                   sa.shape[1], _ptr(y), out_len, out_len)
-        return y
+                   sa.shape[1], _ptr(out), out_len, out.shape[1])
+        return out
 
     def process_block(self, x: torch.Tensor, out: torch.Tensor | None = None, sel_a=None,
                       sel_b=None, sel_alpha=None) -> torch.Tensor:

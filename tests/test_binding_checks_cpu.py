@@ -133,6 +133,12 @@ def test_nonuniform_block_extents():
     _refused(nu, lambda: nu.process_block(x, z((N_OUT, L - 1))))
     _refused(nu, lambda: nu.process_block(x, None, z(N_OUT - 1, I32)))
     _refused(nu, lambda: nu.process_signal(z((N_IN + 1, 64)), z((N_OUT, 8), I32)))
+    sched = z((N_OUT, n_blocks_for(64, L)), I32)
+    _reaches(nu, "tvolap_nu_process_signal", lambda: nu.process_signal(z((N_IN, 64)), sched))
+    _reaches(nu, "tvolap_nu_process_signal",
+             lambda: nu.process_signal(z((N_IN, 64)), sched, out=z((N_OUT, 70))))
+    _refused(nu, lambda: nu.process_signal(z((N_IN, 64)), sched, out=z((N_OUT, 63))))
+    _refused(nu, lambda: nu.process_signal(z((N_IN, 64)), sched, out=z((N_OUT - 1, 64))))
 
 
 def test_batch_source_and_server_snapshot_buffers():
