@@ -140,9 +140,13 @@ class ClockSampler:
         self.reader = threading.Thread(target=self._read, daemon=True)
         self.reader.start()
         deadline = time.time() + wait_s
-        while prime is not None and not self.first.is_set() and time.time() < deadline:
-            prime()
-            self.primed += 1
+        try:
+            while prime is not None and not self.first.is_set() and time.time() < deadline:
+                prime()
+                self.primed += 1
+        except BaseException:
+            self._stop()
+            raise
         return self
 
     def command(self):
@@ -164,7 +168,10 @@ class ClockSampler:
 
     def __exit__(self, *exc):
         self.t_close = time.time()
-        if self.proc is None:
+        self._stop()
+
+    def _stop(self):
+        if self.proc is None or self.proc.poll() is not None:
             return
         self.proc.terminate()
         try:

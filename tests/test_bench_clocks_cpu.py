@@ -115,3 +115,13 @@ def test_smi_index_falls_back_without_a_gpu():
     if torch.cuda.is_available():
         pytest.skip("needs a machine without a GPU")
     assert bench.smi_index(torch.device("cuda", 3)) == "3"
+
+
+def test_failing_prime_stops_the_sampler():
+    clk = FakeSampler(period=0.5)
+
+    def prime():
+        raise RuntimeError("step failed")
+    with pytest.raises(RuntimeError):
+        clk.start(prime=prime)
+    assert clk.proc.poll() is not None
