@@ -118,7 +118,7 @@ def test_smi_index_falls_back_without_a_gpu():
 
 
 def test_failing_prime_stops_the_sampler():
-    clk = FakeSampler(period=0.5)
+    clk = FakeSampler(period=0.01, buffered=True)     # no row arrives early: prime runs
 
     def prime():
         raise RuntimeError("step failed")
