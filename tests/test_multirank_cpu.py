@@ -1,7 +1,9 @@
 """The N > 1 path on CPU: world-size-2 gloo ranks run the bench's whole-job
-rate (max elapsed over ranks, units of all ranks), and the reference arm
-leaves ranks other than 0 without work. Channels, sources and streams are
-independent, so ranks are replicas: no data-path collective exists to test."""
+rate (max elapsed over ranks, units of all ranks), the reference arm
+leaves ranks other than 0 without work, and a rank that leaves between steps
+makes the survivor's next collective fail instead of hang. Channels, sources
+and streams are independent, so ranks are replicas: no data-path collective
+exists to test."""
 import os
 import socket
 import subprocess
@@ -64,3 +66,38 @@ def test_reference_arm_other_ranks_exit_without_work():
                        capture_output=True, text=True, env=env, timeout=300, cwd=ROOT)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def _rank_leaves(rank, ws, port, q):
+    import datetime
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=ws, timeout=datetime.timedelta(seconds=10))
+    dist.barrier()                                  # both ranks up
+    if rank == 1:
+        os._exit(3)                                 # leaves between steps, nothing in flight
+    try:
+        bench.job_rate(100.0, 1000.0, ws, steps=3, device="cpu")
+        q.put((rank, "no error"))
+    except Exception as e:                          # the collective ends with an error
+        q.put((rank, "error: " + type(e).__name__))
+
+
+def test_a_rank_that_leaves_ends_the_next_collective_with_an_error():
+    """Failure detection without a GPU: rank 1 exits between steps; rank 0's
+    next collective (the whole-job rate's max over ranks) raises within the
+    process group's short timeout instead of hanging."""
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_leaves, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert procs[1].exitcode == 3
+    assert procs[0].exitcode == 0
+    rank, msg = q.get(timeout=5)
+    assert rank == 0 and msg.startswith("error"), msg
