@@ -641,7 +641,8 @@ def run_adjoint(args):
             "config": {"workload": f"differentiable_{C}ch_L256_M47_N240000",
                        "backward": "input spectra recomputed inside the adjoint kernel",
                        "param_bytes": pbytes,
-                       "l2": "parameters (2.9 GB) far larger than the 129 MB L2; no flush"},
+                       "l2": f"parameters ({pbytes / 1e9:.2f} GB) read and written per step, "
+                             "larger than the 129 MB L2; no flush"},
             "segmented_k32_ms_per_step": round(seg_ms, 4),
             "roofline": {"bound": "hbm", "achieved": round(adj_gbs, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(adj_gbs / hbm, 4), "traffic": None,
