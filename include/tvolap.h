@@ -323,9 +323,14 @@ TVOLAP_API int tvolap_bank_spectra(tvolap_t h, int slot, float *out_dev);
  * and the caller still passes every input and output buffer.
  *  - Returns TVOLAP_ERR_CAPACITY when 8 * P * n_blocks * (n_in + n_out) exceeds
  *    TVOLAP_STATIC_SCRATCH_BYTES, with nothing enqueued.
+ *  - The device that is current at the call must be the plan's (its
+ *    stream's) device; otherwise TVOLAP_ERR_ARG, with nothing enqueued.
  *  - The first call on a device looks the array's device address up
- *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress, with that device current). Under lazy module
+ *    loading that first lookup is also when the device reserves the
+ *    TVOLAP_STATIC_SCRATCH_BYTES of the array, so make the first call at
+ *    start-up, before any stream capture and before the device-memory budget
+ *    is fixed; later calls take no device memory.
  *  - All calls, from every handle on a device, share the one array; calls that
  *    overlap on the GPU (other streams, other threads) race on it and give
  *    undefined results. Each call writes all the scratch it reads, so nothing
@@ -670,6 +675,46 @@ TVOLAP_API int tvolap_server_admit(tvolap_server_t s, int L, int M, int n_out, i
                                    const float *ir_dev, int ir_len, int64_t ir_stride, int *id);
 
 /*
+ * Admission queue (continuous batching, Section 2's c channels served block by
+ * block as they come and go). A request that finds no free slot or arena
+ * piece waits instead of being refused; waiting requests are admitted in
+ * arrival order, oldest first, as retired streams free their slots and
+ * memory: at tvolap_server_submit itself and at every tvolap_server_due, so
+ * at most one base tick after the room appears. Nothing overtakes the oldest
+ * request (a large request at the head holds back smaller ones behind it).
+ * tvolap_server_admit does not look at the queue.
+ *
+ * tvolap_server_submit
+ *   arguments as tvolap_server_admit, except ticket, which receives the
+ *   request's number (1, 2, 3, ... in submission order). ir_dev stays valid
+ *   until the request has been admitted and its stream is live, or it is
+ *   cancelled, or the server is destroyed. Returns TVOLAP_ERR_ARG for
+ *   invalid arguments and TVOLAP_ERR_CAPACITY only when the stream's
+ *   footprint is larger than the whole arena (it could never be admitted);
+ *   otherwise TVOLAP_OK, whether the request was admitted at once or queued.
+ * tvolap_server_admitted
+ *   moves out up to cap records of requests admitted from the queue since the
+ *   last call, oldest first: tickets[k] received stream id ids[k] after
+ *   waiting wait_ticks[k] base ticks (wait_ticks may be NULL); *count
+ *   receives the number written. Records not taken stay for the next call.
+ * tvolap_server_cancel
+ *   removes a still-waiting request (TVOLAP_ERR_ARG when ticket is not
+ *   waiting: unknown, admitted or cancelled).
+ * tvolap_server_queue
+ *   requests waiting, the base ticks the oldest has waited, requests admitted
+ *   from the queue so far and the longest wait of those (any pointer may be
+ *   NULL).
+ */
+TVOLAP_API int tvolap_server_submit(tvolap_server_t s, int L, int M, int n_out, int n_filters,
+                                    const float *ir_dev, int ir_len, int64_t ir_stride,
+                                    int64_t *ticket);
+TVOLAP_API int tvolap_server_admitted(tvolap_server_t s, int64_t *tickets, int32_t *ids,
+                                      int64_t *wait_ticks, int cap, int *count);
+TVOLAP_API int tvolap_server_cancel(tvolap_server_t s, int64_t ticket);
+TVOLAP_API int tvolap_server_queue(tvolap_server_t s, int *waiting, int64_t *oldest_wait_ticks,
+                                   int64_t *admitted_total, int64_t *max_wait_ticks);
+
+/*
  * Stream snapshots (serving resilience, migration between slots or servers):
  * tvolap_server_stream_bytes gives the bytes of stream id's snapshot (a
  * 256-byte header, then its arena piece: transformed filters, delay line,
@@ -715,6 +760,8 @@ TVOLAP_API int tvolap_server_staging(tvolap_server_t s, int buffer, float **in,
 /*
  * Streams due at the next tick, in increasing id order (live streams whose
  * phase matches; streams whose admission work has finished turn live here).
+ * Admits waiting requests of the admission queue that now fit (they turn
+ * live at a later tick, once their bank transform has finished).
  * First waits for the tick that last used the next tick's staging set, whose
  * index goes to *buffer (may be NULL). Writes up to cap ids to ids_host and
  * the total to count.
@@ -802,6 +849,16 @@ TVOLAP_API int tvolap_sched_admit(tvolap_sched_t s, int L, int M, int n_out, int
 /* Fault injection (as TVOLAP_SERVER_OPT_FAIL_ADMITS): the next n admissions
    with valid arguments return TVOLAP_ERR_CAPACITY and change nothing. */
 TVOLAP_API int tvolap_sched_fail_admits(tvolap_sched_t s, int64_t n);
+/* Admission queue (as tvolap_server_submit / _admitted / _cancel / _queue):
+   submit queues a request and admits from the queue at once; pump admits
+   waiting requests, oldest first, while they fit (*admitted may be NULL). */
+TVOLAP_API int tvolap_sched_submit(tvolap_sched_t s, int L, int M, int n_out, int n_filters,
+                                   int64_t *ticket);
+TVOLAP_API int tvolap_sched_pump(tvolap_sched_t s, int *admitted);
+TVOLAP_API int tvolap_sched_cancel(tvolap_sched_t s, int64_t ticket);
+TVOLAP_API int tvolap_sched_admitted(tvolap_sched_t s, int64_t *tickets, int32_t *ids,
+                                     int64_t *wait_ticks, int cap, int *count);
+TVOLAP_API int tvolap_sched_queue(tvolap_sched_t s, int *waiting, int64_t *oldest_wait_ticks);
 TVOLAP_API int tvolap_sched_activate(tvolap_sched_t s, int id);
 TVOLAP_API int tvolap_sched_retire(tvolap_sched_t s, int id);
 /* Due ids at the next tick (live streams only), as tvolap_server_due. */

@@ -111,6 +111,11 @@ SIGNATURES = {
     "tvolap_server_footprint": (c_int, [c_void_p, c_int, c_int, c_int, c_int, P_int64]),
     "tvolap_server_admit": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_int64,
                                     P_int]),
+    "tvolap_server_submit": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int,
+                                     c_int64, P_int64]),
+    "tvolap_server_admitted": (c_int, [c_void_p, P_int64, P_int32, P_int64, c_int, P_int]),
+    "tvolap_server_cancel": (c_int, [c_void_p, c_int64]),
+    "tvolap_server_queue": (c_int, [c_void_p, P_int, P_int64, P_int64, P_int64]),
     "tvolap_server_retire": (c_int, [c_void_p, c_int]),
     "tvolap_server_stream_bytes": (c_int, [c_void_p, c_int, P_int64]),
     "tvolap_server_snapshot": (c_int, [c_void_p, c_int, c_void_p, c_int64]),
@@ -130,6 +135,11 @@ SIGNATURES = {
     "tvolap_sched_footprint": (c_int, [c_int, c_int, c_int, c_int, P_int64]),
     "tvolap_sched_admit": (c_int, [c_void_p, c_int, c_int, c_int, c_int, P_int, P_int64, P_int]),
     "tvolap_sched_fail_admits": (c_int, [c_void_p, c_int64]),
+    "tvolap_sched_submit": (c_int, [c_void_p, c_int, c_int, c_int, c_int, P_int64]),
+    "tvolap_sched_pump": (c_int, [c_void_p, P_int]),
+    "tvolap_sched_cancel": (c_int, [c_void_p, c_int64]),
+    "tvolap_sched_admitted": (c_int, [c_void_p, P_int64, P_int32, P_int64, c_int, P_int]),
+    "tvolap_sched_queue": (c_int, [c_void_p, P_int, P_int64]),
     "tvolap_sched_activate": (c_int, [c_void_p, c_int]),
     "tvolap_sched_retire": (c_int, [c_void_p, c_int]),
     "tvolap_sched_due": (c_int, [c_void_p, P_int32, c_int, P_int]),

@@ -435,36 +435,27 @@ int take_slot(tvolap_server *s, int L, int M, int n_out, int n_filters, int c, i
     return TVOLAP_OK;
 }
 
-// Stream snapshot: this header, then the stream's arena piece (transformed
-// filters, delay line, pending sums, input history) at byte 256.
-struct StreamSnapHeader {
-    uint32_t magic, version;
-    int32_t L, M, n_out, n_filters, sel, pad;
-    int64_t blocks, piece;
-};
-constexpr uint32_t SNAP_MAGIC = 0x53535654u;   // "TVSS"
-constexpr int64_t SNAP_DATA = 256;
-static_assert(sizeof(StreamSnapHeader) <= SNAP_DATA, "snapshot header");
-
-}  // namespace
-
-extern "C" {
-
-int tvolap_server_admit(tvolap_server_t s, int L, int M, int n_out, int n_filters,
-                        const float *ir_dev, int ir_len, int64_t ir_stride, int *id)
+// Arguments of an admission (or a submitted request): responses, hop class.
+int check_admit_args(tvolap_server *s, int L, int M, int n_out, int n_filters, const float *ir_dev,
+                     int ir_len, int64_t ir_stride, int *cls)
 {
-    TVOLAP_TRACE();
-    if (!s) return TVOLAP_ERR_STATE;
-    if (!id || ir_len < 0 || (int64_t)ir_len > 2 * (int64_t)L * M || (ir_len > 0 && !ir_dev) ||
+    if (ir_len < 0 || (int64_t)ir_len > 2 * (int64_t)L * M || (ir_len > 0 && !ir_dev) ||
         ir_stride < ir_len)
         return TVOLAP_ERR_ARG;
     if (ir_dev && (reinterpret_cast<uintptr_t>(ir_dev) & 3u)) return TVOLAP_ERR_ARG;
-    int e = s->sch.check_stream_args(L, M, n_out, n_filters);
+    const int e = s->sch.check_stream_args(L, M, n_out, n_filters);
     if (e != TVOLAP_OK) return e;
-    const int c = class_of(s, L);
-    if (c < 0) return TVOLAP_ERR_ARG;
+    *cls = class_of(s, L);
+    return *cls < 0 ? TVOLAP_ERR_ARG : TVOLAP_OK;
+}
+
+// Admission proper: a slot and piece, the state zeroed and the bank
+// transformed (Eqs. 2, 4, 6) on the admission stream; live once that is done.
+int admit_now(tvolap_server *s, int L, int M, int n_out, int n_filters, const float *ir_dev,
+              int ir_len, int64_t ir_stride, int c, int *id)
+{
     int i = -1;
-    e = take_slot(s, L, M, n_out, n_filters, c, &i);
+    int e = take_slot(s, L, M, n_out, n_filters, c, &i);
     if (e != TVOLAP_OK) return e;
     const SchedStream &ss = s->sch.st[i];
     char *base = s->arena + ss.offset;
@@ -486,6 +477,82 @@ int tvolap_server_admit(tvolap_server_t s, int L, int M, int n_out, int n_filter
     if (cudaEventRecord(s->adm_ev[i], s->adm) != cudaSuccess) return undo(TVOLAP_ERR_CUDA);
     s->pending.push_back(i);
     *id = i;
+    return TVOLAP_OK;
+}
+
+// Admit queued requests, oldest first, while slots and arena pieces allow.
+int pump_queue(tvolap_server *s)
+{
+    return s->sch.pump([&](const AdmitRequest &r, int *id) {
+        return admit_now(s, r.L, r.M, r.n_out, r.n_filters, static_cast<const float *>(r.payload),
+                         (int)r.arg0, r.arg1, class_of(s, r.L), id);
+    }, nullptr);
+}
+
+// Stream snapshot: this header, then the stream's arena piece (transformed
+// filters, delay line, pending sums, input history) at byte 256.
+struct StreamSnapHeader {
+    uint32_t magic, version;
+    int32_t L, M, n_out, n_filters, sel, pad;
+    int64_t blocks, piece;
+};
+constexpr uint32_t SNAP_MAGIC = 0x53535654u;   // "TVSS"
+constexpr int64_t SNAP_DATA = 256;
+static_assert(sizeof(StreamSnapHeader) <= SNAP_DATA, "snapshot header");
+
+}  // namespace
+
+extern "C" {
+
+int tvolap_server_admit(tvolap_server_t s, int L, int M, int n_out, int n_filters,
+                        const float *ir_dev, int ir_len, int64_t ir_stride, int *id)
+{
+    TVOLAP_TRACE();
+    if (!s) return TVOLAP_ERR_STATE;
+    if (!id) return TVOLAP_ERR_ARG;
+    int c = -1;
+    const int e = check_admit_args(s, L, M, n_out, n_filters, ir_dev, ir_len, ir_stride, &c);
+    if (e != TVOLAP_OK) return e;
+    return admit_now(s, L, M, n_out, n_filters, ir_dev, ir_len, ir_stride, c, id);
+}
+
+int tvolap_server_submit(tvolap_server_t s, int L, int M, int n_out, int n_filters,
+                         const float *ir_dev, int ir_len, int64_t ir_stride, int64_t *ticket)
+{
+    TVOLAP_TRACE();
+    if (!s) return TVOLAP_ERR_STATE;
+    if (!ticket) return TVOLAP_ERR_ARG;
+    int c = -1;
+    int e = check_admit_args(s, L, M, n_out, n_filters, ir_dev, ir_len, ir_stride, &c);
+    if (e != TVOLAP_OK) return e;
+    e = s->sch.submit(L, M, n_out, n_filters, ir_dev, ir_len, ir_stride, ticket);
+    if (e != TVOLAP_OK) return e;
+    return pump_queue(s);
+}
+
+int tvolap_server_admitted(tvolap_server_t s, int64_t *tickets, int32_t *ids, int64_t *wait_ticks,
+                           int cap, int *count)
+{
+    if (!s) return TVOLAP_ERR_STATE;
+    if (!count || cap < 0 || (cap > 0 && (!tickets || !ids))) return TVOLAP_ERR_ARG;
+    *count = s->sch.take_admitted(tickets, ids, wait_ticks, cap);
+    return TVOLAP_OK;
+}
+
+int tvolap_server_cancel(tvolap_server_t s, int64_t ticket)
+{
+    if (!s) return TVOLAP_ERR_STATE;
+    return s->sch.cancel(ticket);
+}
+
+int tvolap_server_queue(tvolap_server_t s, int *waiting, int64_t *oldest_wait_ticks,
+                        int64_t *admitted_total, int64_t *max_wait_ticks)
+{
+    if (!s) return TVOLAP_ERR_STATE;
+    if (waiting) *waiting = s->sch.queue_len();
+    if (oldest_wait_ticks) *oldest_wait_ticks = s->sch.oldest_wait();
+    if (admitted_total) *admitted_total = s->sch.admitted_from_queue;
+    if (max_wait_ticks) *max_wait_ticks = s->sch.max_wait;
     return TVOLAP_OK;
 }
 
@@ -591,6 +658,8 @@ int tvolap_server_due(tvolap_server_t s, int32_t *ids_host, int cap, int *count,
         complete(s, b);
     }
     activate_ready(s);
+    const int pe = pump_queue(s);            // requests waiting for a slot and memory
+    if (pe != TVOLAP_OK) return pe;
     s->sch.due(s->ids);
     for (int i = 0; i < (int)s->ids.size() && i < cap; ++i) ids_host[i] = s->ids[i];
     *count = (int)s->ids.size();

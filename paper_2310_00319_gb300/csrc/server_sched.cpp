@@ -50,6 +50,10 @@ int Scheduler::init(int base, int mx, int cap, int mo, int64_t arena)
     for (int i = 0; i < cap; ++i) free_ids_.insert(i);
     free_.clear();
     if (arena_bytes > 0) free_[0] = arena_bytes;
+    queue_.clear();
+    admitted_.clear();
+    next_ticket_ = 1;
+    submitted = admitted_from_queue = cancelled = max_wait = sum_wait = 0;
     return TVOLAP_OK;
 }
 
@@ -148,6 +152,54 @@ int Scheduler::admit(int L, int M, int n_out, int n_filters, int *id)
     used += lay.total;
     *id = i;
     return TVOLAP_OK;
+}
+
+int Scheduler::submit(int L, int M, int n_out, int n_filters, const void *payload, int64_t arg0,
+                      int64_t arg1, int64_t *ticket)
+{
+    const int e = check_stream_args(L, M, n_out, n_filters);
+    if (e != TVOLAP_OK) return e;
+    if (stream_layout(L, M, n_out, n_filters).total > arena_bytes) return TVOLAP_ERR_CAPACITY;
+    AdmitRequest r;
+    r.ticket = next_ticket_++;
+    r.submit_tick = tick;
+    r.L = L;
+    r.M = M;
+    r.n_out = n_out;
+    r.n_filters = n_filters;
+    r.payload = payload;
+    r.arg0 = arg0;
+    r.arg1 = arg1;
+    queue_.push_back(r);
+    ++submitted;
+    *ticket = r.ticket;
+    return TVOLAP_OK;
+}
+
+int Scheduler::cancel(int64_t ticket)
+{
+    for (auto it = queue_.begin(); it != queue_.end(); ++it) {
+        if (it->ticket == ticket) {
+            queue_.erase(it);
+            ++cancelled;
+            return TVOLAP_OK;
+        }
+    }
+    return TVOLAP_ERR_ARG;
+}
+
+int Scheduler::take_admitted(int64_t *tickets, int32_t *ids, int64_t *waits, int cap)
+{
+    int n = 0;
+    while (n < cap && !admitted_.empty()) {
+        const AdmitRecord &r = admitted_.front();
+        if (tickets) tickets[n] = r.ticket;
+        if (ids) ids[n] = r.id;
+        if (waits) waits[n] = r.wait_ticks;
+        admitted_.pop_front();
+        ++n;
+    }
+    return n;
 }
 
 int Scheduler::activate(int id)
@@ -249,6 +301,48 @@ int tvolap_sched_fail_admits(tvolap_sched_t s, int64_t n)
     if (!s) return TVOLAP_ERR_STATE;
     if (n < 0) return TVOLAP_ERR_ARG;
     s->s.fail_admits = n;
+    return TVOLAP_OK;
+}
+
+int tvolap_sched_submit(tvolap_sched_t s, int L, int M, int n_out, int n_filters, int64_t *ticket)
+{
+    if (!s) return TVOLAP_ERR_STATE;
+    if (!ticket) return TVOLAP_ERR_ARG;
+    int e = s->s.submit(L, M, n_out, n_filters, nullptr, 0, 0, ticket);
+    if (e != TVOLAP_OK) return e;
+    return s->s.pump([&](const tvolap::AdmitRequest &r, int *id) {
+        return s->s.admit(r.L, r.M, r.n_out, r.n_filters, id);
+    }, nullptr);
+}
+
+int tvolap_sched_pump(tvolap_sched_t s, int *admitted)
+{
+    if (!s) return TVOLAP_ERR_STATE;
+    return s->s.pump([&](const tvolap::AdmitRequest &r, int *id) {
+        return s->s.admit(r.L, r.M, r.n_out, r.n_filters, id);
+    }, admitted);
+}
+
+int tvolap_sched_cancel(tvolap_sched_t s, int64_t ticket)
+{
+    if (!s) return TVOLAP_ERR_STATE;
+    return s->s.cancel(ticket);
+}
+
+int tvolap_sched_admitted(tvolap_sched_t s, int64_t *tickets, int32_t *ids, int64_t *wait_ticks,
+                          int cap, int *count)
+{
+    if (!s) return TVOLAP_ERR_STATE;
+    if (!count || cap < 0) return TVOLAP_ERR_ARG;
+    *count = s->s.take_admitted(tickets, ids, wait_ticks, cap);
+    return TVOLAP_OK;
+}
+
+int tvolap_sched_queue(tvolap_sched_t s, int *waiting, int64_t *oldest_wait_ticks)
+{
+    if (!s) return TVOLAP_ERR_STATE;
+    if (waiting) *waiting = s->s.queue_len();
+    if (oldest_wait_ticks) *oldest_wait_ticks = s->s.oldest_wait();
     return TVOLAP_OK;
 }
 

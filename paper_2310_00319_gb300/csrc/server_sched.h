@@ -5,9 +5,12 @@
 #pragma once
 
 #include <cstdint>
+#include <deque>
 #include <map>
 #include <set>
 #include <vector>
+
+#include "../../include/tvolap.h"
 
 namespace tvolap {
 
@@ -37,6 +40,24 @@ struct SchedStream {
     int64_t load = 0;       // stream_block_bytes
 };
 
+// A request waiting for admission: a stream's shape, the base tick at which
+// it was submitted and an opaque payload that the server keeps for it (its
+// response buffer); the scheduler never dereferences the payload.
+struct AdmitRequest {
+    int64_t ticket = 0, submit_tick = 0;
+    int L = 0, M = 0, n_out = 0, n_filters = 0;
+    const void *payload = nullptr;
+    int64_t arg0 = 0, arg1 = 0;
+};
+
+// A request that left the queue: its ticket, the stream id it received and
+// the base ticks it waited.
+struct AdmitRecord {
+    int64_t ticket = 0;
+    int id = -1;
+    int64_t wait_ticks = 0;
+};
+
 class Scheduler {
 public:
     // Returns 0 or a negative tvolap_status.
@@ -52,6 +73,43 @@ public:
     // Undo advance(ids) of the last tick.
     void rollback(const std::vector<int> &ids);
 
+    // Admission queue (continuous batching): requests wait in arrival order
+    // and are admitted, oldest first, as slots and arena pieces free up.
+    // submit() refuses only a request that could never fit (its footprint is
+    // larger than the whole arena) with TVOLAP_ERR_CAPACITY.
+    int submit(int L, int M, int n_out, int n_filters, const void *payload, int64_t arg0,
+               int64_t arg1, int64_t *ticket);
+    // Admit from the head of the queue while admission succeeds; try_admit(req, &id)
+    // returns a tvolap_status and, on success, the new stream's id. Stops at the
+    // first TVOLAP_ERR_CAPACITY (strict arrival order: nothing overtakes the
+    // head); any other error is returned with the head still queued.
+    template <class F>
+    int pump(F try_admit, int *n_admitted)
+    {
+        int n = 0;
+        while (!queue_.empty()) {
+            const AdmitRequest &r = queue_.front();
+            int id = -1;
+            const int e = try_admit(r, &id);
+            if (e != TVOLAP_OK) {
+                if (n_admitted) *n_admitted = n;
+                return e == TVOLAP_ERR_CAPACITY ? TVOLAP_OK : e;   // no room yet: wait
+            }
+            admitted_.push_back(AdmitRecord{r.ticket, id, tick - r.submit_tick});
+            wait_hist_add(tick - r.submit_tick);
+            queue_.pop_front();
+            ++n;
+        }
+        if (n_admitted) *n_admitted = n;
+        return TVOLAP_OK;
+    }
+    int cancel(int64_t ticket);
+    // Moves up to cap records of admissions from the queue (oldest first) out.
+    int take_admitted(int64_t *tickets, int32_t *ids, int64_t *waits, int cap);
+    int queue_len() const { return (int)queue_.size(); }
+    int64_t oldest_wait() const { return queue_.empty() ? 0 : tick - queue_.front().submit_tick; }
+    int64_t submitted = 0, admitted_from_queue = 0, cancelled = 0, max_wait = 0, sum_wait = 0;
+
     int64_t largest_free() const;
     bool valid_id(int id) const { return id >= 0 && id < capacity && st[id].state != 0; }
 
@@ -65,7 +123,16 @@ public:
     std::vector<int64_t> phase_load;     // per base tick mod n_phase
 
 private:
+    void wait_hist_add(int64_t w)
+    {
+        ++admitted_from_queue;
+        sum_wait += w;
+        if (w > max_wait) max_wait = w;
+    }
     int64_t take(int64_t bytes);         // arena offset or -1
+    std::deque<AdmitRequest> queue_;
+    std::deque<AdmitRecord> admitted_;
+    int64_t next_ticket_ = 1;
     void give(int64_t off, int64_t bytes);
     std::set<int> free_ids_;
     std::map<int64_t, int64_t> free_;    // offset -> size

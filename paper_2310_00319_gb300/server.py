@@ -72,6 +72,11 @@ class Server:
         self.buf = 0             # staging set of the next tick (set by due)
         self._ids = np.zeros(capacity, np.int32)
         self._keep = {}          # response buffers held until their stream is live
+        self._queued = {}        # response buffers of requests waiting in the queue
+        self._admitted = []      # (ticket, id, wait_ticks) not yet taken by admitted()
+        self._adm_t = np.zeros(capacity, np.int64)
+        self._adm_i = np.zeros(capacity, np.int32)
+        self._adm_w = np.zeros(capacity, np.int64)
 
     # ------------------------------------------------------------------ lifetime
     def close(self):
@@ -80,6 +85,7 @@ class Server:
             self.h = ctypes.c_void_p()
             self._in = self._out = self.sel = None
             self._keep.clear()
+            self._queued.clear()
 
     def __del__(self):
         try:
@@ -89,6 +95,60 @@ class Server:
 
     def _call(self, name, *args):
         return _lib.check(getattr(self.lib, name)(self.h, *args), name)
+
+    # ------------------------------------------------------------------ queue
+    @staticmethod
+    def _irs(irs):
+        import torch
+        if irs.dtype != torch.float32 or irs.device.type != "cuda" or irs.dim() != 3:
+            raise ValueError("irs must be a CUDA float32 tensor [n_filters, n_out, ir_len]")
+        return irs.contiguous()
+
+    def submit(self, L: int, irs, M: int | None = None) -> int:
+        """Queue a stream (admission queue): admitted at once when it fits,
+        otherwise, in arrival order, at a later due() as streams retire.
+        Returns the request's ticket; admitted() maps tickets to stream ids."""
+        import torch
+        irs = self._irs(irs)
+        F, n_out, ir_len = irs.shape
+        M = partitions(ir_len, L) if M is None else M
+        t = ctypes.c_int64()
+        with torch.cuda.device(self.device):
+            self._call("tvolap_server_submit", L, M, n_out, F, ctypes.c_void_p(irs.data_ptr()),
+                       ir_len, ir_len, ctypes.byref(t))
+        self._queued[t.value] = irs
+        self._drain()
+        return t.value
+
+    def _drain(self):
+        n = ctypes.c_int()
+        while True:
+            self._call("tvolap_server_admitted", self._adm_t.ctypes.data_as(_lib.P_int64),
+                       self._adm_i.ctypes.data_as(_lib.P_int32),
+                       self._adm_w.ctypes.data_as(_lib.P_int64), self.capacity, ctypes.byref(n))
+            for k in range(n.value):
+                t, i, w = int(self._adm_t[k]), int(self._adm_i[k]), int(self._adm_w[k])
+                self._keep[i] = self._queued.pop(t)
+                self._admitted.append((t, i, w))
+            if n.value < self.capacity:
+                return
+
+    def admitted(self) -> list:
+        """(ticket, stream id, base ticks waited) of the requests admitted from
+        the queue since the last call, oldest first."""
+        out, self._admitted = self._admitted, []
+        return out
+
+    def cancel(self, ticket: int):
+        self._call("tvolap_server_cancel", ctypes.c_int64(ticket))
+        self._queued.pop(ticket, None)
+
+    def queue(self) -> dict:
+        w, o, a, m = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._call("tvolap_server_queue", ctypes.byref(w), ctypes.byref(o), ctypes.byref(a),
+                   ctypes.byref(m))
+        return {"waiting": w.value, "oldest_wait_ticks": o.value, "admitted_total": a.value,
+                "max_wait_ticks": m.value}
 
     # ------------------------------------------------------------------ streams
     def footprint(self, L: int, M: int, n_out: int, n_filters: int) -> int:
@@ -101,9 +161,7 @@ class Server:
         output o). Returns the stream id; raises TvolapError (status
         TVOLAP_ERR_CAPACITY) when it does not fit."""
         import torch
-        if irs.dtype != torch.float32 or irs.device.type != "cuda" or irs.dim() != 3:
-            raise ValueError("irs must be a CUDA float32 tensor [n_filters, n_out, ir_len]")
-        irs = irs.contiguous()
+        irs = self._irs(irs)
         F, n_out, ir_len = irs.shape
         M = partitions(ir_len, L) if M is None else M
         i = ctypes.c_int()
@@ -168,6 +226,7 @@ class Server:
                    ctypes.byref(n), ctypes.byref(b))
         self.buf = b.value
         ids = self._ids[:n.value].copy()
+        self._drain()
         for i in [k for k in self._keep if self.state(k)[0] != STATE_PENDING]:
             del self._keep[i]
         return ids
@@ -226,6 +285,36 @@ class Scheduler:
         _lib.check(_lib.load().tvolap_sched_footprint(L, M, n_out, n_filters, ctypes.byref(b)),
                    "tvolap_sched_footprint")
         return b.value
+
+    def submit(self, L, M, n_out, n_filters) -> int:
+        t = ctypes.c_int64()
+        self._call("tvolap_sched_submit", L, M, n_out, n_filters, ctypes.byref(t))
+        return t.value
+
+    def pump(self) -> int:
+        n = ctypes.c_int()
+        self._call("tvolap_sched_pump", ctypes.byref(n))
+        return n.value
+
+    def cancel(self, ticket: int):
+        self._call("tvolap_sched_cancel", ctypes.c_int64(ticket))
+
+    def admitted(self) -> list:
+        cap = 64
+        t, i, w = np.zeros(cap, np.int64), np.zeros(cap, np.int32), np.zeros(cap, np.int64)
+        n, out = ctypes.c_int(), []
+        while True:
+            self._call("tvolap_sched_admitted", t.ctypes.data_as(_lib.P_int64),
+                       i.ctypes.data_as(_lib.P_int32), w.ctypes.data_as(_lib.P_int64), cap,
+                       ctypes.byref(n))
+            out += [(int(t[k]), int(i[k]), int(w[k])) for k in range(n.value)]
+            if n.value < cap:
+                return out
+
+    def queue(self):
+        w, o = ctypes.c_int(), ctypes.c_int64()
+        self._call("tvolap_sched_queue", ctypes.byref(w), ctypes.byref(o))
+        return w.value, o.value
 
     def admit(self, L, M, n_out, n_filters):
         i, off, ph = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
