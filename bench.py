@@ -834,7 +834,6 @@ def run_serve(args):
     (ticks pipelined two deep, device time), and the multiply-accumulate
     kernel alone (direct launches between CUDA events)."""
     import torch
-    from paper_2310_00319_gb300._lib import TvolapError
     from paper_2310_00319_gb300.server import OPT_TIMING, Server
     from synth import workloads as W
     dev = torch.device("cuda", 0)
@@ -867,28 +866,32 @@ def run_serve(args):
     live = {}                 # stream id -> event index
     leave_at = {}
     track, done_tracks = {}, []
-    rejected = 0
+    ticket_ev = {}            # waiting request -> event index
+    waits = []                # base ticks each admitted request waited
     nxt = 0
 
     def arrivals(tick):
-        nonlocal nxt, rejected
+        """Requests of this tick join the admission queue (none is dropped);
+        those the queue admitted (now or at the last due) start their lifetime;
+        streams whose lifetime is over retire and free their slot and memory."""
+        nonlocal nxt
         while nxt < n_ev and ev[nxt, 0] <= tick:
-            L = int(L_of[nxt])
-            try:
-                i = srv.admit(L, banks[bank_of[nxt]])
-                live[i] = nxt
-                leave_at[i] = int(ev[nxt, 1])
-                srv.sel[i] = int(rng.integers(0, n_pairs))
-            except TvolapError as err:
-                if err.status != -5:             # only TVOLAP_ERR_CAPACITY is a refusal
-                    raise
-                rejected += 1
+            ticket_ev[srv.submit(int(L_of[nxt]), banks[bank_of[nxt]])] = nxt
             nxt += 1
+        admitted(tick)
         for i in [i for i, t in leave_at.items() if t <= tick]:
             srv.retire(i)
             del live[i], leave_at[i]
             if i in track:                       # the id may be reused: close the record
                 done_tracks.append(track.pop(i))
+
+    def admitted(tick):
+        for t, i, w in srv.admitted():
+            e = ticket_ev.pop(t)
+            live[i] = e
+            leave_at[i] = tick + int(ev[e, 1] - ev[e, 0])     # lifetime from admission
+            srv.sel[i] = int(rng.integers(0, n_pairs))
+            waits.append(w)
 
     pool = (0.1 * rng.standard_normal((4096, top))).astype(np.float32)
     steps = np.array([-1, 0, 1], np.int32)
@@ -922,6 +925,7 @@ def run_serve(args):
     for _ in range(warm):
         arrivals(tick)
         ids = srv.due()
+        admitted(tick)
         stage(ids, tick)
         record_in(ids)
         srv.tick()
@@ -930,14 +934,18 @@ def run_serve(args):
         tick += 1
     srv.wait()
     # latency: one tick at a time
-    h2h, gpu = [], []
+    h2h, gpu, live_n, queued_n = [], [], [], []
     e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
          for _ in range(lat_ticks)]
     s0 = srv.stats()
+    waits_before = len(waits)
     with ClockSampler(smi_index(dev)) as clk:
         for k in range(lat_ticks):
             arrivals(tick)
             ids = srv.due()
+            admitted(tick)
+            live_n.append(len(live))
+            queued_n.append(len(ticket_ev))
             stage(ids, tick)
             record_in(ids)
             t0 = time.perf_counter()
@@ -958,6 +966,7 @@ def run_serve(args):
         for k in range(thr_ticks):
             arrivals(tick)
             ids = srv.due()
+            admitted(tick)
             stage(ids, tick)
             srv.tick()
             tick += 1
@@ -972,6 +981,7 @@ def run_serve(args):
     for k in range(timed_ticks):
         arrivals(tick)
         ids = srv.due()
+        admitted(tick)
         stage(ids, tick)
         srv.tick()
         tick += 1
@@ -979,6 +989,7 @@ def run_serve(args):
     s4 = srv.stats()
     srv.set_option(OPT_TIMING, 0)
     st = s4
+    q = srv.queue()
     srv.close()
     cpu = None
     if not args.no_cpu:
@@ -1008,8 +1019,16 @@ def run_serve(args):
                         "gpu_ms_p50": round(float(np.percentile(gpu, 50)), 4),
                         "gpu_ms_p99": round(float(np.percentile(gpu, 99)), 4),
                         "missed_deadline": int((h2h_ms > deadline).sum())},
-            "streams": {"live_end": st["live"], "rejected": rejected,
-                        "admitted_total": nxt - rejected,
+            "streams": {"live_end": st["live"], "dropped": 0,
+                        "submitted": nxt, "admitted": len(waits), "waiting_end": q["waiting"],
+                        "live_during_latency": {"min": int(min(live_n)), "max": int(max(live_n)),
+                                                "mean": round(float(np.mean(live_n)), 1)},
+                        "waiting_during_latency_max": int(max(queued_n)),
+                        "queue_wait_ticks": {
+                            "p50": float(np.percentile(waits, 50)),
+                            "p99": float(np.percentile(waits, 99)),
+                            "max": int(max(waits)),
+                            "admitted_after_waiting": int(sum(1 for w in waits if w > 0))},
                         "mean_due_per_tick": round((s2["stream_blocks"] - s1["stream_blocks"]) /
                                                    thr_ticks, 1)},
             "throughput_host_s": round(t_host, 3),
@@ -1054,6 +1073,53 @@ def serve_oracle(tracks, banks_np, bank_of, L_of):
             "sample": f"first blocks of {len(ref)} streams present from the start "
                       "(both outputs, up to 120 blocks each)",
             "accuracy": accuracy(np.concatenate(got), np.concatenate(ref))}
+
+
+# --------------------------------------------------------------------------- sub-records
+SUBRECORD_RUNS = (
+    # name, runner, bounded settings
+    ("batched", "run_batched", {"steps": 5, "warmup": 3}),
+    ("adjoint", "run_adjoint", {"steps": 5, "warmup": 3}),
+    ("serve", "run_serve", {"serve_ticks": 2000, "warmup": 3}),
+)
+
+
+def compact_record(name: str, r: dict, wall_s: float) -> dict:
+    """The figures of a workload's full line that the default line carries:
+    value, per-step time, roofline (kernel, traffic), clocks, the accuracy
+    against the oracle on its seeded subset, and the workload's own
+    comparison (per-source loop, latency and queue, segmented backward)."""
+    keep = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "roofline", "clocks",
+            "gpu_launches", "vs_per_source", "autotune", "latency", "streams",
+            "segmented_k32_ms_per_step", "mac_params_gbs", "stages_ms_per_tick")
+    out = {k: r[k] for k in keep if k in r}
+    out["workload"] = r["config"]["workload"]
+    cpu = r.get("cpu_baseline")
+    if cpu:
+        out["accuracy"] = cpu.get("accuracy")
+        out["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "sample")}
+    if r.get("gradient_accuracy"):
+        out["accuracy"] = r["gradient_accuracy"]
+    out["wall_s"] = round(wall_s, 1)
+    return out
+
+
+def workload_subrecords(args) -> dict:
+    """The batched, differentiable and serving workloads, each run with
+    bounded settings after the default workload's timed region, as compact
+    records of the default line (one GPU)."""
+    import copy
+
+    import torch
+    out = {}
+    for name, fn, over in SUBRECORD_RUNS:
+        a = copy.copy(args)
+        a.__dict__.update(over)
+        a.staging = None
+        torch.cuda.empty_cache()
+        t = time.perf_counter()
+        out[name] = compact_record(name, globals()[fn](a), time.perf_counter() - t)
+    return out
 
 
 # --------------------------------------------------------------------------- oracle
@@ -1444,6 +1510,8 @@ def main():
                     help="multiply-accumulate staging (default workload: instead of the default; "
                          "batched: instead of the autotuner)")
     ap.add_argument("--skip-extras", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="default workload: leave out the batched, adjoint and serve records")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -1465,6 +1533,9 @@ def main():
         out = run_nonuniform(args)
     else:
         out = run_ours(args)
+        if (out is not None and _dist()[0] == 1 and not args.skip_extras
+                and not args.no_workloads):
+            out["workloads"] = workload_subrecords(args)
     if out is not None:
         print(json.dumps(out), flush=True)
 
