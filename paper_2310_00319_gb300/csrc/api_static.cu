@@ -22,16 +22,26 @@ static __device__ __align__(256) unsigned char g_static_scratch[TVOLAP_STATIC_SC
 
 constexpr int MAX_DEVICES = 64;
 
-// Device address of g_static_scratch, looked up once per device (host code
-// cannot use the symbol itself: on the host it is only a stand-in).
-void *scratch_address(int &status)
+// Device address of g_static_scratch on the plan's device, looked up once per
+// device (host code cannot use the symbol itself: on the host it is only a
+// stand-in). The plan's device is its stream's; the lookup resolves the symbol
+// on the current device, so the two must be the same (TVOLAP_ERR_ARG if not:
+// the kernels would otherwise run on the plan's device against another GPU's
+// copy of the array).
+void *scratch_address(cudaStream_t stream, int &status)
 {
     static std::mutex mu;
     static void *addr[MAX_DEVICES] = {};
-    int dev = 0;
+    int dev = 0, plan_dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaStreamGetDevice(stream, &plan_dev);
     if (e != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+        cudaGetLastError();
         status = TVOLAP_ERR_CUDA;
+        return nullptr;
+    }
+    if (plan_dev != dev) {
+        status = TVOLAP_ERR_ARG;
         return nullptr;
     }
     std::lock_guard<std::mutex> lock(mu);
@@ -67,7 +77,7 @@ extern "C" int tvolap_process_signal_static(tvolap_t h, const float *x_dev, int6
     const int64_t bytes = (int64_t)sizeof(float2) * h->P * nb * (h->n_in + h->n_out);
     if (bytes > (int64_t)TVOLAP_STATIC_SCRATCH_BYTES) return TVOLAP_ERR_CAPACITY;
     int st = TVOLAP_OK;
-    float2 *X = reinterpret_cast<float2 *>(scratch_address(st));
+    float2 *X = reinterpret_cast<float2 *>(scratch_address(h->stream, st));
     if (st != TVOLAP_OK) return st;
     float2 *Y = X + (int64_t)h->n_in * nb * h->P;
     // every element of X and Y is written before it is read: nothing to clear

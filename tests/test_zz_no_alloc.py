@@ -1,22 +1,27 @@
 """tvolap_process_signal_static: the offline path for callers that must not
 allocate device memory while running (a real-time audio callback, a process
 under a fixed device-memory budget). It keeps its scratch in a fixed device
-array; this test calls it through the C ABI and checks it against
-tvolap_process_signal on two calls in a row, and that the second call leaves
-the device's free memory unchanged.
+array. These tests call it through the C ABI and check it against the FP64
+oracle (and against tvolap_process_signal) on two calls in a row, that the
+second call leaves the device's free memory unchanged, that a request of
+exactly the array's size works and one block more is refused, and that a
+call with another device current than the plan's is refused.
 
-Tolerance: relative L2 error <= 1e-5 and max-abs error <= 1e-4 x peak, the
-tolerance of the other GPU parity tests.
+Tolerance: relative L2 error <= 1e-5 and max-abs error <= 1e-4 x the oracle's
+peak, the tolerance of the other GPU parity tests.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from synth import workloads as W
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+STATIC_BYTES = 32 << 20          # TVOLAP_STATIC_SCRATCH_BYTES
 
 
 def _dev():
@@ -38,7 +43,22 @@ def _close(y, ref):
         assert rel <= 1e-5 and mx <= 1e-4, (o, rel, mx)
 
 
-def test_static_scratch_entry_point_matches_process_signal():
+def _static(lib, plan, wl, x, sa, sb, sal, y):
+    return lib.tvolap_process_signal_static(plan.h, _p(x), wl.N, wl.N, _p(sa), _p(sb), _p(sal),
+                                            sa.shape[1], _p(y), wl.out_len, wl.out_len)
+
+
+def _inputs(wl, dev):
+    return (torch.from_numpy(wl.x).to(dev), torch.from_numpy(wl.sched_a).to(dev),
+            torch.from_numpy(wl.sched_b).to(dev), torch.from_numpy(wl.sched_alpha).to(dev))
+
+
+def _oracle(wl):
+    return oracle.tvolap_direct(wl.x, wl.irs, wl.L, wl.sched_a, wl.sched_b, wl.sched_alpha,
+                                out_len=wl.out_len, out_to_in=list(wl.out_to_in))
+
+
+def test_static_scratch_entry_point_matches_oracle():
     dev = _dev()
     from paper_2310_00319_gb300 import Plan, _lib
     lib = _lib.load()
@@ -50,16 +70,12 @@ def test_static_scratch_entry_point_matches_process_signal():
         plan = Plan(128, wl.M, n_in=2, n_out=3, out_to_in=list(wl.out_to_in), n_slots=5,
                     device=dev)
         plan.load_bank(0, torch.from_numpy(wl.irs).to(dev))
-        x = torch.from_numpy(wl.x).to(dev)
-        sa = torch.from_numpy(wl.sched_a).to(dev)
-        sb = torch.from_numpy(wl.sched_b).to(dev)
-        sal = torch.from_numpy(wl.sched_alpha).to(dev)
-        ref = plan.process_signal(x, sa, sb, sal, out_len=wl.out_len).cpu().numpy()
+        x, sa, sb, sal = _inputs(wl, dev)
+        lib_y = plan.process_signal(x, sa, sb, sal, out_len=wl.out_len).cpu().numpy()
         y = torch.full((3, wl.out_len), float("nan"), device=dev)
         torch.cuda.synchronize()
         free_before = torch.cuda.mem_get_info(dev)[0]
-        st = lib.tvolap_process_signal_static(plan.h, _p(x), wl.N, wl.N, _p(sa), _p(sb), _p(sal),
-                                              sa.shape[1], _p(y), wl.out_len, wl.out_len)
+        st = _static(lib, plan, wl, x, sa, sb, sal, y)
         assert st == 0, _lib.STATUS.get(st, st)
         plan.check()
         torch.cuda.synchronize()
@@ -67,8 +83,46 @@ def test_static_scratch_entry_point_matches_process_signal():
         if i > 0:
             # the array was set up by the first call: this call took no device memory
             assert free_after == free_before
-        _close(y.cpu().numpy(), ref)
+        got = y.cpu().numpy()
+        _close(got, _oracle(wl))
+        _close(got, lib_y)
         plan.close()
+
+
+def test_static_scratch_at_capacity_and_one_block_beyond():
+    """One input and one output at L = 128: 8 * P * n_blocks * 2 bytes equals
+    the array's size at n_blocks = 8192 (out_len up to 8191 * 128); that call
+    runs and matches the oracle, and one sample more (8193 blocks) is refused
+    with TVOLAP_ERR_CAPACITY and leaves the output untouched."""
+    dev = _dev()
+    from paper_2310_00319_gb300 import Plan, _lib
+    lib = _lib.load()
+    L, P = 128, 256
+    nb = STATIC_BYTES // (8 * P * 2)
+    assert nb == 8192
+    out_len = (nb - 1) * L                             # the largest length with nb blocks
+    wl = W.random_case(503, L=L, ir_len=400, N=out_len, n_in=1, n_out=1, n_slots=3,
+                       out_len=out_len)
+    assert wl.sched_a.shape[1] == nb
+    plan = Plan(L, wl.M, n_in=1, n_out=1, n_slots=3, device=dev)
+    plan.load_bank(0, torch.from_numpy(wl.irs).to(dev))
+    x, sa, sb, sal = _inputs(wl, dev)
+    y = torch.full((1, out_len), float("nan"), device=dev)
+    st = _static(lib, plan, wl, x, sa, sb, sal, y)
+    assert st == 0, _lib.STATUS.get(st, st)
+    plan.check()
+    _close(y.cpu().numpy(), _oracle(wl))
+    # one block more
+    big = W.random_case(504, L=L, ir_len=400, N=out_len + 1, n_in=1, n_out=1, n_slots=3,
+                        out_len=out_len + 1)
+    assert big.sched_a.shape[1] == nb + 1
+    x, sa, sb, sal = _inputs(big, dev)
+    y2 = torch.full((1, out_len + 1), 7.0, device=dev)
+    st = _static(lib, plan, big, x, sa, sb, sal, y2)
+    assert st == -5                                     # TVOLAP_ERR_CAPACITY
+    torch.cuda.synchronize()
+    assert torch.all(y2 == 7.0)
+    plan.close()
 
 
 def test_static_scratch_rejects_oversize():
@@ -83,4 +137,23 @@ def test_static_scratch_rejects_oversize():
     y = torch.zeros((8, N), device=dev)
     st = lib.tvolap_process_signal_static(plan.h, _p(x), N, N, _p(sa), None, None, nb, _p(y), N, N)
     assert st == -5                                     # TVOLAP_ERR_CAPACITY
+    plan.close()
+
+
+def test_static_scratch_refuses_another_current_device():
+    """The plan's device (its stream's) must be current: with another device
+    current the call is refused (TVOLAP_ERR_ARG). Needs two GPUs."""
+    dev = _dev()
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs a second GPU")
+    from paper_2310_00319_gb300 import Plan, _lib
+    lib = _lib.load()
+    wl = W.random_case(505, L=64, ir_len=300, N=2000, n_in=1, n_out=1, n_slots=2)
+    plan = Plan(64, wl.M, n_in=1, n_out=1, n_slots=2, device=dev)
+    plan.load_bank(0, torch.from_numpy(wl.irs).to(dev))
+    x, sa, sb, sal = _inputs(wl, dev)
+    y = torch.zeros((1, wl.out_len), device=dev)
+    with torch.cuda.device(1):
+        st = _static(lib, plan, wl, x, sa, sb, sal, y)
+    assert st == -1                                     # TVOLAP_ERR_ARG
     plan.close()
