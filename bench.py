@@ -377,6 +377,12 @@ def run_ours(args):
         out["e2e"] = run_e2e(args, plan, wl, dev, stream)
         out["vs_per_source"] = run_per_source(args, wl, dev, stream, ms_per_step)
         out["stream"] = run_stream(args, wl, dev, stream)
+        # the same streaming ticks at 4x the channels: the tick reads about
+        # 296 MB of delay line and filter spectra, more than the L2 holds
+        from synth import workloads as W
+        wl4 = W.plain_at_scale(n_ch=4 * args.channels, N=650 * wl.L, ir_len=args.ir_len)
+        out["stream_beyond_l2"] = run_stream(args, wl4, dev, stream)
+        del wl4
     if rank == 0 and not args.skip_extras and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(args, wl, budget_s=args.cpu_seconds,
                                            y_channel0=y[0].cpu().numpy())
@@ -521,20 +527,62 @@ def run_stream(args, wl, dev, stream, ticks=600, warm=50):
         p.process_block(blocks[t], out, sa[warm], sb[warm], sal[warm])
         fixed[i][1].record(stream)
     torch.cuda.synchronize(dev)
+    # the three stages timed on their own (events around each; the next tick
+    # waits for the previous one's events)
+    from paper_2310_00319_gb300.tvolap import OPT_STAGE_TIMING
+    p.set_option(OPT_STAGE_TIMING, 1)
+    for i in range(ticks):
+        t = warm + i
+        p.process_block(blocks[t], out, sa[t], sb[t], sal[t])
+    st_ms, n_timed = p.stage_times()
+    p.set_option(OPT_STAGE_TIMING, 0)
     p.check()
     ms = np.array([a.elapsed_time(b) for a, b in evs])
     ms_fixed = np.array([a.elapsed_time(b) for a, b in fixed])
     p.close()
     deadline_ms = L / 48000 * 1e3
     bpt = costmodel.stream_mac_bytes_per_tick(wl.n_out, 2 * L, wl.M, 2)
-    return {"ticks": ticks, "tick_ms_p50": round(float(np.percentile(ms, 50)), 4),
+    mac_ms = st_ms[1] / n_timed
+    peaks, _ = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    mac_gbs = bpt / (mac_ms * 1e-3) / 1e9
+    return {"ticks": ticks, "channels": wl.n_out,
+            "tick_ms_p50": round(float(np.percentile(ms, 50)), 4),
             "tick_ms_p99": round(float(np.percentile(ms, 99)), 4),
             "deadline_ms": round(deadline_ms, 4),
             "channel_samples_per_s": round(wl.n_out * L / (ms.mean() * 1e-3), 1),
             "mac_bytes_per_tick": bpt,
             "logical_gbs_per_tick": round(bpt / (ms.mean() * 1e-3) / 1e9, 1),
+            "stages_ms_per_tick": {"forward": round(st_ms[0] / n_timed, 5),
+                                   "mac": round(mac_ms, 5),
+                                   "inverse": round(st_ms[2] / n_timed, 5)},
+            "mac_roofline": {"bound": "hbm", "achieved": round(mac_gbs, 1), "peak": hbm,
+                             "unit": "GB/s", "frac": round(mac_gbs / hbm, 4),
+                             "kernel": "k_mac_stream (delay line + 2 filter spectra read, "
+                                       "Y written; algorithmic bytes)",
+                             "working_set_mb": round(bpt / 1e6, 1),
+                             "l2_mb": round(torch.cuda.get_device_properties(dev).L2_cache_size
+                                            / 1e6, 1)},
             "constant_load": {"switching_every_block_ms_mean": round(float(ms.mean()), 5),
                               "fixed_selection_ms_mean": round(float(ms_fixed.mean()), 5)}}
+
+
+def run_stream_only(args):
+    """Streaming ticks alone (process_block, one hop per call) on
+    ``--channels`` channels of the default workload's shape (L = 256, M = 94,
+    eight stored responses per channel, a new mixed filter every block)."""
+    import torch
+    from synth import workloads as W
+    dev = torch.device("cuda", 0)
+    ticks = max(args.steps, 10)
+    wl = W.plain_at_scale(n_ch=args.channels, N=(ticks + 50) * 256, ir_len=args.ir_len)
+    r = run_stream(args, wl, dev, torch.cuda.current_stream(dev), ticks=ticks)
+    return {"metric": "channel-samples/s (streaming ticks)",
+            "value": r["channel_samples_per_s"], "unit": UNIT, "n_gpus": 1, "steps": ticks,
+            "warmup": 50, "ms_per_step": r["tick_ms_p50"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"plain_at_scale_streaming_{args.channels}ch_L256_M94"},
+            "roofline": dict(r["mac_roofline"], traffic=None), "stream": r}
 
 
 # --------------------------------------------------------------------------- adjoint
@@ -1491,7 +1539,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain_at_scale",
                     choices=["plain_at_scale", "adjoint", "batched", "serve", "mixdown",
-                             "nonuniform"])
+                             "nonuniform", "stream"])
     ap.add_argument("--channels", type=int, default=64)
     ap.add_argument("--samples", type=int, default=480000)
     ap.add_argument("--ir-len", type=int, default=48000,
@@ -1531,6 +1579,8 @@ def main():
         out = run_mixdown(args)
     elif args.workload == "nonuniform":
         out = run_nonuniform(args)
+    elif args.workload == "stream":
+        out = run_stream_only(args)
     else:
         out = run_ours(args)
         if (out is not None and _dist()[0] == 1 and not args.skip_extras

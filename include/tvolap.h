@@ -486,11 +486,23 @@ typedef enum tvolap_option {
        5 = as 0 with up to four filters per group. 0, 1, 3 and 4 give
        identical results, and so do 2 and 5; 2 and 5 differ from the others
        only in the rounding of blocks whose group holds four filters. */
-    TVOLAP_OPT_MAC_STAGING = 1
+    TVOLAP_OPT_MAC_STAGING = 1,
+    /* 1: tvolap_process_block records CUDA events around its three stages
+       (forward transform, multiply-accumulate, inverse + overlap-add) and
+       each call first waits for the previous call's events, adding their
+       times up for tvolap_stage_times; 0 (default): off. Setting it (either
+       value) clears the sums. */
+    TVOLAP_OPT_STAGE_TIMING = 2
 } tvolap_option;
 
 /* Set a plan option (takes effect for the following calls). */
 TVOLAP_API int tvolap_set_option(tvolap_t h, int option, int value);
+
+/* Stage times of the streaming ticks timed since TVOLAP_OPT_STAGE_TIMING was
+   set: stage_ms[0..2] = forward transform, multiply-accumulate (Eq. 7),
+   inverse transform + overlap-add, in milliseconds summed over *ticks ticks
+   (may be NULL). Waits for the last timed tick. */
+TVOLAP_API int tvolap_stage_times(tvolap_t h, double *stage_ms, int64_t *ticks);
 
 /*
  * Synchronise the stream and report deferred device-side errors: returns

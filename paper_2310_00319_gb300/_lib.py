@@ -47,6 +47,7 @@ SIGNATURES = {
     "tvolap_bank_spectra": (c_int, [c_void_p, c_int, c_void_p]),
     "tvolap_check": (c_int, [c_void_p]),
     "tvolap_set_option": (c_int, [c_void_p, c_int, c_int]),
+    "tvolap_stage_times": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_double), P_int64]),
     "tvolap_set_mix": (c_int, [c_void_p, c_int, c_void_p]),
     "tvolap_nu_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int, c_int,
                                  c_int, c_void_p,

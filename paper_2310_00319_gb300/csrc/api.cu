@@ -44,7 +44,38 @@ void free_plan(tvolap_plan *h)
                     h->mix_off, h->mix_members, h->mix_ola, h->Ymix_stream};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (cudaEvent_t e : h->tev)
+        if (e) cudaEventDestroy(e);
     delete h;
+}
+
+// Adds the stage times of the last timed tick (waits for it).
+cudaError_t timing_collect(tvolap_plan *h)
+{
+    if (!h->tev_pending) return cudaSuccess;
+    cudaError_t e = cudaEventSynchronize(h->tev[3]);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, h->tev[i], h->tev[i + 1]);
+        h->stage_ms[i] += ms;
+    }
+    h->tev_pending = 0;
+    if (e == cudaSuccess) h->timed_ticks += 1;
+    return e;
+}
+
+// Event i of a timed tick (i = 0 before the forward transform, 1 before the
+// multiply-accumulate, 2 before the inverse, 3 after it); nothing when off.
+cudaError_t timing_mark(tvolap_plan *h, int i)
+{
+    if (!h->timing) return cudaSuccess;
+    if (i == 0) {
+        const cudaError_t e = timing_collect(h);
+        if (e != cudaSuccess) return e;
+    }
+    const cudaError_t e = cudaEventRecord(h->tev[i], h->stream);
+    if (i == 3 && e == cudaSuccess) h->tev_pending = 1;
+    return e;
 }
 
 int64_t blocks_for(const tvolap_plan *h, int64_t out_len)
@@ -339,9 +370,13 @@ int tvolap_process_block(tvolap_t h, const float *in_dev, float *out_dev, const 
     if (!h) return TVOLAP_ERR_STATE;
     if (!in_dev || !out_dev) return TVOLAP_ERR_ARG;
     if (!sel_a && (sel_b || sel_alpha)) return TVOLAP_ERR_ARG;
-    cudaError_t e = launch_forward_stream(h, in_dev);
+    cudaError_t e = timing_mark(h, 0);
+    if (e == cudaSuccess) e = launch_forward_stream(h, in_dev);
+    if (e == cudaSuccess) e = timing_mark(h, 1);
     if (e == cudaSuccess) e = launch_mac_stream(h, sel_a, sel_b, sel_alpha);
+    if (e == cudaSuccess) e = timing_mark(h, 2);
     if (e == cudaSuccess) e = launch_inverse_stream(h, out_dev);
+    if (e == cudaSuccess) e = timing_mark(h, 3);
     if (e != cudaSuccess) return cuda_status(e);
     h->tick += 1;
     return TVOLAP_OK;
@@ -728,7 +763,29 @@ int tvolap_set_option(tvolap_t h, int option, int value)
         h->mac_variant = value;
         return TVOLAP_OK;
     }
+    if (option == TVOLAP_OPT_STAGE_TIMING) {
+        if (value != 0 && value != 1) return TVOLAP_ERR_ARG;
+        cudaError_t e = timing_collect(h);
+        for (int i = 0; i < 4 && e == cudaSuccess && value; ++i)
+            if (!h->tev[i]) e = cudaEventCreate(&h->tev[i]);
+        if (e != cudaSuccess) return cuda_status(e);
+        h->timing = value;
+        h->stage_ms[0] = h->stage_ms[1] = h->stage_ms[2] = 0.0;
+        h->timed_ticks = 0;
+        return TVOLAP_OK;
+    }
     return TVOLAP_ERR_ARG;
+}
+
+int tvolap_stage_times(tvolap_t h, double *stage_ms, int64_t *ticks)
+{
+    if (!h) return TVOLAP_ERR_STATE;
+    if (!stage_ms) return TVOLAP_ERR_ARG;
+    const cudaError_t e = timing_collect(h);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int i = 0; i < 3; ++i) stage_ms[i] = h->stage_ms[i];
+    if (ticks) *ticks = h->timed_ticks;
+    return TVOLAP_OK;
 }
 
 }  // extern "C"

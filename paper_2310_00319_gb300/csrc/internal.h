@@ -55,6 +55,15 @@ struct tvolap_plan {
     int32_t *mix_members;         // [n_out]
     float *mix_ola;               // [n_mix][3L] pending overlap-add sums (streaming)
     float2 *Ymix_stream;          // [n_mix][P] this tick's mixed spectra
+
+    // stage timing of streaming ticks (TVOLAP_OPT_STAGE_TIMING): events around
+    // the forward transform, the multiply-accumulate and the inverse of the
+    // last tick, and the times of the earlier timed ticks
+    int timing;
+    cudaEvent_t tev[4];
+    int tev_pending;
+    double stage_ms[3];
+    int64_t timed_ticks;
 };
 
 namespace tvolap {

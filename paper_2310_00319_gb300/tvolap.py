@@ -48,6 +48,9 @@ def n_blocks_for(out_len: int, L: int) -> int:
     return 0 if out_len <= 0 else (out_len - 1) // L + 2
 
 
+OPT_MAC_STAGING, OPT_STAGE_TIMING = 1, 2
+
+
 class Plan:
     """One TVOLAP plan: hop L, M partitions, n_in inputs, n_out outputs,
     n_slots stored filters. Calls run on ``stream`` (default: the current
@@ -115,8 +118,17 @@ class Plan:
         """TVOLAP_OPT_MAC_STAGING (1): 0 = persistent TMA groups (default),
         1 = cp.async, 2 = TMA groups of up to four filters, 3 = one TMA group
         per CTA, 4 = as 3 with two bins per thread, 5 = as 0 with up to four
-        filters per group."""
+        filters per group. TVOLAP_OPT_STAGE_TIMING (2): 1 = time the three
+        stages of process_block (see stage_times)."""
         self._call("tvolap_set_option", int(option), int(value))
+
+    def stage_times(self):
+        """(forward, multiply-accumulate, inverse) milliseconds summed over the
+        ticks timed since TVOLAP_OPT_STAGE_TIMING was set, and that tick count."""
+        ms = (ctypes.c_double * 3)()
+        n = ctypes.c_int64()
+        self._call("tvolap_stage_times", ms, ctypes.byref(n))
+        return list(ms), n.value
 
     def check(self):
         """Synchronise and raise if a kernel met an invalid slot index."""

@@ -318,6 +318,35 @@ def test_streaming_equals_offline_delayed_by_L(L, ir_len, n_in, n_out, routing):
     _assert_close(y[:, L:L + N], ref[:, :min(N, y.shape[1] - L)], "stream")
 
 
+def test_stage_timing_changes_no_output():
+    """TVOLAP_OPT_STAGE_TIMING: the three stages of every tick are timed (all
+    times positive, one count per tick) and the outputs are those of the
+    untimed ticks, bit for bit."""
+    dev = _dev()
+    from paper_2310_00319_gb300.tvolap import OPT_STAGE_TIMING
+    L, N = 64, 64 * 25
+    wl = W.random_case(210, L=L, ir_len=700, N=N, n_in=2, n_out=3, n_slots=3, out_len=N,
+                       out_to_in=[0, 1, 1])
+    xd = _t(wl.x, dev)
+    sa, sb, sal = _t(wl.sched_a.T.copy(), dev), _t(wl.sched_b.T.copy(), dev), \
+        _t(wl.sched_alpha.T.copy(), dev)
+    runs = []
+    for timing in (0, 1):
+        plan = _plan(wl, dev)
+        plan.set_option(OPT_STAGE_TIMING, timing)
+        outs = [plan.process_block(xd[:, t * L:(t + 1) * L].contiguous(), None, sa[t], sb[t],
+                                   sal[t]).clone() for t in range(N // L)]
+        ms, n = plan.stage_times()
+        if timing:
+            assert n == N // L and all(v > 0 for v in ms), (ms, n)
+        else:
+            assert n == 0 and ms == [0.0, 0.0, 0.0]
+        plan.check()
+        runs.append(torch.cat(outs, dim=1).cpu().numpy())
+        plan.close()
+    np.testing.assert_array_equal(runs[0], runs[1])
+
+
 def test_streaming_set_filter_and_select():
     """set_filter exchanges all partitions at once; select mixes two slots."""
     dev = _dev()
