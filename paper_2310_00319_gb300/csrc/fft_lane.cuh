@@ -1,0 +1,343 @@
+// Transforms with sixteen values per thread (sm_103a), for the offline
+// forward transform, the partition bank and the offline inverse with its
+// overlap-add.
+//
+// The arithmetic is that of fft_core.cuh: a real block of 4L samples whose
+// upper half is zero (Eqs. 3-4) goes through a P = 2L point complex Stockham
+// FFT of z(r) = x(2r) + i x(2r+1) pre-rotated by e^{-i pi r/P}, radix 8 while
+// three or more bits remain, then one radix-4 or radix-2 stage, and a split
+// step gives the P half-bin spectrum values; the inverse runs it backwards.
+// What differs is the work split: T = P/16 threads run one transform (one
+// warp at P = 512), each thread holding sixteen values, and the butterflies a
+// thread runs are chosen so that
+//   * the first stage runs on the registers the inputs were loaded into;
+//   * in the forward transform the last stage leaves Z(k) and Z(P-1-k) in the
+//     same thread, so the split step needs no shared-memory pass and each
+//     thread stores its spectrum values straight to memory;
+//   * in the inverse the merge step (the split's inverse) runs on the values
+//     a thread loads, and the last stage leaves each thread the output pairs
+//     r = j + T q (q < 16), a set that a hop of L samples (P/4 pairs) maps
+//     onto itself, so the overlap-add of consecutive blocks runs on registers.
+// Twiddles come from one table load per butterfly (the stage's first row)
+// raised to the needed powers; rotations and split factors from one table
+// load times the constants e^{-i pi k/16}. Threads of a transform wait for
+// each other with __syncwarp when the transform fits in a warp, else on a
+// named barrier of its T threads.
+#pragma once
+
+#include "fft_core.cuh"
+
+namespace tvolap {
+
+template <int P>
+struct Lane {
+    static_assert(P >= 32 && P <= 2048, "transform size");
+    static constexpr int T = P / 16;                 // threads per transform
+    static constexpr int THREADS = 256;
+    static constexpr int F = THREADS / T;            // transforms per CTA
+    static constexpr int S = 2 * T;                  // first-stage butterflies (P / 8)
+};
+
+// e^{-i pi k / 16}, k < 16
+__device__ __forceinline__ float2 c16(int k)
+{
+    constexpr float re[16] = {1.0f, 0.98078525066375732f, 0.92387950420379639f, 0.83146959543228149f,
+                              0.70710676908493042f, 0.55557024478912354f, 0.38268342614173889f,
+                              0.19509032368659973f, 0.0f, -0.19509032368659973f,
+                              -0.38268342614173889f, -0.55557024478912354f, -0.70710676908493042f,
+                              -0.83146959543228149f, -0.92387950420379639f, -0.98078525066375732f};
+    constexpr float im[16] = {-0.0f, -0.19509032368659973f, -0.38268342614173889f,
+                              -0.55557024478912354f, -0.70710676908493042f, -0.83146959543228149f,
+                              -0.92387950420379639f, -0.98078525066375732f, -1.0f,
+                              -0.98078525066375732f, -0.92387950420379639f, -0.83146959543228149f,
+                              -0.70710676908493042f, -0.55557024478912354f, -0.38268342614173889f,
+                              -0.19509032368659973f};
+    return make_float2(re[k], im[k]);
+}
+
+// Dynamic shared memory of a lane kernel: one P-value buffer per transform.
+template <int LG>
+inline size_t smem_lane()
+{
+    return (size_t)Lane<(1 << LG)>::F * (1 << LG) * sizeof(float2);
+}
+
+// dft8 (forward) of v[0..3] with v[4..7] zero: the first radix-2 layer of the
+// even/odd split reduces to copies. Same values as dft8 on zero-padded inputs
+// up to the sign of zero.
+__device__ __forceinline__ void dft8_half(float2 *v)
+{
+    const float h = 0.70710678118654752440f;
+    // even half e = DFT4(v0, v2, 0, 0), odd half o = DFT4(v1, v3, 0, 0)
+    const float2 e0 = cadd(v[0], v[2]), e2 = csub(v[0], v[2]);
+    const float2 e1 = make_float2(v[0].x + v[2].y, v[0].y - v[2].x);   // v0 - i v2
+    const float2 e3 = make_float2(v[0].x - v[2].y, v[0].y + v[2].x);   // v0 + i v2
+    float2 o0 = cadd(v[1], v[3]), o2 = csub(v[1], v[3]);
+    float2 o1 = make_float2(v[1].x + v[3].y, v[1].y - v[3].x);
+    float2 o3 = make_float2(v[1].x - v[3].y, v[1].y + v[3].x);
+    o1 = cmul(o1, make_float2(h, -h));
+    o2 = make_float2(o2.y, -o2.x);                                      // -i o2
+    o3 = cmul(o3, make_float2(-h, -h));
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3);
+    v[7] = csub(e3, o3);
+}
+
+// Wait for the T threads of transform f.
+template <int T>
+__device__ __forceinline__ void lane_sync(int f)
+{
+    if constexpr (T <= 32) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(f + 1), "r"(T) : "memory");
+    }
+}
+
+// Radix of the stage at Ns (as fft_core.cuh: 8 while P/Ns >= 8).
+template <int P, int Ns>
+struct LStage {
+    static constexpr int R = stage_radix(P, Ns);
+    static constexpr bool LAST = Ns * R == P;
+    static constexpr int NB = 16 / R;                // butterflies per thread
+};
+
+// w[r] = w1^r, r < R (w[0] = 1)
+template <int R>
+__device__ __forceinline__ void powers(float2 w1, float2 (&w)[R])
+{
+    w[0] = make_float2(1.f, 0.f);
+    if constexpr (R > 1) w[1] = w1;
+    if constexpr (R > 2) w[2] = cmul(w1, w1);
+    if constexpr (R > 3) w[3] = cmul(w[2], w1);
+    if constexpr (R > 4) {
+        w[4] = cmul(w[2], w[2]);
+        w[5] = cmul(w[4], w1);
+        w[6] = cmul(w[4], w[2]);
+        w[7] = cmul(w[4], w[3]);
+    }
+}
+
+// Butterfly b of stage (Ns, R): its R inputs from the swizzled buffer, rotated
+// by the stage's twiddles, transformed.
+template <int P, int Ns, bool INV>
+__device__ __forceinline__ void lane_bfly(const float2 *buf, int b, const float2 *__restrict__ tw,
+                                          float2 (&v)[LStage<P, Ns>::R])
+{
+    constexpr int R = LStage<P, Ns>::R, stride = P / R;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = buf[swz(b + r * stride)];
+    if constexpr (Ns > 1) {
+        float2 w[R];
+        powers<R>(__ldg(tw + tw_offset(P, Ns) + (b & (Ns - 1))), w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = INV ? cmulc(v[r], w[r]) : cmul(v[r], w[r]);
+    }
+    dftR<R, INV>(v);
+}
+
+template <int P, int Ns>
+__device__ __forceinline__ void lane_store(float2 *buf, int b, const float2 (&v)[LStage<P, Ns>::R])
+{
+    constexpr int R = LStage<P, Ns>::R;
+    const int base = (b / Ns) * Ns * R + (b & (Ns - 1));
+#pragma unroll
+    for (int s = 0; s < R; ++s) buf[swz(base + s * Ns)] = v[s];
+}
+
+// Middle stages (neither the first nor the last): butterflies b = j + T u.
+// Enters with the stage's input in buf (synchronised) and leaves with its
+// output there (synchronised).
+template <int P, int Ns, bool INV>
+__device__ __forceinline__ void lane_middle(float2 *buf, int j, int f, const float2 *__restrict__ tw)
+{
+    if constexpr (!LStage<P, Ns>::LAST) {
+        constexpr int R = LStage<P, Ns>::R, NB = LStage<P, Ns>::NB, T = Lane<P>::T;
+        float2 v[NB][R];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) lane_bfly<P, Ns, INV>(buf, j + T * u, tw, v[u]);
+        lane_sync<T>(f);
+#pragma unroll
+        for (int u = 0; u < NB; ++u) lane_store<P, Ns>(buf, j + T * u, v[u]);
+        lane_sync<T>(f);
+        lane_middle<P, Ns * R, INV>(buf, j, f, tw);
+    }
+}
+
+// Ns of the last stage.
+template <int P, int Ns = 1>
+__host__ __device__ constexpr int last_ns()
+{
+    if constexpr (LStage<P, Ns>::LAST) {
+        return Ns;
+    } else {
+        return last_ns<P, Ns * LStage<P, Ns>::R>();
+    }
+}
+
+// The windowed input pair n (samples 2n, 2n+1 of the block starting at
+// sample `start`, Eq. 1 with the half-amplitude Hann window): 8-byte loads
+// where the row allows, zero outside [0, N).
+struct SignalPairs {
+    const float *xc;
+    const float *win;
+    int64_t start, N;
+    bool pairs, inside;   // 8-byte aligned row; and every pair of the block in [0, N)
+    __device__ __forceinline__ void set_range(int L)
+    {
+        inside = pairs && start >= 0 && start + 2 * (int64_t)L <= N;
+    }
+    __device__ __forceinline__ float2 operator()(int n) const
+    {
+        const int64_t i0 = start + 2 * n;
+        const float2 w = __ldg(reinterpret_cast<const float2 *>(win) + n);
+        float2 v;
+        if (inside) {                                  // the whole block lies in [0, N)
+            v = __ldg(reinterpret_cast<const float2 *>(xc + i0));
+        } else if (pairs && i0 >= 0 && i0 + 1 < N) {
+            v = __ldg(reinterpret_cast<const float2 *>(xc + i0));
+        } else {
+            v.x = (i0 >= 0 && i0 < N) ? __ldg(xc + i0) : 0.f;
+            v.y = (i0 + 1 >= 0 && i0 + 1 < N) ? __ldg(xc + i0 + 1) : 0.f;
+        }
+        return make_float2(v.x * w.x, v.y * w.y);
+    }
+};
+
+// The forward transform of one block. src(n) gives the windowed pair
+// (x(2n), x(2n+1)) for n < P/2 (the upper half is the zero padding); st(k, v)
+// receives X(k), each k < P exactly once per thread set. The buffer holds P
+// values (swizzled); on entry it may still be read by this transform's
+// threads for an earlier transform (the first barrier covers that).
+template <int P, class Src, class Store>
+__device__ __forceinline__ void forward_lane(float2 *buf, int j, int f, bool active, Src src,
+                                             const float2 *__restrict__ rot,
+                                             const float2 *__restrict__ post,
+                                             const float2 *__restrict__ tw, Store st)
+{
+    constexpr int T = Lane<P>::T, S = Lane<P>::S;
+    // first stage (Ns = 1, radix 8, stride S): butterflies j and S - 1 - j run
+    // on the inputs this thread loads; inputs r >= 4 are the zero padding
+    const int bb[2] = {j, S - 1 - j};
+    float2 v[2][8];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const float2 r0 = active ? __ldg(rot + bb[u]) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            v[u][r] = active ? cmul(src(bb[u] + S * r), cmul(r0, c16(2 * r))) : make_float2(0.f, 0.f);
+        dft8_half(v[u]);
+    }
+    lane_sync<T>(f);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) lane_store<P, 1>(buf, bb[u], v[u]);
+    lane_sync<T>(f);
+    lane_middle<P, 8, false>(buf, j, f, tw);
+    // last stage: butterflies b and Ns - 1 - b hold Z(k) and Z(P - 1 - k)
+    constexpr int NS = last_ns<P>(), R = LStage<P, NS>::R, H = LStage<P, NS>::NB / 2;
+    float2 lo[H][R], hi[H][R];
+#pragma unroll
+    for (int u = 0; u < H; ++u) {
+        lane_bfly<P, NS, false>(buf, j + T * u, tw, lo[u]);
+        lane_bfly<P, NS, false>(buf, NS - 1 - j - T * u, tw, hi[u]);
+    }
+    // split: for k < P/2 in butterfly b (s < R/2), the partner P - 1 - k is
+    // output R - 1 - s of butterfly NS - 1 - b
+    auto split = [&](float2 zk, float2 zkk, float2 w, int k) {
+        const float2 E = make_float2(0.5f * (zk.x + zkk.x), 0.5f * (zk.y - zkk.y));
+        const float2 d = make_float2(0.5f * (zk.x - zkk.x), 0.5f * (zk.y + zkk.y));
+        const float2 O = make_float2(d.y, -d.x);           // (zk - conj zkk) / 2i
+        const float2 t = cmul(w, O);
+        st(k, cadd(E, t));
+        st(P - 1 - k, cconj(csub(E, t)));
+    };
+#pragma unroll
+    for (int u = 0; u < H; ++u) {
+        const int b = j + T * u, bh = NS - 1 - b;
+        const float2 pb = __ldg(post + b), ph = __ldg(post + bh);
+#pragma unroll
+        for (int s = 0; s < R / 2; ++s) {
+            // W^{k + 1/2} for k = b + s NS: post(b) e^{-i pi s / R}
+            split(lo[u][s], hi[u][R - 1 - s], cmul(pb, c16(16 / R * s)), b + s * NS);
+            split(hi[u][s], lo[u][R - 1 - s], cmul(ph, c16(16 / R * s)), bh + s * NS);
+        }
+    }
+}
+
+// The inverse transform of one block, its rotation undone and scaled by 1/P:
+// ld(k) gives Y(k); emit(q, v) receives v = (y(2r), y(2r+1)) for the pairs
+// r = j + T q, q < 16, with q / 4 increasing for each q mod 4 (the order the
+// overlap-add needs). Buffer as forward_lane.
+template <int P, class Load, class Emit>
+__device__ __forceinline__ void inverse_lane(float2 *buf, int j, int f, Load ld,
+                                             const float2 *__restrict__ rot,
+                                             const float2 *__restrict__ post,
+                                             const float2 *__restrict__ tw, Emit emit)
+{
+    constexpr int T = Lane<P>::T, S = Lane<P>::S;
+    // merge: butterflies j and S - 1 - j of the first stage hold both members
+    // of every pair (n, P - 1 - n) of their inputs
+    const int bb[2] = {j, S - 1 - j};
+    float2 v[2][8];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[u][r] = ld(bb[u] + S * r);
+    const float2 pb[2] = {__ldg(post + bb[0]), __ldg(post + bb[1])};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            // n = bb[u] + S r < P/2, partner P - 1 - n = input 7 - r of the other butterfly
+            const float2 yk = v[u][r], ykk = v[1 - u][7 - r];
+            const float2 E = make_float2(0.5f * (yk.x + ykk.x), 0.5f * (yk.y - ykk.y));
+            const float2 d = make_float2(0.5f * (yk.x - ykk.x), 0.5f * (yk.y + ykk.y));
+            const float2 O = cmulc(d, cmul(pb[u], c16(2 * r)));   // post(n) = post(b) e^{-i pi r/8}
+            v[u][r] = cadd(E, make_float2(-O.y, O.x));               // E + i O
+            v[1 - u][7 - r] = cadd(cconj(E), make_float2(O.y, O.x)); // conj E + i conj O
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) dft8<true>(v[u]);
+    lane_sync<T>(f);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) lane_store<P, 1>(buf, bb[u], v[u]);
+    lane_sync<T>(f);
+    lane_middle<P, 8, true>(buf, j, f, tw);
+    // last stage: butterflies b = j + T u give the pairs r = b + s NS = j + T q,
+    // q = u + NB s
+    constexpr int NS = last_ns<P>(), R = LStage<P, NS>::R, NB = LStage<P, NS>::NB;
+    const float inv_p = 1.0f / (float)P;
+    const float2 r0 = __ldg(rot + j);
+    // y(2r) + i y(2r+1) = Z(r) e^{+i pi r/P} / P, rot(r) = rot(j) e^{-i pi q/16}
+    auto out = [&](int q, float2 z) { return cscale(cmulc(z, cmul(r0, c16(q))), inv_p); };
+    if constexpr (R >= 4) {
+        // q = u + NB s: for a given q mod 4 (fixed u, NB | 4 or NB = 2), q / 4 grows with s
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            float2 w[R];
+            lane_bfly<P, NS, true>(buf, j + T * u, tw, w);
+#pragma unroll
+            for (int s = 0; s < R; ++s) emit(u + NB * s, out(u + NB * s, w[s]));
+        }
+    } else {
+        // radix 2: a butterfly gives hops q / 4 and q / 4 + 2; emit in q order
+        float2 o[16];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            float2 w[R];
+            lane_bfly<P, NS, true>(buf, j + T * u, tw, w);
+#pragma unroll
+            for (int s = 0; s < R; ++s) o[u + NB * s] = out(u + NB * s, w[s]);
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) emit(q, o[q]);
+    }
+}
+
+}  // namespace tvolap

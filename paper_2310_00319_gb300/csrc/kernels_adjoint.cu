@@ -16,6 +16,7 @@
 // A thread owns two bins (16-byte loads and stores) of one block; the partition
 // loop is unrolled 8 deep to keep enough loads in flight.
 #include "fft_block.cuh"
+#include "fft_lane.cuh"
 #include "internal.h"
 
 namespace tvolap {
@@ -124,12 +125,12 @@ k_adjoint_mac(const float4 *__restrict__ G, int64_t g_first, int g_count,
 
 // The adjoint of k_adjoint_mac with the input spectra recomputed in place: a
 // CTA transforms F consecutive blocks q of its output's input channel (Eqs. 1,
-// 3, 5, the same arithmetic as the forward transform kernel), leaves their
-// spectra in the FFT buffer not holding the result, then runs the adjoint of
-// Eq. 7 for those blocks exactly as k_adjoint_mac does. No input spectra are
-// stored anywhere. grid: x = ceil(q_count / F), y = outputs.
+// 3, 5, the same arithmetic as the forward transform kernel), keeps their
+// spectra in shared memory, then runs the adjoint of Eq. 7 for those blocks
+// exactly as k_adjoint_mac does. No input spectra are stored anywhere.
+// grid: x = ceil(q_count / F), y = outputs.
 template <int LG>
-__global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
+__global__ void __launch_bounds__(Lane<(1 << LG)>::THREADS)
 k_adjoint_mac_x(const float4 *__restrict__ G, int64_t g_first, int g_count,
                 const float *__restrict__ x, int64_t N, int64_t x_stride, int L,
                 const float *__restrict__ win, const float2 *__restrict__ rot,
@@ -138,45 +139,28 @@ k_adjoint_mac_x(const float4 *__restrict__ G, int64_t g_first, int g_count,
                 int q_count, const int32_t *__restrict__ out_to_in, float4 *__restrict__ dP,
                 float4 *__restrict__ dX, int64_t dx_rows)
 {
-    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F, P4 = P / 2;
+    constexpr int P = 1 << LG, T = Lane<P>::T, F = Lane<P>::F, P4 = P / 2;
     extern __shared__ float2 sm[];
     const int f = threadIdx.x / T, j = threadIdx.x % T;
-    float2 *A = sm + f * P, *B = sm + (F + f) * P;
+    float2 *buf = sm + f * P;                          // the transform's working buffer
     const int o = blockIdx.y;
     const int c = out_to_in[o];
     const int64_t q0 = q_first + (int64_t)blockIdx.x * F;
     const int64_t q_end = q_first + q_count;
-    // forward transform of block q = q0 + f into the buffer the FFT result is not in
-    bool z_in_a;
+    // forward transform of block q = q0 + f, as the forward transform kernel
+    // computes it, into the spectra area (F blocks after the buffers)
     {
         const int64_t q = q0 + f;
         const bool active = q < q_end;
-        const int64_t start = (q - 1) * (int64_t)L;     // block l = q - 1 starts at l*L
-        const float *xc = x + (int64_t)c * x_stride;
-        const bool pairs = (reinterpret_cast<uintptr_t>(xc) & 7) == 0;
-        auto src = [&](int n) {      // as the forward transform kernel
-            const int64_t i0 = start + n;
-            const float2 w = __ldg(reinterpret_cast<const float2 *>(win) + (n >> 1));
-            float2 v;
-            if (pairs && i0 >= 0 && i0 + 1 < N) {
-                v = __ldg(reinterpret_cast<const float2 *>(xc + i0));
-            } else {
-                v.x = (i0 >= 0 && i0 < N) ? __ldg(xc + i0) : 0.f;
-                v.y = (i0 + 1 >= 0 && i0 + 1 < N) ? __ldg(xc + i0 + 1) : 0.f;
-            }
-            return make_float2(v.x * w.x, v.y * w.y);
-        };
-        // the window, pre-rotation and FFT of forward_block (upper half zero)
-        float2 z[8];
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const int r = j + s * T;
-            z[s] = (s < 4 && active) ? cmul(src(2 * r), __ldg(rot + r)) : make_float2(0.f, 0.f);
-        }
-        float2 *Z = fft_complex_regs<P, false>(z, A, B, j, tw);
-        z_in_a = (Z == A);                               // the same for every transform
-        float2 *Xs = z_in_a ? B : A;
-        split_forward<P>(Z, j, post, [&](int k, float2 v) { Xs[k] = v; });
+        SignalPairs src;
+        src.xc = x + (int64_t)c * x_stride;
+        src.win = win;
+        src.start = (q - 1) * (int64_t)L;               // block l = q - 1 starts at l*L
+        src.N = N;
+        src.pairs = (reinterpret_cast<uintptr_t>(src.xc) & 7) == 0;
+        src.set_range(L);
+        float2 *Xs = sm + (F + f) * P;
+        forward_lane<P>(buf, j, f, active, src, rot, post, tw, [&](int k, float2 v) { Xs[k] = v; });
     }
     __syncthreads();
     const int64_t MP4 = (int64_t)M * P4;
@@ -186,8 +170,7 @@ k_adjoint_mac_x(const float4 *__restrict__ G, int64_t g_first, int g_count,
         const int ff = it / P4, k = it % P4;
         const int64_t q = q0 + ff;
         if (q >= q_end) continue;
-        const float4 xq = reinterpret_cast<const float4 *>(z_in_a ? sm + (F + ff) * P
-                                                                  : sm + ff * P)[k];
+        const float4 xq = reinterpret_cast<const float4 *>(sm + (F + ff) * P)[k];
         const float4 *Gq = G + ((int64_t)o * g_count + (q - g_first)) * P4 + k;
         const float4 *Pq = Pm + (int64_t)o * p_blocks * MP4 + q * MP4 + k;
         float4 *dPq = dPo + q * MP4 + k;
@@ -256,11 +239,11 @@ cudaError_t launch_adjoint_mac_x(tvolap_plan *h, const float2 *G, int64_t g_firs
     }
     TVOLAP_DISPATCH(h->lgP, {
         constexpr int P = 1 << LG;
-        const size_t sm = smem_fft<LG>();
+        const size_t sm = 2 * smem_lane<LG>();          // buffers, then the blocks' spectra
         cudaError_t e = set_smem(k_adjoint_mac_x<LG>, sm);
         if (e != cudaSuccess) return e;
-        dim3 grid((unsigned)((q_count + Geo<P>::F - 1) / Geo<P>::F), (unsigned)h->n_out);
-        k_adjoint_mac_x<LG><<<grid, Geo<P>::THREADS, sm, h->stream>>>(
+        dim3 grid((unsigned)((q_count + Lane<P>::F - 1) / Lane<P>::F), (unsigned)h->n_out);
+        k_adjoint_mac_x<LG><<<grid, Lane<P>::THREADS, sm, h->stream>>>(
             reinterpret_cast<const float4 *>(G), g_first, g_count, x, N, x_stride, h->L, h->win,
             h->rot, h->post, h->tw, reinterpret_cast<const float4 *>(Pm), p_blocks, h->M, q_first,
             q_count, h->out_to_in, reinterpret_cast<float4 *>(dP), reinterpret_cast<float4 *>(dX),

@@ -5,9 +5,12 @@
 //   k_inverse_ola       Eq. 8 and the overlap-add of Eqs. 9-12, offline
 //   k_forward_stream    one new block per input into the delay line
 //   k_inverse_stream    one block per output, overlap-add against the state
-// Every transform is P = 2L complex points (see fft_core.cuh); T = P/8 threads
-// run one transform, F = max(1, 256/T) transforms share a 256-thread CTA.
+// Every transform is P = 2L complex points (see fft_core.cuh). The offline
+// forward, bank and inverse kernels run T = P/16 threads per transform with
+// sixteen values each (fft_lane.cuh); the others run T = P/8 threads per
+// transform (fft_block.cuh). F transforms share a 256-thread CTA.
 #include "fft_block.cuh"
+#include "fft_lane.cuh"
 #include "internal.h"
 
 namespace tvolap {
@@ -44,16 +47,16 @@ __global__ void k_tables(float2 *tw, float2 *rot, float2 *post, float *win, int 
 }
 
 template <int LG>
-__global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
+__global__ void __launch_bounds__(Lane<(1 << LG)>::THREADS)
 k_forward_signal(const float *__restrict__ x, int64_t N, int64_t x_stride, int L, int n_blocks,
                  int64_t total, const float *__restrict__ win, const float2 *__restrict__ rot,
                  const float2 *__restrict__ post, const float2 *__restrict__ tw,
                  float2 *__restrict__ X, int64_t t_first, Ragged rg)
 {
-    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F;
+    constexpr int P = 1 << LG, T = Lane<P>::T, F = Lane<P>::F;
     extern __shared__ float2 sm[];
     const int f = threadIdx.x / T, j = threadIdx.x % T;
-    float2 *A = sm + f * P, *B = sm + (F + f) * P;
+    float2 *buf = sm + f * P;
     const int64_t g = (int64_t)blockIdx.x * F + f;     // transform = (channel, block)
     bool active = g < total;
     const int64_t c = active ? g / n_blocks : 0;
@@ -67,52 +70,44 @@ k_forward_signal(const float *__restrict__ x, int64_t N, int64_t x_stride, int L
         // before the transform's barriers)
         if (!__syncthreads_or(active)) return;
     }
-    const int64_t start = (t_first + t - 1) * (int64_t)L;   // block l = t - 1 starts at l*L
-    const float *xc = x + c * x_stride;
-    // start and n are even: a pair is one 8-byte load when the row is 8-byte aligned
-    const bool pairs = (reinterpret_cast<uintptr_t>(xc) & 7) == 0;
-    auto src = [&](int n) {
-        const int64_t i0 = start + n;
-        const float2 w = __ldg(reinterpret_cast<const float2 *>(win) + (n >> 1));
-        float2 v;
-        if (pairs && i0 >= 0 && i0 + 1 < N) {
-            v = __ldg(reinterpret_cast<const float2 *>(xc + i0));
-        } else {
-            v.x = (i0 >= 0 && i0 < N) ? __ldg(xc + i0) : 0.f;
-            v.y = (i0 + 1 >= 0 && i0 + 1 < N) ? __ldg(xc + i0 + 1) : 0.f;
-        }
-        return make_float2(v.x * w.x, v.y * w.y);
-    };
+    SignalPairs src;
+    src.xc = x + c * x_stride;
+    src.win = win;
+    src.start = (t_first + t - 1) * (int64_t)L;        // block l = t - 1 starts at l*L
+    src.N = N;
+    // start is even: a pair is one 8-byte load when the row is 8-byte aligned
+    src.pairs = (reinterpret_cast<uintptr_t>(src.xc) & 7) == 0;
+    src.set_range(L);
     float2 *Xo = X + g * P;
-    forward_block<P>(A, B, j, active, src, rot, post, tw, [&](int k, float2 v) {
+    forward_lane<P>(buf, j, f, active, src, rot, post, tw, [&](int k, float2 v) {
         if (active) Xo[k] = v;
     });
 }
 
 template <int LG>
-__global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
+__global__ void __launch_bounds__(Lane<(1 << LG)>::THREADS)
 k_bank(const float *__restrict__ ir, int ir_len, int64_t ir_stride, int M, int L, int64_t total,
        const float2 *__restrict__ rot, const float2 *__restrict__ post,
        const float2 *__restrict__ tw, float2 *__restrict__ bank_out)
 {
-    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F;
+    constexpr int P = 1 << LG, T = Lane<P>::T, F = Lane<P>::F;
     extern __shared__ float2 sm[];
     const int f = threadIdx.x / T, j = threadIdx.x % T;
-    float2 *A = sm + f * P, *B = sm + (F + f) * P;
+    float2 *buf = sm + f * P;
     const int64_t g = (int64_t)blockIdx.x * F + f;     // transform = (response, partition)
     const bool active = g < total;
     const int64_t s = active ? g / M : 0;
     const int64_t m = active ? g % M : 0;
     const float *h = ir + s * ir_stride;
     const int64_t base = 2 * m * (int64_t)L;            // partition m: taps [2mL, 2mL + 2L)
-    auto src = [&](int n) {
-        const int64_t i0 = base + n;
+    auto src = [&](int n) {                            // taps 2n, 2n+1 of the partition
+        const int64_t i0 = base + 2 * n;
         const float a = (i0 < ir_len) ? __ldg(h + i0) : 0.f;
         const float b = (i0 + 1 < ir_len) ? __ldg(h + i0 + 1) : 0.f;
         return make_float2(a, b);
     };
     float2 *Ho = bank_out + g * P;                     // slots are consecutive [s][m][P]
-    forward_block<P>(A, B, j, active, src, rot, post, tw, [&](int k, float2 v) {
+    forward_lane<P>(buf, j, f, active, src, rot, post, tw, [&](int k, float2 v) {
         if (active) Ho[k] = v;
     });
 }
@@ -150,83 +145,98 @@ k_adjoint_output(const float *__restrict__ g, int64_t g_len, int64_t g_stride, i
     });
 }
 
-// Offline inverse + overlap-add. CTA (segment, output channel) owns output
-// samples [s0, s0 + seg*L) and transforms the blocks that reach them
-// (t = s0/L - 2 .. s0/L + seg), F at a time. The blocks of a round cover the
-// window [(tb-1)L, (tb+F+2)L): its first 3L samples start from the pending
-// sums of the earlier blocks (the carry), each block adds its 4L samples in
-// increasing block order, the first F*L samples are then final and go to y,
-// and the last 3L become the next carry. Every output sample thus sums its
-// contributions in increasing block order, so the result does not depend on
-// the tiling.
+// Offline inverse (Eq. 8) and overlap-add (Eqs. 9-12). A transform's T
+// threads own one segment of seg output hops of one output and run its blocks
+// in order, from the three blocks before the segment (whose 4L outputs reach
+// into it) to its last one; thread j keeps the pending sums of the sample
+// pairs r = j + T q (q < 12) of the next three hops in registers (the pairs a
+// block gives it: a hop moves a pair by P/4 = 4T, q by 4). A hop's samples are
+// final, and written, after the block that starts there: pending (the earlier
+// blocks, added in increasing block order) plus that block's first L samples,
+// the same summation order as adding the blocks one after another.
 template <int LG>
-__global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
-k_inverse_ola(const float2 *__restrict__ Y, int n_blocks, int L, int seg, float *__restrict__ y,
-              int64_t out_len, int64_t y_stride, const float2 *__restrict__ rot,
-              const float2 *__restrict__ post, const float2 *__restrict__ tw, Ragged rg)
+__global__ void __launch_bounds__(Lane<(1 << LG)>::THREADS, 2)
+k_inverse_ola(const float2 *__restrict__ Y, int n_blocks, int L, int seg, int n_seg,
+              float *__restrict__ y, int64_t out_len, int64_t y_stride,
+              const float2 *__restrict__ rot, const float2 *__restrict__ post,
+              const float2 *__restrict__ tw, Ragged rg, int n_outputs)
 {
-    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F, LC = P / 2;
+    constexpr int P = 1 << LG, T = Lane<P>::T, F = Lane<P>::F;
     extern __shared__ float2 sm[];
-    float *carry = reinterpret_cast<float *>(sm + 2 * F * P);    // two buffers of 3L
     const int f = threadIdx.x / T, j = threadIdx.x % T;
-    float2 *A = sm + f * P, *B = sm + (F + f) * P;
-    const int o = blockIdx.y;
-    const int64_t tile0 = (int64_t)blockIdx.x * seg;    // first output hop of the segment
-    const int64_t s0 = tile0 * LC;
-    const int64_t s_end = s0 + (int64_t)seg * LC;
-    const float2 *Yo = Y + (int64_t)o * n_blocks * P;
+    float2 *buf = sm + f * P;
+    const int64_t unit = (int64_t)blockIdx.x * F + f;  // (output, segment)
+    bool on = unit < (int64_t)n_seg * n_outputs;
+    const int o = on ? (int)(unit / n_seg) : 0;
+    const int64_t tile0 = on ? (unit % n_seg) * seg : 0;   // first output hop of the segment
+    const int64_t s0 = tile0 * L;
+    int64_t olen = out_len;
     int64_t nb_o = n_blocks;
-    if (rg.out_len) {                                  // ragged: this output's length
+    if (on && rg.out_len) {                            // ragged: this output's length
         const int64_t oc = rg.out_len[o];
-        if (oc < out_len) out_len = oc < 0 ? 0 : oc;
-        if (s0 >= out_len) return;                     // whole CTA, before any barrier
-        nb_o = blocks_of(out_len, LC);
+        if (oc < olen) olen = oc < 0 ? 0 : oc;
+        nb_o = blocks_of(olen, L);
     }
-    const int64_t w_end = s_end < out_len ? s_end : out_len;   // samples this CTA writes
-    for (int i = threadIdx.x; i < 3 * LC; i += blockDim.x) carry[i] = 0.f;
+    on = on && s0 < olen;
+    // a transform without a segment still takes part in its warp's barriers
+    if constexpr (T > 32) {
+        if (!on) return;                               // its barrier holds its threads only
+    } else {
+        if (!__any_sync(0xffffffffu, on)) return;      // the whole warp has nothing to do
+    }
+    const int64_t s_end = s0 + (int64_t)seg * L;
+    const int64_t w_end = s_end < olen ? s_end : olen; // samples this segment writes
+    const float2 *Yo = Y + (int64_t)o * n_blocks * P;
+    float *yo = y + (int64_t)o * y_stride;
+    const bool pairs = (reinterpret_cast<uintptr_t>(yo) & 7) == 0;
     const int64_t t_lo = tile0 - 2 > 0 ? tile0 - 2 : 0;
     int64_t t_hi = tile0 + seg;
     if (t_hi > nb_o - 1) t_hi = nb_o - 1;
-    const float inv_p = 1.0f / (float)P;
-    float *yo = y + (int64_t)o * y_stride;
-    int cb = 0;
-    for (int64_t tb = t_lo; tb <= t_hi; tb += F) {
-        const int64_t t = tb + f;
-        const bool active = t <= t_hi;
-        const float2 *Yt = Yo + (active ? t : 0) * P;
-        merge_inverse<P>(A, j, post, [&](int k) {
-            return active ? Yt[k] : make_float2(0.f, 0.f);
-        });
-        __syncthreads();
-        // undo the pre-rotation and scale as the last stage stores:
-        // y(2r) + i y(2r+1) = Z(r) e^{+i pi r/P} / P
-        float2 *Z = fft_complex<P, true>(A, B, j, tw, [&](int r, float2 v) {
-            return cscale(cmulc(v, __ldg(rot + r)), inv_p);
-        });
-        const float2 *Zbase = Z - f * P;               // all transforms end in the same half
-        const int nr = (int)(t_hi - tb + 1 < F ? t_hi - tb + 1 : F);   // blocks in this round
-        const int fin = nr * LC;                       // samples final after this round
-        const int span = fin + 3 * LC;
-        const float *cin = carry + cb * 3 * LC;
-        float *cout = carry + (1 - cb) * 3 * LC;
-        const int64_t w0 = (tb - 1) * LC;              // first sample of block tb
-        for (int p = threadIdx.x; p < span; p += blockDim.x) {
-            float v = p < 3 * LC ? cin[p] : 0.f;
-#pragma unroll 4
-            for (int ff = 0; ff < F; ++ff) {
-                if (ff >= nr) break;
-                const int i = p - ff * LC;             // position within block tb+ff
-                if (i >= 0 && i < 4 * LC) v += reinterpret_cast<const float *>(Zbase + ff * P)[i];
-            }
-            if (p < fin) {
-                const int64_t n = w0 + p;
-                if (n >= s0 && n < w_end) yo[n] = v;
-            } else {
-                cout[p - fin] = v;
-            }
+    if (!on) t_hi = t_lo - 1;                          // no blocks, barriers only below
+    float2 pend[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pend[c][i] = make_float2(0.f, 0.f);
+    // every transform of a warp runs the same number of blocks (barriers)
+    int64_t n_run = t_hi - t_lo + 1;
+    if constexpr (T < 32) {
+        int64_t mx = n_run;
+#pragma unroll
+        for (int d = T; d < 32; d *= 2) {
+            const int64_t other = __shfl_xor_sync(0xffffffffu, mx, d);
+            mx = other > mx ? other : mx;
         }
-        cb ^= 1;
-        __syncthreads();
+        n_run = mx;
+    }
+    for (int64_t it = 0; it < n_run; ++it) {
+        const int64_t t = t_lo + it;
+        const bool act = on && t <= t_hi;
+        const float2 *Yt = Yo + (act ? t : 0) * P;
+        // hop t - 1 (block l = t - 1 starts at sample l*L) is final after this
+        // block: pending + the block's first hop; the other hops add to pending
+        const int64_t n0 = (t - 1) * (int64_t)L;
+        inverse_lane<P>(buf, j, f, [&](int k) { return act ? __ldg(Yt + k) : make_float2(0.f, 0.f); },
+                        rot, post, tw, [&](int q, float2 v) {
+            const int c = q >> 2, i = q & 3;
+            if (c == 0) {
+                const float2 fin = cadd(pend[0][i], v);
+                const int64_t n = n0 + 2 * (j + T * i);
+                if (!act) return;
+                if (n >= s0 && n + 1 < w_end && pairs) {
+                    *reinterpret_cast<float2 *>(yo + n) = fin;
+                } else {
+                    if (n >= s0 && n < w_end) yo[n] = fin.x;
+                    if (n + 1 >= s0 && n + 1 < w_end) yo[n + 1] = fin.y;
+                }
+            } else if (c == 1) {
+                pend[0][i] = cadd(pend[1][i], v);
+            } else if (c == 2) {
+                pend[1][i] = cadd(pend[2][i], v);
+            } else {
+                pend[2][i] = v;
+            }
+        });
     }
 }
 
@@ -348,8 +358,19 @@ k_inverse_stream(const float2 *__restrict__ Ys, float *__restrict__ ola, float *
     inverse_stream_block<P>(A, B, j, active, [&](int k) { return Yo[k]; }, st, ou, rot, post, tw);
 }
 
-// Output hops per CTA of the offline inverse (its blocks: seg + 3 = 32).
-constexpr int OLA_SEG = 29;
+// Output hops per segment of the offline inverse. Each segment also
+// transforms the three blocks before it, so long segments waste less; the
+// segments of all outputs should fill one wave of the resident transform
+// groups (groups = SMs x resident CTAs x transforms per CTA) and no more,
+// since a second, partial wave would run nearly alone.
+int64_t ola_seg(int64_t hops_per_output, int n_outputs, int64_t groups)
+{
+    int64_t per_out = groups / (n_outputs > 0 ? n_outputs : 1);
+    if (per_out < 1) per_out = 1;
+    int64_t seg = (hops_per_output + per_out - 1) / per_out;
+    if (seg < 5) seg = 5;                              // at most 3 extra blocks per 5
+    return seg;
+}
 
 // Segment length (output hops per CTA) of the input adjoint.
 int inverse_seg(int L)
@@ -408,11 +429,11 @@ cudaError_t launch_block_spectra(tvolap_plan *h, const float *x, int64_t N, int6
     if (total == 0) return cudaSuccess;
     TVOLAP_DISPATCH(h->lgP, {
         constexpr int P = 1 << LG;
-        const int64_t grid = (total + Geo<P>::F - 1) / Geo<P>::F;
-        const size_t sm = smem_fft<LG>();
+        const int64_t grid = (total + Lane<P>::F - 1) / Lane<P>::F;
+        const size_t sm = smem_lane<LG>();
         cudaError_t e = set_smem(k_forward_signal<LG>, sm);
         if (e != cudaSuccess) return e;
-        k_forward_signal<LG><<<(unsigned)grid, Geo<P>::THREADS, sm, h->stream>>>(
+        k_forward_signal<LG><<<(unsigned)grid, Lane<P>::THREADS, sm, h->stream>>>(
             x, N, x_stride, h->L, n_blocks, total, h->win, h->rot, h->post, h->tw, X, t_first, rg);
     });
     return cudaGetLastError();
@@ -426,11 +447,11 @@ cudaError_t launch_bank(tvolap_plan *h, int first_slot, int count, const float *
     float2 *dst = h->bank + (int64_t)first_slot * h->M * h->P;
     TVOLAP_DISPATCH(h->lgP, {
         constexpr int P = 1 << LG;
-        const int64_t grid = (total + Geo<P>::F - 1) / Geo<P>::F;
-        const size_t sm = smem_fft<LG>();
+        const int64_t grid = (total + Lane<P>::F - 1) / Lane<P>::F;
+        const size_t sm = smem_lane<LG>();
         cudaError_t e = set_smem(k_bank<LG>, sm);
         if (e != cudaSuccess) return e;
-        k_bank<LG><<<(unsigned)grid, Geo<P>::THREADS, sm, h->stream>>>(
+        k_bank<LG><<<(unsigned)grid, Lane<P>::THREADS, sm, h->stream>>>(
             ir, ir_len, ir_stride, h->M, h->L, total, h->rot, h->post, h->tw, dst);
     });
     return cudaGetLastError();
@@ -451,11 +472,11 @@ cudaError_t launch_bank_raw(int lgP, int L, int M, int64_t count, const float *i
     if (total == 0) return cudaSuccess;
     TVOLAP_DISPATCH(lgP, {
         constexpr int P = 1 << LG;
-        const int64_t grid = (total + Geo<P>::F - 1) / Geo<P>::F;
-        const size_t sm = smem_fft<LG>();
+        const int64_t grid = (total + Lane<P>::F - 1) / Lane<P>::F;
+        const size_t sm = smem_lane<LG>();
         cudaError_t e = set_smem(k_bank<LG>, sm);
         if (e != cudaSuccess) return e;
-        k_bank<LG><<<(unsigned)grid, Geo<P>::THREADS, sm, st>>>(ir, ir_len, ir_stride, M, L, total,
+        k_bank<LG><<<(unsigned)grid, Lane<P>::THREADS, sm, st>>>(ir, ir_len, ir_stride, M, L, total,
                                                               rot, post, tw, dst);
     });
     return cudaGetLastError();
@@ -467,16 +488,31 @@ cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, fl
     if (out_len <= 0) return cudaSuccess;
     if (n_outputs < 0) n_outputs = h->n_out;
     if (n_outputs == 0) return cudaSuccess;
-    const int seg = OLA_SEG;
-    const int64_t n_seg = (out_len + (int64_t)seg * h->L - 1) / ((int64_t)seg * h->L);
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
     TVOLAP_DISPATCH(h->lgP, {
         constexpr int P = 1 << LG;
-        const size_t sm = smem_fft<LG>() + (size_t)6 * h->L * sizeof(float);
+        const size_t sm = smem_lane<LG>();
         cudaError_t e = set_smem(k_inverse_ola<LG>, sm);
         if (e != cudaSuccess) return e;
-        dim3 grid((unsigned)n_seg, (unsigned)n_outputs);
-        k_inverse_ola<LG><<<grid, Geo<P>::THREADS, sm, h->stream>>>(
-            Y, n_blocks, h->L, seg, y, out_len, y_stride, h->rot, h->post, h->tw, rg);
+        static int per_sm = 0;                         // resident CTAs (per kernel instance)
+        if (per_sm == 0) {
+            int n = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_inverse_ola<LG>,
+                                                              Lane<P>::THREADS, sm);
+            if (e != cudaSuccess) return e;
+            per_sm = n > 0 ? n : 1;
+        }
+        const int64_t seg = ola_seg((out_len + h->L - 1) / h->L, n_outputs,
+                                    (int64_t)sms * per_sm * Lane<P>::F);
+        if (seg > 0x7fffffffLL / h->L) return cudaErrorInvalidValue;
+        const int64_t n_seg = (out_len + seg * h->L - 1) / (seg * h->L);
+        if (n_seg * n_outputs > 0x7fffffffLL) return cudaErrorInvalidValue;
+        const int64_t units = n_seg * n_outputs;
+        const int64_t grid = (units + Lane<P>::F - 1) / Lane<P>::F;
+        k_inverse_ola<LG><<<(unsigned)grid, Lane<P>::THREADS, sm, h->stream>>>(
+            Y, n_blocks, h->L, (int)seg, (int)n_seg, y, out_len, y_stride, h->rot, h->post, h->tw,
+            rg, n_outputs);
     });
     return cudaGetLastError();
 }

@@ -242,14 +242,17 @@ def test_mac_staging_variants_agree_bitwise(L, n_slots, interp):
 
 
 def test_staging_option_range():
-    """TVOLAP_OPT_MAC_STAGING takes 0 .. 5; other values and options are refused."""
+    """TVOLAP_OPT_MAC_STAGING takes 0 .. 5, TVOLAP_OPT_STAGE_TIMING 0 or 1;
+    other values and options are refused."""
     from paper_2310_00319_gb300 import TvolapError
     dev = _dev()
     wl = W.random_case(3, L=64, ir_len=300, N=2000, n_slots=2)
     plan = _plan(wl, dev)
     for v in range(6):
         plan.set_option(1, v)
-    for opt, v in [(1, -1), (1, 6), (2, 0)]:
+    for v in (1, 0):
+        plan.set_option(2, v)
+    for opt, v in [(1, -1), (1, 6), (2, 2), (2, -1), (3, 0), (0, 0)]:
         with pytest.raises(TvolapError):
             plan.set_option(opt, v)
 
