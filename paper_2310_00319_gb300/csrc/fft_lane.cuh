@@ -205,32 +205,45 @@ struct SignalPairs {
             v.x = (i0 >= 0 && i0 < N) ? __ldg(xc + i0) : 0.f;
             v.y = (i0 + 1 >= 0 && i0 + 1 < N) ? __ldg(xc + i0 + 1) : 0.f;
         }
-        return make_float2(v.x * w.x, v.y * w.y);
+        return __fmul2_rn(v, w);
     }
 };
 
-// The forward transform of one block. src(n) gives the windowed pair
-// (x(2n), x(2n+1)) for n < P/2 (the upper half is the zero padding); st(k, v)
-// receives X(k), each k < P exactly once per thread set. The buffer holds P
-// values (swizzled); on entry it may still be read by this transform's
-// threads for an earlier transform (the first barrier covers that).
-template <int P, class Src, class Store>
-__device__ __forceinline__ void forward_lane(float2 *buf, int j, int f, bool active, Src src,
-                                             const float2 *__restrict__ rot,
-                                             const float2 *__restrict__ post,
-                                             const float2 *__restrict__ tw, Store st)
+// The inputs a thread's first-stage butterflies (j and S - 1 - j) take from a
+// block: z[u][r] = src(bb[u] + S r), r < 4 (the upper half is zero padding);
+// src(n) gives the windowed pair (x(2n), x(2n+1)) for n < P/2.
+template <int P, class Src>
+__device__ __forceinline__ void forward_inputs(int j, bool active, Src src, float2 (&z)[2][4])
+{
+    constexpr int S = Lane<P>::S;
+    const int bb[2] = {j, S - 1 - j};
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) z[u][r] = active ? src(bb[u] + S * r) : make_float2(0.f, 0.f);
+}
+
+// The forward transform of one block from its inputs (forward_inputs);
+// st(k, v) receives X(k), each k < P exactly once per thread set. The buffer
+// holds P values (swizzled); on entry it may still be read by this
+// transform's threads for an earlier transform (the first barrier covers that).
+template <int P, class Store>
+__device__ __forceinline__ void forward_lane_z(float2 *buf, int j, int f, bool active,
+                                               const float2 (&z)[2][4],
+                                               const float2 *__restrict__ rot,
+                                               const float2 *__restrict__ post,
+                                               const float2 *__restrict__ tw, Store st)
 {
     constexpr int T = Lane<P>::T, S = Lane<P>::S;
     // first stage (Ns = 1, radix 8, stride S): butterflies j and S - 1 - j run
-    // on the inputs this thread loads; inputs r >= 4 are the zero padding
+    // on this thread's inputs, pre-rotated by rot(n) = rot(b) e^{-i pi r/8}
     const int bb[2] = {j, S - 1 - j};
     float2 v[2][8];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         const float2 r0 = active ? __ldg(rot + bb[u]) : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-            v[u][r] = active ? cmul(src(bb[u] + S * r), cmul(r0, c16(2 * r))) : make_float2(0.f, 0.f);
+        for (int r = 0; r < 4; ++r) v[u][r] = cmul(z[u][r], cmul(r0, c16(2 * r)));
         dft8_half(v[u]);
     }
     lane_sync<T>(f);
@@ -248,9 +261,12 @@ __device__ __forceinline__ void forward_lane(float2 *buf, int j, int f, bool act
     }
     // split: for k < P/2 in butterfly b (s < R/2), the partner P - 1 - k is
     // output R - 1 - s of butterfly NS - 1 - b
+    const float2 half = make_float2(0.5f, 0.5f);
     auto split = [&](float2 zk, float2 zkk, float2 w, int k) {
-        const float2 E = make_float2(0.5f * (zk.x + zkk.x), 0.5f * (zk.y - zkk.y));
-        const float2 d = make_float2(0.5f * (zk.x - zkk.x), 0.5f * (zk.y + zkk.y));
+        // E = (zk + conj zkk) / 2, d = (zk - conj zkk) / 2 (each lane rounded as
+        // the scalar sum, then halved exactly)
+        const float2 E = __fmul2_rn(__ffma2_rn(zkk, make_float2(1.f, -1.f), zk), half);
+        const float2 d = __fmul2_rn(__ffma2_rn(zkk, make_float2(-1.f, 1.f), zk), half);
         const float2 O = make_float2(d.y, -d.x);           // (zk - conj zkk) / 2i
         const float2 t = cmul(w, O);
         st(k, cadd(E, t));
@@ -267,6 +283,19 @@ __device__ __forceinline__ void forward_lane(float2 *buf, int j, int f, bool act
             split(hi[u][s], lo[u][R - 1 - s], cmul(ph, c16(16 / R * s)), bh + s * NS);
         }
     }
+}
+
+// The forward transform of one block whose inputs src(n) gives (as
+// forward_inputs), loaded and transformed in one go.
+template <int P, class Src, class Store>
+__device__ __forceinline__ void forward_lane(float2 *buf, int j, int f, bool active, Src src,
+                                             const float2 *__restrict__ rot,
+                                             const float2 *__restrict__ post,
+                                             const float2 *__restrict__ tw, Store st)
+{
+    float2 z[2][4];
+    forward_inputs<P>(j, active, src, z);
+    forward_lane_z<P>(buf, j, f, active, z, rot, post, tw, st);
 }
 
 // The inverse transform of one block, its rotation undone and scaled by 1/P:
@@ -295,8 +324,9 @@ __device__ __forceinline__ void inverse_lane(float2 *buf, int j, int f, Load ld,
         for (int r = 0; r < 4; ++r) {
             // n = bb[u] + S r < P/2, partner P - 1 - n = input 7 - r of the other butterfly
             const float2 yk = v[u][r], ykk = v[1 - u][7 - r];
-            const float2 E = make_float2(0.5f * (yk.x + ykk.x), 0.5f * (yk.y - ykk.y));
-            const float2 d = make_float2(0.5f * (yk.x - ykk.x), 0.5f * (yk.y + ykk.y));
+            const float2 half = make_float2(0.5f, 0.5f);
+            const float2 E = __fmul2_rn(__ffma2_rn(ykk, make_float2(1.f, -1.f), yk), half);
+            const float2 d = __fmul2_rn(__ffma2_rn(ykk, make_float2(-1.f, 1.f), yk), half);
             const float2 O = cmulc(d, cmul(pb[u], c16(2 * r)));   // post(n) = post(b) e^{-i pi r/8}
             v[u][r] = cadd(E, make_float2(-O.y, O.x));               // E + i O
             v[1 - u][7 - r] = cadd(cconj(E), make_float2(O.y, O.x)); // conj E + i conj O

@@ -46,6 +46,8 @@ __global__ void k_tables(float2 *tw, float2 *rot, float2 *post, float *win, int 
     }
 }
 
+// Forward transforms of every block of every input channel (Eqs. 1, 3, 5):
+// transform g = (channel, block) per group of T threads.
 template <int LG>
 __global__ void __launch_bounds__(Lane<(1 << LG)>::THREADS)
 k_forward_signal(const float *__restrict__ x, int64_t N, int64_t x_stride, int L, int n_blocks,
@@ -57,7 +59,7 @@ k_forward_signal(const float *__restrict__ x, int64_t N, int64_t x_stride, int L
     extern __shared__ float2 sm[];
     const int f = threadIdx.x / T, j = threadIdx.x % T;
     float2 *buf = sm + f * P;
-    const int64_t g = (int64_t)blockIdx.x * F + f;     // transform = (channel, block)
+    const int64_t g = (int64_t)blockIdx.x * F + f;
     bool active = g < total;
     const int64_t c = active ? g / n_blocks : 0;
     const int64_t t = active ? g % n_blocks : 0;
