@@ -55,11 +55,19 @@ __device__ __forceinline__ float2 c16(int k)
     return make_float2(re[k], im[k]);
 }
 
-// Dynamic shared memory of a lane kernel: one P-value buffer per transform.
+// A transform's buffer holds its P values with one unused slot after every
+// eight: value n at lpad(n) = n + n / 8. The stage stores (rows of eight
+// consecutive values, or values eight apart) then fall on 16 different
+// positions per half warp, and every offset a thread uses within a stage is
+// one runtime base plus compile-time constants.
+__host__ __device__ constexpr int lane_buf(int P) { return P + P / 8; }
+__device__ __forceinline__ int lpad(int n) { return n + (n >> 3); }
+
+// Dynamic shared memory of a lane kernel: one buffer per transform.
 template <int LG>
 inline size_t smem_lane()
 {
-    return (size_t)Lane<(1 << LG)>::F * (1 << LG) * sizeof(float2);
+    return (size_t)Lane<(1 << LG)>::F * lane_buf(1 << LG) * sizeof(float2);
 }
 
 // dft8 (forward) of v[0..3] with v[4..7] zero: the first radix-2 layer of the
@@ -123,15 +131,21 @@ __device__ __forceinline__ void powers(float2 w1, float2 (&w)[R])
     }
 }
 
-// Butterfly b of stage (Ns, R): its R inputs from the swizzled buffer, rotated
+// Butterfly b of stage (Ns, R): its R inputs from the padded buffer, rotated
 // by the stage's twiddles, transformed.
 template <int P, int Ns, bool INV>
 __device__ __forceinline__ void lane_bfly(const float2 *buf, int b, const float2 *__restrict__ tw,
                                           float2 (&v)[LStage<P, Ns>::R])
 {
     constexpr int R = LStage<P, Ns>::R, stride = P / R;
+    if constexpr (stride % 8 == 0) {
+        const float2 *bp = buf + lpad(b);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = buf[swz(b + r * stride)];
+        for (int r = 0; r < R; ++r) v[r] = bp[r * stride / 8 * 9];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = buf[lpad(b + r * stride)];
+    }
     if constexpr (Ns > 1) {
         float2 w[R];
         powers<R>(__ldg(tw + tw_offset(P, Ns) + (b & (Ns - 1))), w);
@@ -146,8 +160,18 @@ __device__ __forceinline__ void lane_store(float2 *buf, int b, const float2 (&v)
 {
     constexpr int R = LStage<P, Ns>::R;
     const int base = (b / Ns) * Ns * R + (b & (Ns - 1));
+    if constexpr (Ns == 1) {
+        float2 *bp = buf + 9 * b;                      // lpad(8 b + s) = 9 b + s, s < 8 = R
 #pragma unroll
-    for (int s = 0; s < R; ++s) buf[swz(base + s * Ns)] = v[s];
+        for (int s = 0; s < R; ++s) bp[s] = v[s];
+    } else if constexpr (Ns % 8 == 0) {
+        float2 *bp = buf + lpad(base);
+#pragma unroll
+        for (int s = 0; s < R; ++s) bp[s * Ns / 8 * 9] = v[s];
+    } else {
+#pragma unroll
+        for (int s = 0; s < R; ++s) buf[lpad(base + s * Ns)] = v[s];
+    }
 }
 
 // Middle stages (neither the first nor the last): butterflies b = j + T u.
@@ -225,8 +249,9 @@ __device__ __forceinline__ void forward_inputs(int j, bool active, Src src, floa
 
 // The forward transform of one block from its inputs (forward_inputs);
 // st(k, v) receives X(k), each k < P exactly once per thread set. The buffer
-// holds P values (swizzled); on entry it may still be read by this
-// transform's threads for an earlier transform (the first barrier covers that).
+// holds lane_buf(P) values (padded layout); on entry it may still be read by
+// this transform's threads for an earlier transform (the first barrier covers
+// that).
 template <int P, class Store>
 __device__ __forceinline__ void forward_lane_z(float2 *buf, int j, int f, bool active,
                                                const float2 (&z)[2][4],

@@ -58,7 +58,7 @@ k_forward_signal(const float *__restrict__ x, int64_t N, int64_t x_stride, int L
     constexpr int P = 1 << LG, T = Lane<P>::T, F = Lane<P>::F;
     extern __shared__ float2 sm[];
     const int f = threadIdx.x / T, j = threadIdx.x % T;
-    float2 *buf = sm + f * P;
+    float2 *buf = sm + f * lane_buf(P);
     const int64_t g = (int64_t)blockIdx.x * F + f;
     bool active = g < total;
     const int64_t c = active ? g / n_blocks : 0;
@@ -95,7 +95,7 @@ k_bank(const float *__restrict__ ir, int ir_len, int64_t ir_stride, int M, int L
     constexpr int P = 1 << LG, T = Lane<P>::T, F = Lane<P>::F;
     extern __shared__ float2 sm[];
     const int f = threadIdx.x / T, j = threadIdx.x % T;
-    float2 *buf = sm + f * P;
+    float2 *buf = sm + f * lane_buf(P);
     const int64_t g = (int64_t)blockIdx.x * F + f;     // transform = (response, partition)
     const bool active = g < total;
     const int64_t s = active ? g / M : 0;
@@ -166,7 +166,7 @@ k_inverse_ola(const float2 *__restrict__ Y, int n_blocks, int L, int seg, int n_
     constexpr int P = 1 << LG, T = Lane<P>::T, F = Lane<P>::F;
     extern __shared__ float2 sm[];
     const int f = threadIdx.x / T, j = threadIdx.x % T;
-    float2 *buf = sm + f * P;
+    float2 *buf = sm + f * lane_buf(P);
     const int64_t unit = (int64_t)blockIdx.x * F + f;  // (output, segment)
     bool on = unit < (int64_t)n_seg * n_outputs;
     const int o = on ? (int)(unit / n_seg) : 0;
