@@ -55,13 +55,21 @@ __device__ __forceinline__ float2 c16(int k)
     return make_float2(re[k], im[k]);
 }
 
-// A transform's buffer holds its P values with one unused slot after every
-// eight: value n at lpad(n) = n + n / 8. The stage stores (rows of eight
-// consecutive values, or values eight apart) then fall on 16 different
-// positions per half warp, and every offset a thread uses within a stage is
-// one runtime base plus compile-time constants.
-__host__ __device__ constexpr int lane_buf(int P) { return P + P / 8; }
-__device__ __forceinline__ int lpad(int n) { return n + (n >> 3); }
+// Buffer layouts (a transform's P values in lane_buf(P) slots). Every array
+// between two stages is written once and read once, each in its own layout,
+// chosen so that a half warp's 64-bit accesses fall on 16 different positions
+// for both its writer and its reader:
+//   * layout A, the first stage's output (written as rows of eight consecutive
+//     values 8b + s, read as 16 consecutive values per half warp): one unused
+//     slot after every 16 values, pa(n) = n + n/16;
+//   * layout B, a middle stage's output (written as two groups of eight values
+//     64 apart, read as 16 consecutive values): bit 3 flipped where bit 6 is
+//     set, pb(n) = n ^ ((n >> 3) & 8), a permutation within each 16 values.
+// For the common strides, every offset a thread uses within a stage is one or
+// two runtime bases plus compile-time constants.
+__host__ __device__ constexpr int lane_buf(int P) { return P + P / 16; }
+__device__ __forceinline__ int pa(int n) { return n + (n >> 4); }
+__device__ __forceinline__ int pb(int n) { return n ^ ((n >> 3) & 8); }
 
 // Dynamic shared memory of a lane kernel: one buffer per transform.
 template <int LG>
@@ -131,20 +139,33 @@ __device__ __forceinline__ void powers(float2 w1, float2 (&w)[R])
     }
 }
 
-// Butterfly b of stage (Ns, R): its R inputs from the padded buffer, rotated
-// by the stage's twiddles, transformed.
+// Butterfly b of stage (Ns, R): its R inputs from the buffer (layout A after
+// the first stage, B after a middle one), rotated by the stage's twiddles,
+// transformed.
 template <int P, int Ns, bool INV>
 __device__ __forceinline__ void lane_bfly(const float2 *buf, int b, const float2 *__restrict__ tw,
                                           float2 (&v)[LStage<P, Ns>::R])
 {
     constexpr int R = LStage<P, Ns>::R, stride = P / R;
-    if constexpr (stride % 8 == 0) {
-        const float2 *bp = buf + lpad(b);
+    if constexpr (Ns == 8) {                           // input in layout A
+        if constexpr (stride % 16 == 0) {
+            const float2 *bp = buf + pa(b);            // pa(b + 16k) = pa(b) + 17k
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = bp[r * stride / 8 * 9];
-    } else {
+            for (int r = 0; r < R; ++r) v[r] = bp[r * stride / 16 * 17];
+        } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = buf[lpad(b + r * stride)];
+            for (int r = 0; r < R; ++r) v[r] = buf[pa(b + r * stride)];
+        }
+    } else {                                           // input in layout B
+        if constexpr (stride % 64 == 0) {
+            // pb(b + 64k) = pb(b) ^ (8 (k mod 2)) + 64k
+            const int b0 = pb(b), b1 = b0 ^ 8;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = buf[((r * stride / 64) & 1 ? b1 : b0) + r * stride];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = buf[pb(b + r * stride)];
+        }
     }
     if constexpr (Ns > 1) {
         float2 w[R];
@@ -155,22 +176,30 @@ __device__ __forceinline__ void lane_bfly(const float2 *buf, int b, const float2
     dftR<R, INV>(v);
 }
 
+// Outputs of butterfly b of a non-last stage: the first stage's in layout A,
+// a middle stage's in layout B.
 template <int P, int Ns>
 __device__ __forceinline__ void lane_store(float2 *buf, int b, const float2 (&v)[LStage<P, Ns>::R])
 {
     constexpr int R = LStage<P, Ns>::R;
     const int base = (b / Ns) * Ns * R + (b & (Ns - 1));
     if constexpr (Ns == 1) {
-        float2 *bp = buf + 9 * b;                      // lpad(8 b + s) = 9 b + s, s < 8 = R
+        float2 *bp = buf + 8 * b + (b >> 1);           // pa(8 b + s) = 8 b + b/2 + s, s < 8 = R
 #pragma unroll
         for (int s = 0; s < R; ++s) bp[s] = v[s];
-    } else if constexpr (Ns % 8 == 0) {
-        float2 *bp = buf + lpad(base);
+    } else if constexpr (Ns == 8) {
+        // base + 8 s keeps base's bit 6: pb flips bit 3 of 8 s, i.e. +-8
+        const int m = (base >> 3) & 8;
 #pragma unroll
-        for (int s = 0; s < R; ++s) bp[s * Ns / 8 * 9] = v[s];
+        for (int s = 0; s < R; ++s) buf[(s & 1 ? base - m : base + m) + s * Ns] = v[s];
+    } else if constexpr (Ns % 64 == 0) {
+        // bit 6 of base + s Ns is bit 6 of base xor bit 0 of s Ns / 64
+        const int b0 = pb(base), b1 = b0 ^ 8;
+#pragma unroll
+        for (int s = 0; s < R; ++s) buf[((s * Ns / 64) & 1 ? b1 : b0) + s * Ns] = v[s];
     } else {
 #pragma unroll
-        for (int s = 0; s < R; ++s) buf[lpad(base + s * Ns)] = v[s];
+        for (int s = 0; s < R; ++s) buf[pb(base + s * Ns)] = v[s];
     }
 }
 
@@ -249,7 +278,7 @@ __device__ __forceinline__ void forward_inputs(int j, bool active, Src src, floa
 
 // The forward transform of one block from its inputs (forward_inputs);
 // st(k, v) receives X(k), each k < P exactly once per thread set. The buffer
-// holds lane_buf(P) values (padded layout); on entry it may still be read by
+// holds lane_buf(P) values; on entry it may still be read by
 // this transform's threads for an earlier transform (the first barrier covers
 // that).
 template <int P, class Store>
