@@ -281,7 +281,7 @@ __device__ __forceinline__ void forward_inputs(int j, bool active, Src src, floa
 // holds lane_buf(P) values; on entry it may still be read by
 // this transform's threads for an earlier transform (the first barrier covers
 // that).
-template <int P, class Store>
+template <int P, bool SYNC_OUT = false, class Store>
 __device__ __forceinline__ void forward_lane_z(float2 *buf, int j, int f, bool active,
                                                const float2 (&z)[2][4],
                                                const float2 *__restrict__ rot,
@@ -313,6 +313,9 @@ __device__ __forceinline__ void forward_lane_z(float2 *buf, int j, int f, bool a
         lane_bfly<P, NS, false>(buf, j + T * u, tw, lo[u]);
         lane_bfly<P, NS, false>(buf, NS - 1 - j - T * u, tw, hi[u]);
     }
+    // SYNC_OUT: every thread of the transform has read the buffer, so st may
+    // write into it
+    if constexpr (SYNC_OUT) lane_sync<T>(f);
     // split: for k < P/2 in butterfly b (s < R/2), the partner P - 1 - k is
     // output R - 1 - s of butterfly NS - 1 - b
     const float2 half = make_float2(0.5f, 0.5f);
@@ -341,7 +344,7 @@ __device__ __forceinline__ void forward_lane_z(float2 *buf, int j, int f, bool a
 
 // The forward transform of one block whose inputs src(n) gives (as
 // forward_inputs), loaded and transformed in one go.
-template <int P, class Src, class Store>
+template <int P, bool SYNC_OUT = false, class Src, class Store>
 __device__ __forceinline__ void forward_lane(float2 *buf, int j, int f, bool active, Src src,
                                              const float2 *__restrict__ rot,
                                              const float2 *__restrict__ post,
@@ -349,7 +352,7 @@ __device__ __forceinline__ void forward_lane(float2 *buf, int j, int f, bool act
 {
     float2 z[2][4];
     forward_inputs<P>(j, active, src, z);
-    forward_lane_z<P>(buf, j, f, active, z, rot, post, tw, st);
+    forward_lane_z<P, SYNC_OUT>(buf, j, f, active, z, rot, post, tw, st);
 }
 
 // The inverse transform of one block, its rotation undone and scaled by 1/P:

@@ -142,14 +142,13 @@ k_adjoint_mac_x(const float4 *__restrict__ G, int64_t g_first, int g_count,
     constexpr int P = 1 << LG, T = Lane<P>::T, F = Lane<P>::F, P4 = P / 2;
     extern __shared__ float2 sm[];
     const int f = threadIdx.x / T, j = threadIdx.x % T;
-    float2 *buf = sm + f * lane_buf(P);                // the transform's working buffer
-    float2 *spectra = sm + F * lane_buf(P);            // then the F blocks' spectra
+    float2 *buf = sm + f * lane_buf(P);                // the transform's buffer, then its spectrum
     const int o = blockIdx.y;
     const int c = out_to_in[o];
     const int64_t q0 = q_first + (int64_t)blockIdx.x * F;
     const int64_t q_end = q_first + q_count;
     // forward transform of block q = q0 + f, as the forward transform kernel
-    // computes it, into the spectra area (F blocks after the buffers)
+    // computes it; its spectrum replaces the transform's data in its buffer
     {
         const int64_t q = q0 + f;
         const bool active = q < q_end;
@@ -160,8 +159,8 @@ k_adjoint_mac_x(const float4 *__restrict__ G, int64_t g_first, int g_count,
         src.N = N;
         src.pairs = (reinterpret_cast<uintptr_t>(src.xc) & 7) == 0;
         src.set_range(L);
-        float2 *Xs = spectra + f * P;
-        forward_lane<P>(buf, j, f, active, src, rot, post, tw, [&](int k, float2 v) { Xs[k] = v; });
+        forward_lane<P, true>(buf, j, f, active, src, rot, post, tw,
+                              [&](int k, float2 v) { buf[k] = v; });
     }
     __syncthreads();
     const int64_t MP4 = (int64_t)M * P4;
@@ -171,7 +170,7 @@ k_adjoint_mac_x(const float4 *__restrict__ G, int64_t g_first, int g_count,
         const int ff = it / P4, k = it % P4;
         const int64_t q = q0 + ff;
         if (q >= q_end) continue;
-        const float4 xq = reinterpret_cast<const float4 *>(spectra + ff * P)[k];
+        const float4 xq = reinterpret_cast<const float4 *>(sm + ff * lane_buf(P))[k];
         const float4 *Gq = G + ((int64_t)o * g_count + (q - g_first)) * P4 + k;
         const float4 *Pq = Pm + (int64_t)o * p_blocks * MP4 + q * MP4 + k;
         float4 *dPq = dPo + q * MP4 + k;
@@ -240,8 +239,7 @@ cudaError_t launch_adjoint_mac_x(tvolap_plan *h, const float2 *G, int64_t g_firs
     }
     TVOLAP_DISPATCH(h->lgP, {
         constexpr int P = 1 << LG;
-        // buffers, then the blocks' spectra
-        const size_t sm = smem_lane<LG>() + (size_t)Lane<P>::F * P * sizeof(float2);
+        const size_t sm = smem_lane<LG>();
         cudaError_t e = set_smem(k_adjoint_mac_x<LG>, sm);
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)((q_count + Lane<P>::F - 1) / Lane<P>::F), (unsigned)h->n_out);
