@@ -517,8 +517,12 @@ TVOLAP_API int tvolap_check(tvolap_t h);
  * Batched sources: many independent sources with different hops, partition
  * counts, numbers of stored filters and signal lengths, run together. The
  * sources are grouped by hop; each group is one plan whose channels are the
- * group's sources (tvolap_process_ragged), all groups share one stream, and
- * the whole batch can be captured once as a CUDA graph and replayed. The
+ * group's sources (tvolap_process_ragged). Every call is ordered on the
+ * batch's stream; inside a run (and a load of filters, and the autotuner)
+ * each group works on a stream of its own, forked from the batch's stream and
+ * joined back into it, so the groups' kernels overlap on the GPU. The whole
+ * batch can be captured once as a CUDA graph (one branch per group) and
+ * replayed. The
  * multiply-accumulate staging (TVOLAP_OPT_MAC_STAGING) can be chosen per
  * group by timing the variants on the batch itself.
  * ======================================================================== */

@@ -1,7 +1,9 @@
 // C ABI of batched sources (tvolap_batch_*): sources grouped by hop, one plan
-// and one ragged call per group (tvolap_process_ragged), all on one stream,
-// captured as one CUDA graph; per-group choice of the multiply-accumulate
-// staging by timing the variants on the batch itself.
+// and one ragged call per group (tvolap_process_ragged). Each group runs on a
+// stream of its own, forked from the batch's stream at the start of a run and
+// joined back at its end, so the groups' kernels overlap on the GPU; the run
+// is captured as one CUDA graph of parallel branches. Per-group choice of the
+// multiply-accumulate staging by timing the variants on the batch itself.
 #include <algorithm>
 #include <map>
 #include <new>
@@ -24,6 +26,8 @@ struct BatchGroup {
     int32_t *sched = nullptr;             // [rows][nb]
     int64_t *n_dev = nullptr, *ol_dev = nullptr;
     int32_t *parts_dev = nullptr;
+    cudaStream_t st = nullptr;            // the group's stream (its plan's)
+    cudaEvent_t done = nullptr;           // the group's work of a run has finished
 };
 
 int64_t blocks_of(int64_t out_len, int L) { return out_len <= 0 ? 0 : (out_len - 1) / L + 2; }
@@ -59,6 +63,7 @@ struct tvolap_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graph = nullptr;
+    cudaEvent_t fork = nullptr;           // the batch stream's work before a run
 };
 
 namespace {
@@ -69,6 +74,8 @@ void release(tvolap_batch *b)
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (BatchGroup &g : b->groups) {
         tvolap_destroy(g.plan);
+        if (g.done) cudaEventDestroy(g.done);
+        if (g.st) cudaStreamDestroy(g.st);
         cudaFree(g.x);
         cudaFree(g.y);
         cudaFree(g.sched);
@@ -76,20 +83,49 @@ void release(tvolap_batch *b)
         cudaFree(g.ol_dev);
         cudaFree(g.parts_dev);
     }
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
 
+// The groups' streams (all, or group `only`) wait for the work enqueued on
+// the batch's stream so far.
+cudaError_t fork_groups(tvolap_batch *b, BatchGroup *only = nullptr)
+{
+    cudaError_t e = cudaEventRecord(b->fork, b->stream);
+    for (BatchGroup &g : b->groups)
+        if (e == cudaSuccess && (!only || only == &g)) e = cudaStreamWaitEvent(g.st, b->fork, 0);
+    return e;
+}
+
+// The batch's stream waits for the work enqueued on the groups' streams.
+cudaError_t join_groups(tvolap_batch *b, BatchGroup *only = nullptr)
+{
+    cudaError_t e = cudaSuccess;
+    for (BatchGroup &g : b->groups) {
+        if (only && only != &g) continue;
+        const cudaError_t r = cudaEventRecord(g.done, g.st);
+        const cudaError_t w = r == cudaSuccess ? cudaStreamWaitEvent(b->stream, g.done, 0) : r;
+        if (e == cudaSuccess) e = w;
+    }
+    return e;
+}
+
+int ragged(BatchGroup &g)
+{
+    return tvolap_process_ragged(g.plan, g.x, g.max_n, g.n_dev, g.ol_dev, g.parts_dev, g.max_out,
+                                 g.sched, nullptr, nullptr, g.nb, g.y, g.max_out);
+}
+
+// One run: every group on its own stream, between a fork and a join.
 int run_direct(tvolap_batch *b)
 {
-    for (BatchGroup &g : b->groups) {
-        if (g.max_out == 0) continue;
-        const int e = tvolap_process_ragged(g.plan, g.x, g.max_n, g.n_dev, g.ol_dev, g.parts_dev,
-                                            g.max_out, g.sched, nullptr, nullptr, g.nb, g.y,
-                                            g.max_out);
-        if (e != TVOLAP_OK) return e;
-    }
-    return TVOLAP_OK;
+    cudaError_t ce = fork_groups(b);
+    int e = ce == cudaSuccess ? TVOLAP_OK : cuda_status(ce);
+    for (BatchGroup &g : b->groups)
+        if (e == TVOLAP_OK && g.max_out > 0) e = ragged(g);
+    ce = join_groups(b);                   // also after an error: a capture needs every branch joined
+    return e != TVOLAP_OK ? e : cuda_status(ce);
 }
 
 }  // namespace
@@ -115,6 +151,8 @@ int tvolap_batch_create(tvolap_batch_t *out, const tvolap_batch_source *src, int
         return code;
     };
     b->src.assign(src, src + n_src);
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+        return fail(TVOLAP_ERR_CUDA);
     if (stream) {
         b->stream = static_cast<cudaStream_t>(stream);
     } else {
@@ -150,7 +188,10 @@ int tvolap_batch_create(tvolap_batch_t *out, const tvolap_batch_source *src, int
             ph[r] = s.M;
         }
         g.nb = blocks_of(g.max_out, g.L);
-        int e = tvolap_create(&g.plan, g.L, g.M, 0, n, n, nullptr, n_slots, b->stream);
+        if (cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess)
+            return fail(TVOLAP_ERR_CUDA);
+        int e = tvolap_create(&g.plan, g.L, g.M, 0, n, n, nullptr, n_slots, g.st);
         if (e != TVOLAP_OK) return fail(e);
         const size_t xs = (size_t)n * std::max<int64_t>(g.max_n, 1) * sizeof(float);
         const size_t ys = (size_t)n * std::max<int64_t>(g.max_out, 1) * sizeof(float);
@@ -171,8 +212,11 @@ int tvolap_batch_create(tvolap_batch_t *out, const tvolap_batch_source *src, int
             cudaMemcpyAsync(g.parts_dev, ph.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice,
                             b->stream) != cudaSuccess)
             return fail(TVOLAP_ERR_CUDA);
-        // the host arrays above are copied before they go out of scope
-        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(TVOLAP_ERR_CUDA);
+        // the host arrays above are copied before they go out of scope; the
+        // plan's tables are made on the group's stream
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess ||
+            cudaStreamSynchronize(g.st) != cudaSuccess)
+            return fail(TVOLAP_ERR_CUDA);
         ++gi;
     }
     *out = b;
@@ -183,6 +227,7 @@ int tvolap_batch_destroy(tvolap_batch_t b)
 {
     if (!b) return TVOLAP_OK;
     cudaStreamSynchronize(b->stream);
+    for (BatchGroup &g : b->groups) cudaStreamSynchronize(g.st);
     release(b);
     return TVOLAP_OK;
 }
@@ -247,9 +292,14 @@ int tvolap_batch_load_filters(tvolap_batch_t b, int i, const float *ir_dev, int 
     if (i < 0 || i >= (int)b->src.size()) return TVOLAP_ERR_ARG;
     const tvolap_batch_source &s = b->src[i];
     if (ir_len > 2 * (int64_t)s.L * s.M) return TVOLAP_ERR_ARG;
-    const BatchGroup &g = b->groups[b->group_of[i]];
-    return tvolap_load_bank(g.plan, g.slot_base[b->row_of[i]], s.n_filters, ir_dev, ir_len,
-                            ir_stride);
+    BatchGroup &g = b->groups[b->group_of[i]];
+    // on the group's stream, ordered after and before the batch stream's work
+    cudaError_t ce = fork_groups(b, &g);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    const int e = tvolap_load_bank(g.plan, g.slot_base[b->row_of[i]], s.n_filters, ir_dev, ir_len,
+                                   ir_stride);
+    ce = join_groups(b, &g);
+    return e != TVOLAP_OK ? e : cuda_status(ce);
 }
 
 int tvolap_batch_run(tvolap_batch_t b)
@@ -304,19 +354,15 @@ int tvolap_batch_autotune(tvolap_batch_t b, int reps, int *chosen)
         BatchGroup &g = b->groups[gi];
         float best = -1.f;
         int best_opt = 0;
+        if (fork_groups(b, &g) != cudaSuccess) status = TVOLAP_ERR_CUDA;
         for (int opt = 0; opt <= 5 && status == TVOLAP_OK; ++opt) {
             status = tvolap_set_option(g.plan, TVOLAP_OPT_MAC_STAGING, opt);
             if (status != TVOLAP_OK || g.max_out == 0) break;
-            auto one = [&]() {
-                return tvolap_process_ragged(g.plan, g.x, g.max_n, g.n_dev, g.ol_dev, g.parts_dev,
-                                             g.max_out, g.sched, nullptr, nullptr, g.nb, g.y,
-                                             g.max_out);
-            };
-            status = one();                                        // warm: workspaces, caches
+            status = ragged(g);                                    // warm: workspaces, caches
             if (status != TVOLAP_OK) break;
-            cudaEventRecord(e0, b->stream);
-            for (int r = 0; r < reps && status == TVOLAP_OK; ++r) status = one();
-            cudaEventRecord(e1, b->stream);
+            cudaEventRecord(e0, g.st);
+            for (int r = 0; r < reps && status == TVOLAP_OK; ++r) status = ragged(g);
+            cudaEventRecord(e1, g.st);
             if (cudaEventSynchronize(e1) != cudaSuccess) status = TVOLAP_ERR_CUDA;
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
@@ -325,6 +371,7 @@ int tvolap_batch_autotune(tvolap_batch_t b, int reps, int *chosen)
                 best_opt = opt;
             }
         }
+        if (join_groups(b, &g) != cudaSuccess && status == TVOLAP_OK) status = TVOLAP_ERR_CUDA;
         if (status == TVOLAP_OK) {
             status = tvolap_set_option(g.plan, TVOLAP_OPT_MAC_STAGING, best_opt);
             g.staging = best_opt;
