@@ -59,6 +59,11 @@ SMS, FP32_LANES = 152, 128
 # by the channel count (the traffic grows in proportion to it).
 MAC_TRAFFIC_BYTES = 2 * (309.679360e6 + 214.811648e6)
 
+# DRAM bytes (read + write) of one launch of the fused adjoint kernel at the
+# 16-channel differentiable workload: an ncu capture of the same kernel at 2
+# channels, scaled by the channel count.
+ADJ_TRAFFIC_BYTES = 8 * (369.795072e6 + 310.738688e6)
+
 
 def fp32_peak_tflops(mhz: float) -> float:
     return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
@@ -693,7 +698,8 @@ def run_adjoint(args):
                              "larger than the 129 MB L2; no flush"},
             "segmented_k32_ms_per_step": round(seg_ms, 4),
             "roofline": {"bound": "hbm", "achieved": round(adj_gbs, 1), "peak": hbm,
-                         "unit": "GB/s", "frac": round(adj_gbs / hbm, 4), "traffic": None,
+                         "unit": "GB/s", "frac": round(adj_gbs / hbm, 4),
+                         "traffic": ADJ_TRAFFIC_BYTES if C == 16 else None,
                          "kernel": "k_adjoint_mac_x (read P, write dP; X recomputed)"},
             "mac_params_gbs": round(fwd_gbs, 1),
             "stages_ms": {k: round(v, 4) for k, v in tot.items()},
