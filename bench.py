@@ -803,8 +803,10 @@ def run_batched(args):
         default_ms = per_ms = None
     else:
         default_ms = time_loop()
-        for p, *_, L in per:
-            p.set_option(1, tuned[L])
+        tiling = {B.group_info(g)[0]: B.group_tiling(g) for g in range(B.n_groups)}
+        for p, *_, L in per:                 # the batch's choices for the source's hop
+            p.set_option(1, tiling[L][0])
+            p.set_option(3, tiling[L][1])
         per_ms = time_loop()
     for p, *_ in per:
         p.check()
@@ -831,12 +833,15 @@ def run_batched(args):
                 "per_source_ms_per_step": round(per_ms, 4), "batched_ms_per_step": round(ms, 4),
                 "ratio": round(per_ms / ms, 3),
                 "per_source_default_staging_ms": round(default_ms, 4),
-                "note": "per-source loop with the staging chosen for its hop"},
+                "note": "per-source loop with the staging and transform CTA size chosen for "
+                        "its hop"},
             "roofline": {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1),
                          "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
                          "kernel": "whole step: Eq. 7 flops / replay time (lower bound on "
                                    "the multiply-accumulate kernels)"},
-            "autotune": {str(L): v for L, v in tuned.items()},
+            "autotune": {str(B.group_info(g)[0]): {"mac_staging": B.group_tiling(g)[0],
+                                                   "xform_threads": B.group_tiling(g)[1]}
+                         for g in range(B.n_groups)},
             "gpu_launches": launches * args.steps, "clocks": clocks, "cpu_baseline": cpu}
 
 

@@ -492,7 +492,13 @@ typedef enum tvolap_option {
        each call first waits for the previous call's events, adding their
        times up for tvolap_stage_times; 0 (default): off. Setting it (either
        value) clears the sums. */
-    TVOLAP_OPT_STAGE_TIMING = 2
+    TVOLAP_OPT_STAGE_TIMING = 2,
+    /* Threads per CTA of the offline transform kernels (forward transforms,
+       partition bank, inverse + overlap-add): 0 (default) or 256, 128, 64
+       (never fewer than one transform's 2L / 16 threads). Each transform runs
+       on 2L / 16 threads, so this sets how many transforms share a CTA and
+       its shared memory. Results do not depend on it. */
+    TVOLAP_OPT_XFORM_THREADS = 3
 } tvolap_option;
 
 /* Set a plan option (takes effect for the following calls). */
@@ -587,15 +593,22 @@ TVOLAP_API int tvolap_batch_capture(tvolap_batch_t b);
 
 /*
  * For every hop group, time each multiply-accumulate staging (0 .. 5) over
- * reps runs on the batch itself and keep the fastest; drops a captured graph.
- * chosen (may be NULL): host int [number of groups], the staging per group in
- * increasing hop order. Synchronises.
+ * reps runs on the batch itself and keep the fastest, then, with it, each
+ * CTA size of the transform kernels (TVOLAP_OPT_XFORM_THREADS 256, 128, 64:
+ * how many transforms share a CTA) and keep the fastest; drops a captured
+ * graph. chosen (may be NULL): host int [number of groups], the staging per
+ * group in increasing hop order (tvolap_batch_group_tiling gives both
+ * choices). Synchronises.
  */
 TVOLAP_API int tvolap_batch_autotune(tvolap_batch_t b, int reps, int *chosen);
 
 /* Set the multiply-accumulate staging of group g (-1: every group); drops a
    captured graph. */
 TVOLAP_API int tvolap_batch_set_staging(tvolap_batch_t b, int g, int staging);
+
+/* Group g's multiply-accumulate staging and transform CTA size (0 = default). */
+TVOLAP_API int tvolap_batch_group_tiling(tvolap_batch_t b, int g, int *mac_staging,
+                                         int *xform_threads);
 
 /* Number of hop groups, and group g's hop, sources and staging. */
 TVOLAP_API int tvolap_batch_groups(tvolap_batch_t b, int *n_groups);

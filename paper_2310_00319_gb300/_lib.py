@@ -104,6 +104,7 @@ SIGNATURES = {
     "tvolap_batch_set_staging": (c_int, [c_void_p, c_int, c_int]),
     "tvolap_batch_groups": (c_int, [c_void_p, P_int]),
     "tvolap_batch_group_info": (c_int, [c_void_p, c_int, P_int, P_int, P_int]),
+    "tvolap_batch_group_tiling": (c_int, [c_void_p, c_int, P_int, P_int]),
     "tvolap_batch_check": (c_int, [c_void_p]),
     # streaming server
     "tvolap_server_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int, c_int64,

@@ -118,8 +118,9 @@ class BatchedTvolap:
         self.run()
 
     def autotune(self, reps: int = 3) -> dict:
-        """Per hop group, keep the fastest multiply-accumulate staging.
-        Returns {L: staging}."""
+        """Per hop group, keep the fastest multiply-accumulate staging, then
+        the fastest transform CTA size. Returns {L: staging};
+        group_tiling(g) gives both choices."""
         ng = self.n_groups
         chosen = (ctypes.c_int * ng)()
         self._call("tvolap_batch_autotune", int(reps), chosen)
@@ -158,3 +159,10 @@ class BatchedTvolap:
         self._call("tvolap_batch_group_info", int(g), ctypes.byref(L), ctypes.byref(n),
                    ctypes.byref(st))
         return L.value, n.value, st.value
+
+    def group_tiling(self, g: int):
+        """(multiply-accumulate staging, transform CTA size; 0 = default) of
+        hop group g."""
+        st, th = ctypes.c_int(), ctypes.c_int()
+        self._call("tvolap_batch_group_tiling", int(g), ctypes.byref(st), ctypes.byref(th))
+        return st.value, th.value

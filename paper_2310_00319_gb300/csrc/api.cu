@@ -763,6 +763,11 @@ int tvolap_set_option(tvolap_t h, int option, int value)
         h->mac_variant = value;
         return TVOLAP_OK;
     }
+    if (option == TVOLAP_OPT_XFORM_THREADS) {
+        if (value != 0 && value != 64 && value != 128 && value != 256) return TVOLAP_ERR_ARG;
+        h->xform_threads = value;
+        return TVOLAP_OK;
+    }
     if (option == TVOLAP_OPT_STAGE_TIMING) {
         if (value != 0 && value != 1) return TVOLAP_ERR_ARG;
         cudaError_t e = timing_collect(h);

@@ -3,7 +3,8 @@
 // stream of its own, forked from the batch's stream at the start of a run and
 // joined back at its end, so the groups' kernels overlap on the GPU; the run
 // is captured as one CUDA graph of parallel branches. Per-group choice of the
-// multiply-accumulate staging by timing the variants on the batch itself.
+// multiply-accumulate staging and of the transforms' CTA size by timing the
+// variants on the batch itself.
 #include <algorithm>
 #include <map>
 #include <new>
@@ -17,7 +18,7 @@
 namespace {
 
 struct BatchGroup {
-    int L = 0, M = 0, staging = 0;
+    int L = 0, M = 0, staging = 0, xform_threads = 0;
     tvolap_t plan = nullptr;
     std::vector<int> src;                 // source indices, in row order
     std::vector<int> slot_base;           // first filter slot of each row
@@ -371,12 +372,35 @@ int tvolap_batch_autotune(tvolap_batch_t b, int reps, int *chosen)
                 best_opt = opt;
             }
         }
-        if (join_groups(b, &g) != cudaSuccess && status == TVOLAP_OK) status = TVOLAP_ERR_CUDA;
         if (status == TVOLAP_OK) {
             status = tvolap_set_option(g.plan, TVOLAP_OPT_MAC_STAGING, best_opt);
             g.staging = best_opt;
             if (chosen) chosen[gi] = best_opt;
         }
+        // then the transforms' CTA size (transforms per CTA), with that staging
+        float best_t = -1.f;
+        int best_th = 0;
+        const int ths[3] = {256, 128, 64};
+        for (int k = 0; k < 3 && status == TVOLAP_OK && g.max_out > 0; ++k) {
+            status = tvolap_set_option(g.plan, TVOLAP_OPT_XFORM_THREADS, ths[k]);
+            if (status == TVOLAP_OK) status = ragged(g);
+            if (status != TVOLAP_OK) break;
+            cudaEventRecord(e0, g.st);
+            for (int r = 0; r < reps && status == TVOLAP_OK; ++r) status = ragged(g);
+            cudaEventRecord(e1, g.st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) status = TVOLAP_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best_t < 0.f || ms < best_t) {
+                best_t = ms;
+                best_th = ths[k];
+            }
+        }
+        if (status == TVOLAP_OK && best_th > 0) {
+            status = tvolap_set_option(g.plan, TVOLAP_OPT_XFORM_THREADS, best_th);
+            g.xform_threads = best_th;
+        }
+        if (join_groups(b, &g) != cudaSuccess && status == TVOLAP_OK) status = TVOLAP_ERR_CUDA;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -415,6 +439,15 @@ int tvolap_batch_group_info(tvolap_batch_t b, int g, int *L, int *n_sources, int
     if (L) *L = b->groups[g].L;
     if (n_sources) *n_sources = (int)b->groups[g].src.size();
     if (staging) *staging = b->groups[g].staging;
+    return TVOLAP_OK;
+}
+
+int tvolap_batch_group_tiling(tvolap_batch_t b, int g, int *mac_staging, int *xform_threads)
+{
+    if (!b) return TVOLAP_ERR_STATE;
+    if (g < 0 || g >= (int)b->groups.size()) return TVOLAP_ERR_ARG;
+    if (mac_staging) *mac_staging = b->groups[g].staging;
+    if (xform_threads) *xform_threads = b->groups[g].xform_threads;
     return TVOLAP_OK;
 }
 

@@ -71,11 +71,21 @@ __host__ __device__ constexpr int lane_buf(int P) { return P + P / 16; }
 __device__ __forceinline__ int pa(int n) { return n + (n >> 4); }
 __device__ __forceinline__ int pb(int n) { return n ^ ((n >> 3) & 8); }
 
-// Dynamic shared memory of a lane kernel: one buffer per transform.
+// Dynamic shared memory of a lane kernel of `threads` threads: one buffer per
+// transform.
 template <int LG>
-inline size_t smem_lane()
+inline size_t smem_lane(int threads)
 {
-    return (size_t)Lane<(1 << LG)>::F * lane_buf(1 << LG) * sizeof(float2);
+    return (size_t)(threads / Lane<(1 << LG)>::T) * lane_buf(1 << LG) * sizeof(float2);
+}
+
+// Threads of a lane kernel's CTA for the plan option (0: the default 256), at
+// least one transform's T threads: 64, 128 or 256.
+template <int P>
+inline int lane_threads(int option)
+{
+    int th = option == 64 || option == 128 ? option : Lane<P>::THREADS;
+    return th < Lane<P>::T ? Lane<P>::T : th;
 }
 
 // dft8 (forward) of v[0..3] with v[4..7] zero: the first radix-2 layer of the

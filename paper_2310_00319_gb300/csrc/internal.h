@@ -40,6 +40,7 @@ struct tvolap_plan {
                                   // groups of <= 4 slots, 3: TMA, one group of <= 3 slots
                                   // per CTA, 4: as 3 with two bins per thread,
                                   // 5: as 0 with groups of <= 4 slots
+    int xform_threads;            // CTA size of the offline transform kernels (0: 256)
     int4 *ovf_list;               // groups the group kernel hands to the per-warp kernel
     int *ovf_count;
     int64_t ovf_cap;

@@ -239,7 +239,7 @@ cudaError_t launch_adjoint_mac_x(tvolap_plan *h, const float2 *G, int64_t g_firs
     }
     TVOLAP_DISPATCH(h->lgP, {
         constexpr int P = 1 << LG;
-        const size_t sm = smem_lane<LG>();
+        const size_t sm = smem_lane<LG>(Lane<P>::THREADS);
         cudaError_t e = set_smem(k_adjoint_mac_x<LG>, sm);
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)((q_count + Lane<P>::F - 1) / Lane<P>::F), (unsigned)h->n_out);

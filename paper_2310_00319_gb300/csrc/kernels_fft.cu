@@ -55,7 +55,8 @@ k_forward_signal(const float *__restrict__ x, int64_t N, int64_t x_stride, int L
                  const float2 *__restrict__ post, const float2 *__restrict__ tw,
                  float2 *__restrict__ X, int64_t t_first, Ragged rg)
 {
-    constexpr int P = 1 << LG, T = Lane<P>::T, F = Lane<P>::F;
+    constexpr int P = 1 << LG, T = Lane<P>::T;
+    const int F = blockDim.x / T;                      // transforms per CTA (launch's choice)
     extern __shared__ float2 sm[];
     const int f = threadIdx.x / T, j = threadIdx.x % T;
     float2 *buf = sm + f * lane_buf(P);
@@ -92,7 +93,8 @@ k_bank(const float *__restrict__ ir, int ir_len, int64_t ir_stride, int M, int L
        const float2 *__restrict__ rot, const float2 *__restrict__ post,
        const float2 *__restrict__ tw, float2 *__restrict__ bank_out)
 {
-    constexpr int P = 1 << LG, T = Lane<P>::T, F = Lane<P>::F;
+    constexpr int P = 1 << LG, T = Lane<P>::T;
+    const int F = blockDim.x / T;                      // transforms per CTA (launch's choice)
     extern __shared__ float2 sm[];
     const int f = threadIdx.x / T, j = threadIdx.x % T;
     float2 *buf = sm + f * lane_buf(P);
@@ -163,7 +165,8 @@ k_inverse_ola(const float2 *__restrict__ Y, int n_blocks, int L, int seg, int n_
               const float2 *__restrict__ rot, const float2 *__restrict__ post,
               const float2 *__restrict__ tw, Ragged rg, int n_outputs)
 {
-    constexpr int P = 1 << LG, T = Lane<P>::T, F = Lane<P>::F;
+    constexpr int P = 1 << LG, T = Lane<P>::T;
+    const int F = blockDim.x / T;                      // transforms per CTA (launch's choice)
     extern __shared__ float2 sm[];
     const int f = threadIdx.x / T, j = threadIdx.x % T;
     float2 *buf = sm + f * lane_buf(P);
@@ -431,11 +434,12 @@ cudaError_t launch_block_spectra(tvolap_plan *h, const float *x, int64_t N, int6
     if (total == 0) return cudaSuccess;
     TVOLAP_DISPATCH(h->lgP, {
         constexpr int P = 1 << LG;
-        const int64_t grid = (total + Lane<P>::F - 1) / Lane<P>::F;
-        const size_t sm = smem_lane<LG>();
-        cudaError_t e = set_smem(k_forward_signal<LG>, sm);
+        const int th = lane_threads<P>(h->xform_threads), F = th / Lane<P>::T;
+        const int64_t grid = (total + F - 1) / F;
+        const size_t sm = smem_lane<LG>(th);
+        cudaError_t e = set_smem(k_forward_signal<LG>, smem_lane<LG>(Lane<P>::THREADS));
         if (e != cudaSuccess) return e;
-        k_forward_signal<LG><<<(unsigned)grid, Lane<P>::THREADS, sm, h->stream>>>(
+        k_forward_signal<LG><<<(unsigned)grid, th, sm, h->stream>>>(
             x, N, x_stride, h->L, n_blocks, total, h->win, h->rot, h->post, h->tw, X, t_first, rg);
     });
     return cudaGetLastError();
@@ -449,11 +453,12 @@ cudaError_t launch_bank(tvolap_plan *h, int first_slot, int count, const float *
     float2 *dst = h->bank + (int64_t)first_slot * h->M * h->P;
     TVOLAP_DISPATCH(h->lgP, {
         constexpr int P = 1 << LG;
-        const int64_t grid = (total + Lane<P>::F - 1) / Lane<P>::F;
-        const size_t sm = smem_lane<LG>();
-        cudaError_t e = set_smem(k_bank<LG>, sm);
+        const int th = lane_threads<P>(h->xform_threads), F = th / Lane<P>::T;
+        const int64_t grid = (total + F - 1) / F;
+        const size_t sm = smem_lane<LG>(th);
+        cudaError_t e = set_smem(k_bank<LG>, smem_lane<LG>(Lane<P>::THREADS));
         if (e != cudaSuccess) return e;
-        k_bank<LG><<<(unsigned)grid, Lane<P>::THREADS, sm, h->stream>>>(
+        k_bank<LG><<<(unsigned)grid, th, sm, h->stream>>>(
             ir, ir_len, ir_stride, h->M, h->L, total, h->rot, h->post, h->tw, dst);
     });
     return cudaGetLastError();
@@ -475,7 +480,7 @@ cudaError_t launch_bank_raw(int lgP, int L, int M, int64_t count, const float *i
     TVOLAP_DISPATCH(lgP, {
         constexpr int P = 1 << LG;
         const int64_t grid = (total + Lane<P>::F - 1) / Lane<P>::F;
-        const size_t sm = smem_lane<LG>();
+        const size_t sm = smem_lane<LG>(Lane<P>::THREADS);
         cudaError_t e = set_smem(k_bank<LG>, sm);
         if (e != cudaSuccess) return e;
         k_bank<LG><<<(unsigned)grid, Lane<P>::THREADS, sm, st>>>(ir, ir_len, ir_stride, M, L, total,
@@ -494,25 +499,26 @@ cudaError_t launch_inverse_ola(tvolap_plan *h, const float2 *Y, int n_blocks, fl
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
     TVOLAP_DISPATCH(h->lgP, {
         constexpr int P = 1 << LG;
-        const size_t sm = smem_lane<LG>();
-        cudaError_t e = set_smem(k_inverse_ola<LG>, sm);
+        const int th = lane_threads<P>(h->xform_threads), F = th / Lane<P>::T;
+        const size_t sm = smem_lane<LG>(th);
+        cudaError_t e = set_smem(k_inverse_ola<LG>, smem_lane<LG>(Lane<P>::THREADS));
         if (e != cudaSuccess) return e;
-        static int per_sm = 0;                         // resident CTAs (per kernel instance)
-        if (per_sm == 0) {
+        static int per_sm[3] = {0, 0, 0};              // resident CTAs per launch size
+        const int slot = th == 64 ? 0 : th == 128 ? 1 : 2;
+        if (per_sm[slot] == 0) {
             int n = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_inverse_ola<LG>,
-                                                              Lane<P>::THREADS, sm);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_inverse_ola<LG>, th, sm);
             if (e != cudaSuccess) return e;
-            per_sm = n > 0 ? n : 1;
+            per_sm[slot] = n > 0 ? n : 1;
         }
         const int64_t seg = ola_seg((out_len + h->L - 1) / h->L, n_outputs,
-                                    (int64_t)sms * per_sm * Lane<P>::F);
+                                    (int64_t)sms * per_sm[slot] * F);
         if (seg > 0x7fffffffLL / h->L) return cudaErrorInvalidValue;
         const int64_t n_seg = (out_len + seg * h->L - 1) / (seg * h->L);
         if (n_seg * n_outputs > 0x7fffffffLL) return cudaErrorInvalidValue;
         const int64_t units = n_seg * n_outputs;
-        const int64_t grid = (units + Lane<P>::F - 1) / Lane<P>::F;
-        k_inverse_ola<LG><<<(unsigned)grid, Lane<P>::THREADS, sm, h->stream>>>(
+        const int64_t grid = (units + F - 1) / F;
+        k_inverse_ola<LG><<<(unsigned)grid, th, sm, h->stream>>>(
             Y, n_blocks, h->L, (int)seg, (int)n_seg, y, out_len, y_stride, h->rot, h->post, h->tw,
             rg, n_outputs);
     });

@@ -48,7 +48,7 @@ def n_blocks_for(out_len: int, L: int) -> int:
     return 0 if out_len <= 0 else (out_len - 1) // L + 2
 
 
-OPT_MAC_STAGING, OPT_STAGE_TIMING = 1, 2
+OPT_MAC_STAGING, OPT_STAGE_TIMING, OPT_XFORM_THREADS = 1, 2, 3
 
 
 class Plan:
@@ -119,7 +119,8 @@ class Plan:
         1 = cp.async, 2 = TMA groups of up to four filters, 3 = one TMA group
         per CTA, 4 = as 3 with two bins per thread, 5 = as 0 with up to four
         filters per group. TVOLAP_OPT_STAGE_TIMING (2): 1 = time the three
-        stages of process_block (see stage_times)."""
+        stages of process_block (see stage_times). TVOLAP_OPT_XFORM_THREADS
+        (3): threads per CTA of the offline transforms, 0 (256), 128 or 64."""
         self._call("tvolap_set_option", int(option), int(value))
 
     def stage_times(self):

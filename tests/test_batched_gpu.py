@@ -86,6 +86,9 @@ def test_autotune_keeps_results():
     chosen = B.autotune(reps=1)
     assert set(chosen) == {s.L for s in S}
     assert [B.group_info(g)[2] for g in range(B.n_groups)] == [chosen[L] for L in sorted(chosen)]
+    for g in range(B.n_groups):
+        st, th = B.group_tiling(g)
+        assert st == B.group_info(g)[2] and th in (64, 128, 256)
     B.run()
     B.check()
     for i in range(len(S)):

@@ -241,6 +241,32 @@ def test_mac_staging_variants_agree_bitwise(L, n_slots, interp):
     _assert_close(y0, _ref(wl), "variants")
 
 
+@pytest.mark.parametrize("L", [16, 64, 256, 512, 1024])
+def test_transform_cta_size_changes_no_result(L):
+    """TVOLAP_OPT_XFORM_THREADS (256, 128, 64 threads per CTA of the offline
+    transforms) only regroups transforms into CTAs: outputs, block spectra and
+    bank spectra are the same bit for bit."""
+    dev = _dev()
+    from paper_2310_00319_gb300.tvolap import OPT_XFORM_THREADS
+    wl = W.random_case(230 + L, L=L, ir_len=3 * L + 7, N=40 * L + 3, n_in=2, n_out=3,
+                       n_slots=3, out_len=41 * L, out_to_in=[0, 1, 1])
+    from paper_2310_00319_gb300 import Plan
+    runs = []
+    for th in (0, 128, 64):
+        plan = Plan(wl.L, wl.M, n_in=wl.n_in, n_out=wl.n_out, out_to_in=wl.out_to_in,
+                    n_slots=wl.irs.shape[0], device=dev)
+        plan.set_option(OPT_XFORM_THREADS, th)             # before the bank transform
+        plan.load_bank(0, _t(wl.irs, dev))
+        y = _run_signal(wl, dev, plan)
+        X = plan.block_spectra(_t(wl.x, dev), 0, wl.n_blocks).cpu().numpy()
+        H = plan.bank_spectra(1).cpu().numpy()
+        runs.append((y, X, H))
+        plan.close()
+    for r in runs[1:]:
+        for a, b in zip(r, runs[0]):
+            np.testing.assert_array_equal(a, b)
+
+
 def test_staging_option_range():
     """TVOLAP_OPT_MAC_STAGING takes 0 .. 5, TVOLAP_OPT_STAGE_TIMING 0 or 1;
     other values and options are refused."""
@@ -252,7 +278,9 @@ def test_staging_option_range():
         plan.set_option(1, v)
     for v in (1, 0):
         plan.set_option(2, v)
-    for opt, v in [(1, -1), (1, 6), (2, 2), (2, -1), (3, 0), (0, 0)]:
+    for v in (0, 64, 128, 256):
+        plan.set_option(3, v)
+    for opt, v in [(1, -1), (1, 6), (2, 2), (2, -1), (3, 32), (3, 512), (4, 0), (0, 0)]:
         with pytest.raises(TvolapError):
             plan.set_option(opt, v)
 
