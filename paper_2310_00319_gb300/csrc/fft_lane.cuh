@@ -149,12 +149,10 @@ __device__ __forceinline__ void powers(float2 w1, float2 (&w)[R])
     }
 }
 
-// Butterfly b of stage (Ns, R): its R inputs from the buffer (layout A after
-// the first stage, B after a middle one), rotated by the stage's twiddles,
-// transformed.
-template <int P, int Ns, bool INV>
-__device__ __forceinline__ void lane_bfly(const float2 *buf, int b, const float2 *__restrict__ tw,
-                                          float2 (&v)[LStage<P, Ns>::R])
+// The R inputs of butterfly b of stage (Ns, R) from the buffer (layout A
+// after the first stage, B after a middle one).
+template <int P, int Ns>
+__device__ __forceinline__ void lane_load(const float2 *buf, int b, float2 (&v)[LStage<P, Ns>::R])
 {
     constexpr int R = LStage<P, Ns>::R, stride = P / R;
     if constexpr (Ns == 8) {                           // input in layout A
@@ -177,13 +175,39 @@ __device__ __forceinline__ void lane_bfly(const float2 *buf, int b, const float2
             for (int r = 0; r < R; ++r) v[r] = buf[pb(b + r * stride)];
         }
     }
+}
+
+// The stage's twiddles w[r] = e^{-2 pi i r k / (Ns R)} of butterfly index k = b mod Ns.
+template <int P, int Ns>
+__device__ __forceinline__ void lane_twiddles(int b, const float2 *__restrict__ tw,
+                                              float2 (&w)[LStage<P, Ns>::R])
+{
+    powers<LStage<P, Ns>::R>(__ldg(tw + tw_offset(P, Ns) + (b & (Ns - 1))), w);
+}
+
+// Butterfly v (inputs loaded) rotated by the twiddles w, transformed.
+template <int P, int Ns, bool INV>
+__device__ __forceinline__ void lane_apply(float2 (&v)[LStage<P, Ns>::R],
+                                           const float2 (&w)[LStage<P, Ns>::R])
+{
+    constexpr int R = LStage<P, Ns>::R;
     if constexpr (Ns > 1) {
-        float2 w[R];
-        powers<R>(__ldg(tw + tw_offset(P, Ns) + (b & (Ns - 1))), w);
 #pragma unroll
         for (int r = 1; r < R; ++r) v[r] = INV ? cmulc(v[r], w[r]) : cmul(v[r], w[r]);
     }
     dftR<R, INV>(v);
+}
+
+// Butterfly b of stage (Ns, R): loaded, rotated by its twiddles, transformed.
+template <int P, int Ns, bool INV>
+__device__ __forceinline__ void lane_bfly(const float2 *buf, int b, const float2 *__restrict__ tw,
+                                          float2 (&v)[LStage<P, Ns>::R])
+{
+    constexpr int R = LStage<P, Ns>::R;
+    lane_load<P, Ns>(buf, b, v);
+    float2 w[R];
+    if constexpr (Ns > 1) lane_twiddles<P, Ns>(b, tw, w);
+    lane_apply<P, Ns, INV>(v, w);
 }
 
 // Outputs of butterfly b of a non-last stage: the first stage's in layout A,
@@ -222,8 +246,19 @@ __device__ __forceinline__ void lane_middle(float2 *buf, int j, int f, const flo
     if constexpr (!LStage<P, Ns>::LAST) {
         constexpr int R = LStage<P, Ns>::R, NB = LStage<P, Ns>::NB, T = Lane<P>::T;
         float2 v[NB][R];
+        if constexpr (T % Ns == 0) {
+            // every butterfly j + T u has the twiddle index j mod Ns: one set for all
+            float2 w[R];
+            lane_twiddles<P, Ns>(j, tw, w);
 #pragma unroll
-        for (int u = 0; u < NB; ++u) lane_bfly<P, Ns, INV>(buf, j + T * u, tw, v[u]);
+            for (int u = 0; u < NB; ++u) {
+                lane_load<P, Ns>(buf, j + T * u, v[u]);
+                lane_apply<P, Ns, INV>(v[u], w);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < NB; ++u) lane_bfly<P, Ns, INV>(buf, j + T * u, tw, v[u]);
+        }
         lane_sync<T>(f);
 #pragma unroll
         for (int u = 0; u < NB; ++u) lane_store<P, Ns>(buf, j + T * u, v[u]);
