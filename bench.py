@@ -382,6 +382,7 @@ def run_ours(args):
         out["e2e"] = run_e2e(args, plan, wl, dev, stream)
         out["vs_per_source"] = run_per_source(args, wl, dev, stream, ms_per_step)
         out["stream"] = run_stream(args, wl, dev, stream)
+        out["static_scratch"] = run_static(args, wl, dev, stream)
         # the same streaming ticks at 4x the channels: the tick reads about
         # 296 MB of delay line and filter spectra, more than the L2 holds
         from synth import workloads as W
@@ -588,6 +589,51 @@ def run_stream_only(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"plain_at_scale_streaming_{args.channels}ch_L256_M94"},
             "roofline": dict(r["mac_roofline"], traffic=None), "stream": r}
+
+
+def run_static(args, wl, dev, stream, reps=10):
+    """tvolap_process_signal_static (its scratch in the library's fixed device
+    array, no allocation) against tvolap_process_signal (workspace from
+    cudaMalloc) on two channels of the default workload: the largest slice
+    whose block spectra fit the 32 MiB array."""
+    import torch
+    from paper_2310_00319_gb300 import Plan
+    from paper_2310_00319_gb300 import _lib as L_
+    from paper_2310_00319_gb300.tvolap import _ptr
+    ch = 2
+    p = Plan(wl.L, wl.M, n_in=ch, n_out=ch, n_slots=wl.irs.shape[0], device=dev)
+    p.load_bank(0, torch.from_numpy(wl.irs).to(dev))
+    x = torch.from_numpy(wl.x[:ch]).to(dev)
+    sa, sb, sal = (torch.from_numpy(a[:ch]).to(dev) for a in (wl.sched_a, wl.sched_b,
+                                                             wl.sched_alpha))
+    y = torch.empty((ch, wl.out_len), dtype=torch.float32, device=dev)
+    N = wl.N
+
+    def static():
+        L_.check(p.lib.tvolap_process_signal_static(
+            p.h, _ptr(x), N, N, _ptr(sa), _ptr(sb), _ptr(sal), sa.shape[1], _ptr(y),
+            wl.out_len, wl.out_len), "tvolap_process_signal_static")
+
+    def plain():
+        p.process_signal(x, sa, sb, sal, out_len=wl.out_len, out=y)
+
+    res = {}
+    for name, fn in (("static_ms", static), ("process_signal_ms", plain)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        res[name] = round(a.elapsed_time(b) / reps, 4)
+    p.check()
+    p.close()
+    return {"channels": ch, "samples_per_channel": wl.out_len, **res,
+            "note": "the static entry point runs the cp.async multiply-accumulate (no scratch "
+                    "beyond the fixed array)"}
 
 
 # --------------------------------------------------------------------------- adjoint
