@@ -6,9 +6,11 @@
 //   k_forward_stream    one new block per input into the delay line
 //   k_inverse_stream    one block per output, overlap-add against the state
 // Every transform is P = 2L complex points (see fft_core.cuh). The offline
-// forward, bank and inverse kernels run T = P/16 threads per transform with
-// sixteen values each (fft_lane.cuh); the others run T = P/8 threads per
-// transform (fft_block.cuh). F transforms share a 256-thread CTA.
+// forward, bank and inverse kernels and the streaming inverse run T = P/16
+// threads per transform with sixteen values each (fft_lane.cuh); the
+// streaming forward (where one transform's latency counts) and the adjoint
+// transforms run T = P/8 threads per transform (fft_block.cuh). F transforms
+// share a CTA.
 #include "fft_block.cuh"
 #include "fft_lane.cuh"
 #include "internal.h"
@@ -344,23 +346,64 @@ k_forward_stream(const float *__restrict__ in, float *__restrict__ hist, int L, 
     }
 }
 
-// Streaming inverse: output block -> L samples, with the 3L pending sums.
+// Streaming inverse: output block -> L samples, with the 3L pending sums st of
+// the output. Thread j owns the sample pairs 2 (j + T i) + {0, 1}, i < 4, of
+// each hop of the frame, and so the same positions of the pending sums: it
+// reads its 12 pending pairs, adds this block's contributions in hop order and
+// writes its output pairs and new pending pairs (the offline kernel's order).
 template <int LG>
-__global__ void __launch_bounds__(Geo<(1 << LG)>::THREADS)
+__global__ void __launch_bounds__(Lane<(1 << LG)>::THREADS)
 k_inverse_stream(const float2 *__restrict__ Ys, float *__restrict__ ola, float *__restrict__ out,
                  int L, int n_out, const float2 *__restrict__ rot, const float2 *__restrict__ post,
                  const float2 *__restrict__ tw)
 {
-    constexpr int P = 1 << LG, T = Geo<P>::T, F = Geo<P>::F;
+    constexpr int P = 1 << LG, T = Lane<P>::T;
+    const int F = blockDim.x / T;
     extern __shared__ float2 sm[];
     const int f = threadIdx.x / T, j = threadIdx.x % T;
-    float2 *A = sm + f * P, *B = sm + (F + f) * P;
+    float2 *buf = sm + f * lane_buf(P);
     const int o = blockIdx.x * F + f;
     const bool active = o < n_out;
     const float2 *Yo = Ys + (int64_t)(active ? o : 0) * P;
     float *st = ola + (int64_t)(active ? o : 0) * 3 * L;
     float *ou = out + (int64_t)(active ? o : 0) * L;
-    inverse_stream_block<P>(A, B, j, active, [&](int k) { return Yo[k]; }, st, ou, rot, post, tw);
+    const bool pairs = (reinterpret_cast<uintptr_t>(ou) & 7) == 0;
+    float2 pend[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            pend[c][i] = active ? *reinterpret_cast<const float2 *>(st + c * L + 2 * (j + T * i))
+                                : make_float2(0.f, 0.f);
+    inverse_lane<P>(buf, j, f, [&](int k) { return active ? Yo[k] : make_float2(0.f, 0.f); }, rot,
+                    post, tw, [&](int q, float2 v) {
+        const int c = q >> 2, i = q & 3;
+        if (c == 0) {
+            const float2 fin = cadd(pend[0][i], v);
+            const int n = 2 * (j + T * i);
+            if (active) {
+                if (pairs) {
+                    *reinterpret_cast<float2 *>(ou + n) = fin;
+                } else {
+                    ou[n] = fin.x;
+                    ou[n + 1] = fin.y;
+                }
+            }
+        } else if (c == 1) {
+            pend[0][i] = cadd(pend[1][i], v);
+        } else if (c == 2) {
+            pend[1][i] = cadd(pend[2][i], v);
+        } else {
+            pend[2][i] = v;
+        }
+    });
+    if (active) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                *reinterpret_cast<float2 *>(st + c * L + 2 * (j + T * i)) = pend[c][i];
+    }
 }
 
 // Output hops per segment of the offline inverse. Each segment also
@@ -591,11 +634,12 @@ cudaError_t launch_inverse_stream(tvolap_plan *h, float *out, const float2 *Ys, 
     if (n_outputs == 0) return cudaSuccess;
     TVOLAP_DISPATCH(h->lgP, {
         constexpr int P = 1 << LG;
-        const int grid = (n_outputs + Geo<P>::F - 1) / Geo<P>::F;
-        const size_t sm = smem_fft<LG>();
+        constexpr int TH = Lane<P>::T < 32 ? 32 : Lane<P>::T, F = TH / Lane<P>::T;
+        const int grid = (n_outputs + F - 1) / F;
+        const size_t sm = smem_lane<LG>(TH);
         cudaError_t e = set_smem(k_inverse_stream<LG>, sm);
         if (e != cudaSuccess) return e;
-        k_inverse_stream<LG><<<grid, Geo<P>::THREADS, sm, h->stream>>>(
+        k_inverse_stream<LG><<<grid, TH, sm, h->stream>>>(
             Ys, ola, out, h->L, n_outputs, h->rot, h->post, h->tw);
     });
     return cudaGetLastError();
