@@ -61,7 +61,7 @@ struct LsuArgs {
 
 template <int R, int D, int NS>
 __device__ __forceinline__ void lsu_run(const LsuArgs &g, int tf, int m_end, const RunSlots<R> &rs,
-                                        float2 (&acc)[R])
+                                        CAcc (&acc)[R])
 {
     const float2 zero = make_float2(0.f, 0.f);
     const int64_t MP = (int64_t)g.M * g.P;
@@ -86,7 +86,7 @@ __device__ __forceinline__ void lsu_run(const LsuArgs &g, int tf, int m_end, con
     for (int r = 0; r < R; ++r) {
         const int t = tf + 2 * r;
         xw[r] = (t < g.n_blocks) ? __ldg(g.Xc + (int64_t)t * P) : zero;
-        acc[r] = zero;
+        acc[r] = cacc_zero();
     }
 #pragma unroll
     for (int q = 0; q < D; ++q) issue(q);
@@ -126,7 +126,7 @@ __device__ __forceinline__ void lsu_process_run(const LsuArgs &g, int tf)
     }
     int m_end = (tf + 2 * (R - 1)) / 2 + 1;     // partitions with t - 2m >= 0 for some block
     if (m_end > g.Mo) m_end = g.Mo;
-    float2 acc[R];
+    CAcc acc[R];
     if (rs.ns == 1) {
         lsu_run<R, D, 1>(g, tf, m_end, rs, acc);
     } else if (rs.ns == 2) {
@@ -137,7 +137,7 @@ __device__ __forceinline__ void lsu_process_run(const LsuArgs &g, int tf)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int t = tf + 2 * r;
-        if (t < g.n_blocks) g.Yo[(int64_t)t * g.P] = acc[r];
+        if (t < g.n_blocks) g.Yo[(int64_t)t * g.P] = cacc_value(acc[r]);
     }
 }
 

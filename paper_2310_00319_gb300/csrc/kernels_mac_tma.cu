@@ -135,7 +135,7 @@ __device__ __forceinline__ void issue_chunk(const TmaArgs &g, const int (&sl)[MA
 // One chunk of D steps from stage buffer st; GUARD: the chunk may pass m_end.
 template <int R, int NS, bool GUARD>
 __device__ __forceinline__ void tma_chunk(const float2 *st, int c, int cu, int m_end,
-                                          const RunSlots<R> &rs, float2 (&xw)[R], float2 (&acc)[R])
+                                          const RunSlots<R> &rs, float2 (&xw)[R], CAcc (&acc)[R])
 {
     constexpr int D = TMA_D;
 #pragma unroll
@@ -154,7 +154,7 @@ __device__ __forceinline__ void tma_chunk(const float2 *st, int c, int cu, int m
 
 template <int R, int NS>
 __device__ __forceinline__ void tma_run(const TmaArgs &g, Pipe &pp, int tf, int m_end,
-                                        const RunSlots<R> &rs, float2 (&acc)[R])
+                                        const RunSlots<R> &rs, CAcc (&acc)[R])
 {
     constexpr int D = TMA_D;
     const int lane = g.lane;
@@ -168,7 +168,6 @@ __device__ __forceinline__ void tma_run(const TmaArgs &g, Pipe &pp, int tf, int 
         if (nchunks > 1) issue_chunk<NS>(g, rs.sl, tf, 1, 1);
     }
     float2 xw[R];
-    const float2 zero = make_float2(0.f, 0.f);
     if (!mbar_wait(g.bar, pp.phase & 1u)) {
         pp.ok = false;
         return;
@@ -178,7 +177,7 @@ __device__ __forceinline__ void tma_run(const TmaArgs &g, Pipe &pp, int tf, int 
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         xw[r] = g.win[r * 32 + lane];
-        acc[r] = zero;
+        acc[r] = cacc_zero();
     }
     constexpr int CU = (R >= D) ? R / D : 1;        // chunks per register rotation
     for (int c0 = 0; c0 < nchunks; c0 += CU) {
@@ -222,7 +221,7 @@ __device__ __forceinline__ void tma_process_run(const TmaArgs &g, Pipe &pp, int 
     }
     int m_end = (tf + 2 * (R - 1)) / 2 + 1;     // partitions with t - 2m >= 0 for some block
     if (m_end > g.M) m_end = g.M;
-    float2 acc[R];
+    CAcc acc[R];
     if (rs.ns == 1) {
         tma_run<R, 1>(g, pp, tf, m_end, rs, acc);
     } else if (rs.ns == 2) {
@@ -234,7 +233,7 @@ __device__ __forceinline__ void tma_process_run(const TmaArgs &g, Pipe &pp, int 
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int t = tf + 2 * r;
-        if (t < g.n_blocks) g.Yo[(int64_t)t * g.P] = acc[r];
+        if (t < g.n_blocks) g.Yo[(int64_t)t * g.P] = cacc_value(acc[r]);
     }
 }
 
@@ -341,7 +340,7 @@ struct GroupGeo {
     static constexpr int HSTAGE_ROWS = NSM * TMA_D;
     static constexpr int BYTES = 256 + (XRING + NSTAGE * HSTAGE_ROWS) * ROW_BYTES * BPL;
     // CTAs per SM the registers must allow
-    static constexpr int MIN_CTAS = BPL == 2 ? (NSM <= 3 ? 3 : 2) : (NSM <= 3 ? 4 : 3);
+    static constexpr int MIN_CTAS = BPL == 2 ? 2 : 3;
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
@@ -359,6 +358,8 @@ static_assert(sizeof(GroupSmem<4>) <= 256, "group header must fit its 256 bytes"
 
 __device__ __forceinline__ int ring_slot(int j) { return j & (XRING - 1); }
 
+__device__ __forceinline__ float4 pack2(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
 // the lane's BPL adjacent bins of one staged row
 template <int BPL>
 __device__ __forceinline__ void ld_bins(const float2 *p, float2 (&v)[BPL])
@@ -375,7 +376,7 @@ __device__ __forceinline__ void ld_bins(const float2 *p, float2 (&v)[BPL])
 template <int NS, int NSM, int BPL>
 __device__ __forceinline__ void group_chunk(const float2 *xs, const float2 *const (&hb)[NSM],
                                             int c, const RunSlots<TMA_R, NSM> &rs,
-                                            float2 (&xw)[TMA_R][BPL], float2 (&acc)[TMA_R][BPL])
+                                            float2 (&xw)[TMA_R][BPL], CAcc (&acc)[TMA_R][BPL])
 {
     constexpr int D = TMA_D, R = TMA_R, ROWB = 32 * BPL;
 #pragma unroll
@@ -394,7 +395,7 @@ template <int NS, int NSM, int BPL>
 __device__ __forceinline__ bool group_consume(GroupSmem<NSM> *gs, const float2 *xring,
                                               const float2 *hst, int w, int lane, int nchunks,
                                               int m_end, const RunSlots<TMA_R, NSM> &rs,
-                                              const int (&idx)[NSM], float2 (&acc)[TMA_R][BPL])
+                                              const int (&idx)[NSM], CAcc (&acc)[TMA_R][BPL])
 {
     constexpr int D = TMA_D, R = TMA_R, ROWB = 32 * BPL;
     float2 xw[R][BPL];
@@ -404,7 +405,7 @@ __device__ __forceinline__ bool group_consume(GroupSmem<NSM> *gs, const float2 *
     for (int r = 0; r < R; ++r) {
         ld_bins<BPL>(xring + ring_slot(R * w + 7 + r) * ROWB + lane * BPL, xw[r]);
 #pragma unroll
-        for (int b = 0; b < BPL; ++b) acc[r][b] = make_float2(0.f, 0.f);
+        for (int b = 0; b < BPL; ++b) acc[r][b] = cacc_zero();
     }
     for (int c = 0; c < nchunks; ++c) {
         const int q = c % NSTAGE;
@@ -574,7 +575,7 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
     }
     int m_end = (tf + 2 * (R - 1)) / 2 + 1;
     if (m_end > M) m_end = M;
-    float2 acc[R][BPL];
+    CAcc acc[R][BPL];
     bool ok;
     if (rs.ns == 1)
         ok = group_consume<1, NSM, BPL>(gs, xring, hst, w, lane, nchunks, m_end, rs, idx, acc);
@@ -595,9 +596,9 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
         if (t < n_blocks) {
             if constexpr (BPL == 2)
                 *reinterpret_cast<float4 *>(Yo + (int64_t)t * P) =
-                    make_float4(acc[r][0].x, acc[r][0].y, acc[r][1].x, acc[r][1].y);
+                    pack2(cacc_value(acc[r][0]), cacc_value(acc[r][1]));
             else
-                Yo[(int64_t)t * P] = acc[r][0];
+                Yo[(int64_t)t * P] = cacc_value(acc[r][0]);
         }
     }
 }
@@ -608,8 +609,9 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
 // counter, so a group's first copies are issued while the CTA still computes
 // the previous group. Two group contexts alternate: each has its half of a
 // two-part X ring, its window barrier and the group's description (output,
-// tile, slots, and the 32 blocks' schedule entries, so the consumers set up
-// their runs from shared memory). The filter stages and their full/empty
+// tile, the staged slots and, per run, its slots' places among them and its
+// blocks' mix weights: the loader warp derives them, eight lanes per run, so
+// a consumer's set-up is a few shared-memory reads). The filter stages and their full/empty
 // barriers are shared and run on through the groups; with PSTAGE stages the
 // loader keeps up to PSTAGE chunks in flight. The loader fills context k for
 // group i as soon as the consumers have released it (group i - 2 done:
@@ -630,16 +632,17 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
 
 struct PersistCtx {
     int T0, o, k0, cin, n_blocks, M, nchunks, n_active, U, end;
-    int slot[4];
-    int a[GROUP_ROWS], b[GROUP_ROWS];          // checked schedule entries of blocks T0 + 2i
-    float al[GROUP_ROWS];
+    int slot[4];                               // the group's staged slots
+    int ns[GW];                                // per run: distinct slots,
+    int idx[GW][4];                            // their places in slot[] (order of first use),
+    float2 w[GW][TMA_R][3];                    // weights of its slots 1.. per block, as (w, w)
 };
 
 struct PersistSmem {
     uint64_t win[2], ready[2], freed[2], full[5], empty[5];
     PersistCtx ctx[2];
 };
-constexpr int PERSIST_HEAD = 1024;
+constexpr int PERSIST_HEAD = 2048;
 static_assert(sizeof(PersistSmem) <= PERSIST_HEAD, "persistent header must fit its bytes");
 
 // PST filter stages (at most 5: the barrier arrays), ring halves of PRING rows.
@@ -666,7 +669,7 @@ template <int NS, int NSM, int BPL, int PST>
 __device__ __forceinline__ bool persist_consume(PersistSmem *ps, const float2 *xring, const float2 *hst,
                                                 int w, int lane, int nchunks, int m_end, uint32_t &seq,
                                                 const RunSlots<TMA_R, NSM> &rs, const int (&idx)[NSM],
-                                                float2 (&acc)[TMA_R][BPL])
+                                                CAcc (&acc)[TMA_R][BPL])
 {
     using G = PersistGeo<NSM, BPL, PST>;
     constexpr int D = TMA_D, R = TMA_R, ROWB = 32 * BPL, NST = PST;
@@ -679,7 +682,7 @@ __device__ __forceinline__ bool persist_consume(PersistSmem *ps, const float2 *x
     for (int r = 0; r < R; ++r) {
         ld_bins<BPL>(xring + pring_slot<G::PRING>(R * w + 7 + r) * ROWB + lane * BPL, xw[r]);
 #pragma unroll
-        for (int b = 0; b < BPL; ++b) acc[r][b] = make_float2(0.f, 0.f);
+        for (int b = 0; b < BPL; ++b) acc[r][b] = cacc_zero();
     }
     for (int c = 0; c < nchunks; ++c, ++seq) {
         const int q = seq % NST;
@@ -857,9 +860,6 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
             if (m_all > cur.M) m_all = cur.M;
             const int nchunks = (m_all + D - 1) / D;
             const int k0 = cur.tile * ROWB, cin = out_to_in[cur.o];
-            cx.a[lane] = a;
-            cx.b[lane] = b;
-            cx.al[lane] = al;
             if (lane == 0) {
                 cx.T0 = cur.T0;
                 cx.o = cur.o;
@@ -871,6 +871,41 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
                 cx.n_active = n_active;
                 cx.U = U;
                 cx.end = 0;
+            }
+            __syncwarp();
+            {
+                // run w = lanes 8w .. 8w + 7 (block r = lane mod 8): its slots in
+                // order of first use (blocks in order, a before b; a slot only where
+                // its weight is nonzero), as run_slots_core finds them
+                const int sh = lane & ~(R - 1), r = lane & (R - 1), run = lane / R;
+                bool ra = (al != 1.f) || (a == b), rb = (al != 0.f) && (b != a);
+                int sl[NSM], ns = 0;
+#pragma unroll
+                for (int j = 0; j < NSM; ++j) {
+                    const unsigned m = (__ballot_sync(0xffffffffu, ra || rb) >> sh) & 0xffu;
+                    const int v = __shfl_sync(0xffffffffu, ra ? a : b, sh + (m ? __ffs(m) - 1 : 0));
+                    sl[j] = m ? v : 0;
+                    if (m) {
+                        ns = j + 1;
+                        ra = ra && (a != v);
+                        rb = rb && (b != v);
+                    }
+                }
+                if (r == 0) {
+                    cx.ns[run] = ns;
+#pragma unroll
+                    for (int j = 0; j < NSM; ++j) {
+                        int q0 = 0;
+                        for (int q = 0; q < U; ++q)
+                            if (j < ns && cx.slot[q] == sl[j]) q0 = q;
+                        cx.idx[run][j] = q0;
+                    }
+                }
+#pragma unroll
+                for (int j = 1; j < NSM; ++j) {
+                    const float wj = (a == sl[j] ? 1.f - al : 0.f) + (b == sl[j] ? al : 0.f);
+                    cx.w[run][r][j - 1] = make_float2(wj, wj);
+                }
             }
             __syncwarp();
             float2 *half = xring + k * G::PRING * ROWB;
@@ -923,28 +958,18 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
         if (!mbar_wait(&ps->ready[k], use)) break;
         const PersistCtx &cx = ps->ctx[k];
         if (cx.end) return;
-        const int T0 = cx.T0, nb_o = cx.n_blocks, nchunks = cx.nchunks, U = cx.U;
+        const int T0 = cx.T0, nb_o = cx.n_blocks, nchunks = cx.nchunks;
         const int tf = T0 + 2 * R * w;
         const bool active = w < cx.n_active;
         RunSlots<R, NSM> rs;
-        {
-            int a[R], b[R];
-            float al[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                a[r] = cx.a[R * w + r];
-                b[r] = cx.b[R * w + r];
-                al[r] = cx.al[R * w + r];
-            }
-            run_slots_core<R, NSM>(a, b, al, rs);
-        }
         int idx[NSM];
+        rs.ns = cx.ns[w];
 #pragma unroll
-        for (int j = 0; j < NSM; ++j) {
-            idx[j] = 0;
-            for (int q = 0; q < U; ++q)
-                if (j < rs.ns && cx.slot[q] == rs.sl[j]) idx[j] = q;
-        }
+        for (int j = 0; j < NSM; ++j) idx[j] = cx.idx[w][j];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int j = 1; j < NSM; ++j) rs.w[r][j - 1] = cx.w[w][r][j - 1];
         int m_end = 0;
         if (active) {
             m_end = (tf + 2 * (R - 1)) / 2 + 1;
@@ -952,7 +977,7 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
         }
         if (!mbar_wait(&ps->win[k], use)) break;
         const float2 *half = xring + k * G::PRING * ROWB;
-        float2 acc[R][BPL];
+        CAcc acc[R][BPL];
         bool ok;
         if (!active || rs.ns == 1)
             ok = persist_consume<1, NSM, BPL, PST>(ps, half, hst, w, lane, nchunks, m_end, seq, rs, idx, acc);
@@ -971,9 +996,9 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
                 if (t < nb_o) {
                     if constexpr (BPL == 2)
                         *reinterpret_cast<float4 *>(Yo + (int64_t)t * P) =
-                            make_float4(acc[r][0].x, acc[r][0].y, acc[r][1].x, acc[r][1].y);
+                            pack2(cacc_value(acc[r][0]), cacc_value(acc[r][1]));
                     else
-                        Yo[(int64_t)t * P] = acc[r][0];
+                        Yo[(int64_t)t * P] = cacc_value(acc[r][0]);
                 }
             }
         }
@@ -1096,7 +1121,7 @@ cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, con
     // CTA; 4: as 3 with two bins per thread where the bins split into 64-bin
     // tiles; 5: persistent groups of up to four filters
     if (h->mac_variant == 0)
-        e = launch_persist<3, 1, 3, 4>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
+        e = launch_persist<3, 1, 3, 3>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
     else if (h->mac_variant == 5)
         e = launch_persist<4, 1, 4, 3>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
     else if (h->mac_variant == 2)
