@@ -478,14 +478,15 @@ typedef enum tvolap_option {
     /* Staging of the offline multiply-accumulate: 0 = tiled bulk tensor copies
        (TMA) when the buffers allow it, else cp.async (default): resident CTAs
        take groups of 64 consecutive blocks from a work counter, staging up to
-       three distinct filters per group; 1 = always cp.async; 2 = TMA, one
-       group per CTA, up to four distinct filters per group (for schedules that
-       cycle four filters; fewer resident groups per SM); 3 = TMA, one group
-       per CTA, up to three filters; 4 = as 3 with two adjacent bins per thread
-       when 2L is a multiple of 64 (fastest for slowly changing filters);
-       5 = as 0 with up to four filters per group. 0, 1, 3 and 4 give
-       identical results, and so do 2 and 5; 2 and 5 differ from the others
-       only in the rounding of blocks whose group holds four filters. */
+       four distinct filters per group, a run of 16 blocks mixing at most
+       three (groups with more go to a per-warp kernel that splits their
+       runs); 1 = always cp.async; 2 = TMA, one group per CTA, up to four
+       distinct filters per group and per run (for schedules that cycle four
+       filters); 3 = TMA, one group per CTA, up to three filters; 4 = as 3
+       with two adjacent bins per thread when 2L is a multiple of 64 (fastest
+       for slowly changing filters); 5 = as 0 with runs of up to four filters.
+       0, 1, 3 and 4 give identical results, and so do 2 and 5; 2 and 5 differ
+       from the others only in the rounding of runs that mix four filters. */
     TVOLAP_OPT_MAC_STAGING = 1,
     /* 1: tvolap_process_block records CUDA events around its three stages
        (forward transform, multiply-accumulate, inverse + overlap-add) and

@@ -709,7 +709,9 @@ struct PersistItem {
     float al;
 };
 
-template <int NSM, int BPL, int PST, int MINB>
+// RNS: most filters one run (8 blocks) may mix in this kernel (NSM or 3);
+// with 3, every run takes the arithmetic of the three-filter kernels.
+template <int NSM, int RNS, int BPL, int PST, int MINB>
 __global__ void __launch_bounds__(32 * (GW + 1), MINB)
 k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap hmap,
                      int n_blocks, int M, int P, int n_slots_total, int null_slot,
@@ -793,7 +795,8 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
             PersistCtx &cx = ps->ctx[k];
             // the next item with work that fits the staging (others: skipped or listed)
             bool found = false;
-            int U = 0, a = 0, b = 0;
+            int U = 0, a = 0, b = 0, rns = 0;
+            int rsl[NSM];                              // this lane's run's slots, order of first use
             float al = 0.f;
             while (I.id < n_items) {
                 if (I.T0 >= I.nb) {
@@ -831,6 +834,28 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
                     ++U;
                     va = va && (a != v);
                     vb = vb && (b != v);
+                }
+                if (!ovf) {
+                    // run w = lanes 8w .. 8w + 7 (block r = lane mod 8): its slots in
+                    // order of first use (blocks in order, a before b; a slot only
+                    // where its weight is nonzero), as run_slots_core finds them
+                    const int sh = lane & ~(R - 1);
+                    bool ra = (al != 1.f) || (a == b), rb = (al != 0.f) && (b != a);
+                    rns = 0;
+#pragma unroll
+                    for (int j = 0; j < NSM; ++j) {
+                        const unsigned m = (__ballot_sync(0xffffffffu, ra || rb) >> sh) & 0xffu;
+                        const int v = __shfl_sync(0xffffffffu, ra ? a : b, sh + (m ? __ffs(m) - 1 : 0));
+                        rsl[j] = m ? v : 0;
+                        if (m) {
+                            rns = j + 1;
+                            ra = ra && (a != v);
+                            rb = rb && (b != v);
+                        }
+                    }
+                    // a run mixing more than RNS filters goes to the per-warp
+                    // kernel with its whole group (that kernel splits it)
+                    if (__any_sync(0xffffffffu, rns > RNS)) ovf = 1;
                 }
                 if (ovf) {
                     // the per-warp kernel takes 32-bin tiles
@@ -874,36 +899,21 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
             }
             __syncwarp();
             {
-                // run w = lanes 8w .. 8w + 7 (block r = lane mod 8): its slots in
-                // order of first use (blocks in order, a before b; a slot only where
-                // its weight is nonzero), as run_slots_core finds them
-                const int sh = lane & ~(R - 1), r = lane & (R - 1), run = lane / R;
-                bool ra = (al != 1.f) || (a == b), rb = (al != 0.f) && (b != a);
-                int sl[NSM], ns = 0;
-#pragma unroll
-                for (int j = 0; j < NSM; ++j) {
-                    const unsigned m = (__ballot_sync(0xffffffffu, ra || rb) >> sh) & 0xffu;
-                    const int v = __shfl_sync(0xffffffffu, ra ? a : b, sh + (m ? __ffs(m) - 1 : 0));
-                    sl[j] = m ? v : 0;
-                    if (m) {
-                        ns = j + 1;
-                        ra = ra && (a != v);
-                        rb = rb && (b != v);
-                    }
-                }
+                // per run: its slots' places among the staged ones, its blocks' weights
+                const int r = lane & (R - 1), run = lane / R;
                 if (r == 0) {
-                    cx.ns[run] = ns;
+                    cx.ns[run] = rns;
 #pragma unroll
                     for (int j = 0; j < NSM; ++j) {
                         int q0 = 0;
                         for (int q = 0; q < U; ++q)
-                            if (j < ns && cx.slot[q] == sl[j]) q0 = q;
+                            if (j < rns && cx.slot[q] == rsl[j]) q0 = q;
                         cx.idx[run][j] = q0;
                     }
                 }
 #pragma unroll
                 for (int j = 1; j < NSM; ++j) {
-                    const float wj = (a == sl[j] ? 1.f - al : 0.f) + (b == sl[j] ? al : 0.f);
+                    const float wj = (a == rsl[j] ? 1.f - al : 0.f) + (b == rsl[j] ? al : 0.f);
                     cx.w[run][r][j - 1] = make_float2(wj, wj);
                 }
             }
@@ -925,14 +935,19 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
                 if (seq >= NST && !(ok = mbar_wait(&ps->empty[q], ((seq - NST) / NST) & 1u))) break;
                 filled |= 1u << q;
                 ppar = (ppar & ~(1u << q)) | (((seq / NST) & 1u) << q);
-                if (lane == 0) {
+                {
                     uint64_t *bar = &ps->full[q];
-                    mbar_expect_tx(bar, (uint32_t)((1 + U) * D * RB));
-                    // new X rows i = -8c - 7 .. -8c, then the group's slots' rows
-                    tma_load_3d(half + pring_slot<G::PRING>(-D * c) * ROWB, &xmap, k0,
-                                cur.T0 - 2 * D * c - 2 * (D - 1), cin, bar);
-                    for (int j = 0; j < U; ++j)
-                        tma_load_3d(hst + (q * G::HSTAGE_ROWS + j * D) * ROWB, &hmap, k0, c * D, cx.slot[j], bar);
+                    if (lane == 0) mbar_expect_tx(bar, (uint32_t)((1 + U) * D * RB));
+                    __syncwarp();
+                    // the chunk's copies from U + 1 lanes at once (about a fifth less
+                    // issue time than one lane issuing them in turn): lane 0 the new
+                    // X rows i = -8c - 7 .. -8c, lane 1 + j the rows of slot j
+                    if (lane == 0)
+                        tma_load_3d(half + pring_slot<G::PRING>(-D * c) * ROWB, &xmap, k0,
+                                    cur.T0 - 2 * D * c - 2 * (D - 1), cin, bar);
+                    else if (lane <= U)
+                        tma_load_3d(hst + (q * G::HSTAGE_ROWS + (lane - 1) * D) * ROWB, &hmap, k0, c * D,
+                                    cx.slot[lane - 1], bar);
                 }
             }
             if (!ok) break;
@@ -983,7 +998,7 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
             ok = persist_consume<1, NSM, BPL, PST>(ps, half, hst, w, lane, nchunks, m_end, seq, rs, idx, acc);
         else if (rs.ns == 2)
             ok = persist_consume<2, NSM, BPL, PST>(ps, half, hst, w, lane, nchunks, m_end, seq, rs, idx, acc);
-        else if (NSM == 3 || rs.ns == 3)
+        else if (RNS == 3 || rs.ns == 3)
             ok = persist_consume<3, NSM, BPL, PST>(ps, half, hst, w, lane, nchunks, m_end, seq, rs, idx, acc);
         else
             ok = persist_consume<NSM, NSM, BPL, PST>(ps, half, hst, w, lane, nchunks, m_end, seq, rs, idx, acc);
@@ -1067,7 +1082,7 @@ cudaError_t launch_group(const float2 *X, int n_blocks, tvolap_plan *h, int grou
     return cudaGetLastError();
 }
 
-template <int NSM, int BPL, int PST, int MINB>
+template <int NSM, int RNS, int BPL, int PST, int MINB>
 cudaError_t launch_persist(const float2 *X, int n_blocks, tvolap_plan *h, int groups,
                            const int32_t *sa, const int32_t *sb, const float *sal,
                            int64_t sched_stride, float2 *Y, Ragged rg)
@@ -1079,11 +1094,11 @@ cudaError_t launch_persist(const float2 *X, int n_blocks, tvolap_plan *h, int gr
     const int smem = PersistGeo<NSM, BPL, PST>::BYTES;
     static int per_sm = 0;                       // resident CTAs per SM (same for every device here)
     if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_mac_signal_persist<NSM, BPL, PST, MINB>,
+        cudaError_t e = cudaFuncSetAttribute(k_mac_signal_persist<NSM, RNS, BPL, PST, MINB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         int n = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mac_signal_persist<NSM, BPL, PST, MINB>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mac_signal_persist<NSM, RNS, BPL, PST, MINB>,
                                                           32 * (GW + 1), smem);
         if (e != cudaSuccess) return e;
         per_sm = n > 0 ? n : 1;
@@ -1092,7 +1107,7 @@ cudaError_t launch_persist(const float2 *X, int n_blocks, tvolap_plan *h, int gr
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
     const int64_t n_items = (int64_t)2 * groups * (h->P / (32 * BPL)) * h->n_out;
     const int64_t grid = n_items < (int64_t)per_sm * sms ? n_items : (int64_t)per_sm * sms;
-    k_mac_signal_persist<NSM, BPL, PST, MINB><<<(unsigned)grid, 32 * (GW + 1), smem, h->stream>>>(
+    k_mac_signal_persist<NSM, RNS, BPL, PST, MINB><<<(unsigned)grid, 32 * (GW + 1), smem, h->stream>>>(
         xmap, hmap, n_blocks, h->M, h->P, h->n_slots_total, h->null_slot, h->out_to_in, sa, sb,
         sal, sched_stride, Y, h->err, h->ovf_list, h->ovf_count, (int)n_items, rg);
     return cudaGetLastError();
@@ -1117,13 +1132,14 @@ cudaError_t launch_mac_signal(tvolap_plan *h, const float2 *X, int n_blocks, con
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(h->ovf_count, 0, 2 * sizeof(int), h->stream);   // overflow count, work counter
     if (e != cudaSuccess) return e;
-    // 0: persistent groups; 2: groups of up to four filters; 3: one group per
-    // CTA; 4: as 3 with two bins per thread where the bins split into 64-bin
-    // tiles; 5: persistent groups of up to four filters
+    // 0: persistent groups of up to four filters, runs of up to three; 2: groups
+    // (and runs) of up to four filters; 3: one group per CTA; 4: as 3 with two
+    // bins per thread where the bins split into 64-bin tiles; 5: as 0 with runs
+    // of up to four filters
     if (h->mac_variant == 0)
-        e = launch_persist<3, 1, 3, 3>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
+        e = launch_persist<4, 3, 1, 4, 3>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
     else if (h->mac_variant == 5)
-        e = launch_persist<4, 1, 4, 3>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
+        e = launch_persist<4, 4, 1, 4, 3>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
     else if (h->mac_variant == 2)
         e = launch_group<4, 1>(X, n_blocks, h, groups, sa, sb, sal, sched_stride, Y, rg);
     else if (h->mac_variant == 4 && h->P % 64 == 0)

@@ -115,10 +115,10 @@ class Plan:
         self._call("tvolap_reset")
 
     def set_option(self, option: int, value: int):
-        """TVOLAP_OPT_MAC_STAGING (1): 0 = persistent TMA groups (default),
-        1 = cp.async, 2 = TMA groups of up to four filters, 3 = one TMA group
-        per CTA, 4 = as 3 with two bins per thread, 5 = as 0 with up to four
-        filters per group. TVOLAP_OPT_STAGE_TIMING (2): 1 = time the three
+        """TVOLAP_OPT_MAC_STAGING (1): 0 = persistent TMA groups of up to four
+        filters, runs of up to three (default), 1 = cp.async, 2 = TMA groups
+        and runs of up to four filters, 3 = one TMA group per CTA, 4 = as 3
+        with two bins per thread, 5 = as 0 with runs of up to four filters. TVOLAP_OPT_STAGE_TIMING (2): 1 = time the three
         stages of process_block (see stage_times). TVOLAP_OPT_XFORM_THREADS
         (3): threads per CTA of the offline transforms, 0 (256), 128 or 64."""
         self._call("tvolap_set_option", int(option), int(value))
