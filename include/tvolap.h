@@ -483,8 +483,8 @@ typedef enum tvolap_option {
        runs); 1 = always cp.async; 2 = TMA, one group per CTA, up to four
        distinct filters per group and per run (for schedules that cycle four
        filters); 3 = TMA, one group per CTA, up to three filters; 4 = as 3
-       with two adjacent bins per thread when 2L is a multiple of 64 (fastest
-       for slowly changing filters); 5 = as 0 with runs of up to four filters.
+       with two adjacent bins per thread when 2L is a multiple of 64; 5 = as 0
+       with runs of up to four filters.
        0, 1, 3 and 4 give identical results, and so do 2 and 5; 2 and 5 differ
        from the others only in the rounding of runs that mix four filters. */
     TVOLAP_OPT_MAC_STAGING = 1,
