@@ -196,6 +196,7 @@ k_inverse_ola(const float2 *__restrict__ Y, int n_blocks, int L, int seg, int n_
     const float2 *Yo = Y + (int64_t)o * n_blocks * P;
     float *yo = y + (int64_t)o * y_stride;
     const bool pairs = (reinterpret_cast<uintptr_t>(yo) & 7) == 0;
+    const bool pf = (reinterpret_cast<uintptr_t>(Yo) & 15) == 0;
     const int64_t t_lo = tile0 - 2 > 0 ? tile0 - 2 : 0;
     int64_t t_hi = tile0 + seg;
     if (t_hi > nb_o - 1) t_hi = nb_o - 1;
@@ -220,6 +221,10 @@ k_inverse_ola(const float2 *__restrict__ Y, int n_blocks, int L, int seg, int n_
         const int64_t t = t_lo + it;
         const bool act = on && t <= t_hi;
         const float2 *Yt = Yo + (act ? t : 0) * P;
+        // the next block's spectrum moves to L2 while this one is transformed
+        // (a bulk prefetch wants a 16-byte aligned source: Y's rows are 8P bytes)
+        if (j == 0 && act && t < t_hi && pf)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Yt + P), "r"(P * 8) : "memory");
         // hop t - 1 (block l = t - 1 starts at sample l*L) is final after this
         // block: pending + the block's first hop; the other hops add to pending
         const int64_t n0 = (t - 1) * (int64_t)L;
