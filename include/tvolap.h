@@ -478,9 +478,9 @@ typedef enum tvolap_option {
     /* Staging of the offline multiply-accumulate: 0 = tiled bulk tensor copies
        (TMA) when the buffers allow it, else cp.async (default): resident CTAs
        take groups of 64 consecutive blocks from a work counter, staging up to
-       four distinct filters per group, a run of 16 blocks mixing at most
-       three (groups with more go to a per-warp kernel that splits their
-       runs); 1 = always cp.async; 2 = TMA, one group per CTA, up to four
+       four distinct filters per group, a run (8 blocks of one parity)
+       mixing at most three (groups with more go to a per-warp kernel that
+       splits their runs); 1 = always cp.async; 2 = TMA, one group per CTA, up to four
        distinct filters per group and per run (for schedules that cycle four
        filters); 3 = TMA, one group per CTA, up to three filters; 4 = as 3
        with two adjacent bins per thread when 2L is a multiple of 64; 5 = as 0

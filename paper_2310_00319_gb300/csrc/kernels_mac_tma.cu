@@ -611,15 +611,16 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
 // two-part X ring, its window barrier and the group's description (output,
 // tile, the staged slots and, per run, its slots' places among them and its
 // blocks' mix weights: the loader warp derives them, eight lanes per run, so
-// a consumer's set-up is a few shared-memory reads). The filter stages and their full/empty
-// barriers are shared and run on through the groups; with PSTAGE stages the
-// loader keeps up to PSTAGE chunks in flight. The loader fills context k for
-// group i as soon as the consumers have released it (group i - 2 done:
-// barrier 'freed'), publishes it ('ready'), issues its window, then its chunks
-// as stages come free; the next group's schedule entries load while the
-// current group's chunks are issued, and one work-counter request is always in
-// flight. Taking groups in counter order keeps the CTAs on neighbouring groups,
-// whose X rows and filter rows overlap in L2. Consumer warps without
+// a consumer's set-up is a few shared-memory reads). The filter stages and
+// their full/empty barriers are shared and run on through the groups; with
+// PSTAGE stages the loader keeps up to PSTAGE chunks in flight. The loader
+// fills context k for group i as soon as the consumers have released it
+// (group i - 2 done: barrier 'freed'), publishes it ('ready'), issues its
+// window, then its chunks as stages come free (a chunk's copies from several
+// lanes at once); the next group's schedule entries load while the current
+// group's chunks are issued, and one work-counter request is always in
+// flight. Taking groups in counter order keeps the CTAs on neighbouring
+// groups, whose X rows and filter rows overlap in L2. Consumer warps without
 // a run in a group (past the output's last block) still take part in every
 // chunk's barriers, so the empty barriers always count four arrivals.
 //
@@ -709,8 +710,9 @@ struct PersistItem {
     float al;
 };
 
-// RNS: most filters one run (8 blocks) may mix in this kernel (NSM or 3);
-// with 3, every run takes the arithmetic of the three-filter kernels.
+// RNS: most filters one run (its 8 blocks of one parity) may mix in this
+// kernel (NSM or 3); with 3, every run takes the arithmetic of the
+// three-filter kernels.
 template <int NSM, int RNS, int BPL, int PST, int MINB>
 __global__ void __launch_bounds__(32 * (GW + 1), MINB)
 k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap hmap,
