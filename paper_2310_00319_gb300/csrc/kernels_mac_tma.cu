@@ -609,9 +609,9 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
 // counter, so a group's first copies are issued while the CTA still computes
 // the previous group. Two group contexts alternate: each has its half of a
 // two-part X ring, its window barrier and the group's description (output,
-// tile, the staged slots and, per run, its slots' places among them and its
-// blocks' mix weights: the loader warp derives them, eight lanes per run, so
-// a consumer's set-up is a few shared-memory reads). The filter stages and
+// tile, the staged slots and the 32 blocks' schedule entries; each consumer
+// warp derives its run's slot order and weights from them with ballots over
+// eight lanes). The filter stages and
 // their full/empty barriers are shared and run on through the groups; with
 // PSTAGE stages the loader keeps up to PSTAGE chunks in flight. The loader
 // fills context k for group i as soon as the consumers have released it
@@ -634,9 +634,8 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
 struct PersistCtx {
     int T0, o, k0, cin, n_blocks, M, nchunks, n_active, U, end;
     int slot[4];                               // the group's staged slots
-    int ns[GW];                                // per run: distinct slots,
-    int idx[GW][4];                            // their places in slot[] (order of first use),
-    float2 w[GW][TMA_R][3];                    // weights of its slots 1.. per block, as (w, w)
+    int a[GROUP_ROWS], b[GROUP_ROWS];          // checked schedule entries of blocks T0 + 2i
+    float al[GROUP_ROWS];
 };
 
 struct PersistSmem {
@@ -837,10 +836,9 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
                     va = va && (a != v);
                     vb = vb && (b != v);
                 }
-                if (!ovf) {
-                    // run w = lanes 8w .. 8w + 7 (block r = lane mod 8): its slots in
-                    // order of first use (blocks in order, a before b; a slot only
-                    // where its weight is nonzero), as run_slots_core finds them
+                if (!ovf && U > RNS) {
+                    // only a group staging more than RNS filters can hold a run that
+                    // mixes more: run w = lanes 8w .. 8w + 7, its distinct slots
                     const int sh = lane & ~(R - 1);
                     bool ra = (al != 1.f) || (a == b), rb = (al != 0.f) && (b != a);
                     rns = 0;
@@ -900,25 +898,9 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
                 cx.end = 0;
             }
             __syncwarp();
-            {
-                // per run: its slots' places among the staged ones, its blocks' weights
-                const int r = lane & (R - 1), run = lane / R;
-                if (r == 0) {
-                    cx.ns[run] = rns;
-#pragma unroll
-                    for (int j = 0; j < NSM; ++j) {
-                        int q0 = 0;
-                        for (int q = 0; q < U; ++q)
-                            if (j < rns && cx.slot[q] == rsl[j]) q0 = q;
-                        cx.idx[run][j] = q0;
-                    }
-                }
-#pragma unroll
-                for (int j = 1; j < NSM; ++j) {
-                    const float wj = (a == rsl[j] ? 1.f - al : 0.f) + (b == rsl[j] ? al : 0.f);
-                    cx.w[run][r][j - 1] = make_float2(wj, wj);
-                }
-            }
+            cx.a[lane] = a;
+            cx.b[lane] = b;
+            cx.al[lane] = al;
             __syncwarp();
             float2 *half = xring + k * G::PRING * ROWB;
             if (lane == 0) {
@@ -975,18 +957,56 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
         if (!mbar_wait(&ps->ready[k], use)) break;
         const PersistCtx &cx = ps->ctx[k];
         if (cx.end) return;
-        const int T0 = cx.T0, nb_o = cx.n_blocks, nchunks = cx.nchunks;
+        const int T0 = cx.T0, nb_o = cx.n_blocks, nchunks = cx.nchunks, U = cx.U;
         const int tf = T0 + 2 * R * w;
         const bool active = w < cx.n_active;
+        // the run's slots in order of first use (blocks in order, a before b; a
+        // slot only where its weight is nonzero), as run_slots_core finds them,
+        // with lane r < 8 holding block r, then every block's weights to all lanes
         RunSlots<R, NSM> rs;
         int idx[NSM];
-        rs.ns = cx.ns[w];
+        {
+            int a = 0, b = 0;
+            float al = 0.f;
+            bool va = false, vb = false;
+            if (lane < R) {
+                a = cx.a[R * w + lane];
+                b = cx.b[R * w + lane];
+                al = cx.al[R * w + lane];
+                va = (al != 1.f) || (a == b);
+                vb = (al != 0.f) && (b != a);
+            }
+            int ns = 0;
 #pragma unroll
-        for (int j = 0; j < NSM; ++j) idx[j] = cx.idx[w][j];
+            for (int j = 0; j < NSM; ++j) {
+                const unsigned m = __ballot_sync(0xffffffffu, va || vb);
+                const int v = __shfl_sync(0xffffffffu, va ? a : b, m ? __ffs(m) - 1 : 0);
+                rs.sl[j] = m ? v : 0;
+                if (m) {
+                    ns = j + 1;
+                    va = va && (a != v);
+                    vb = vb && (b != v);
+                }
+            }
+            rs.ns = ns;
 #pragma unroll
-        for (int r = 0; r < R; ++r)
+            for (int j = 0; j < NSM; ++j) {
+                int q0 = 0;
 #pragma unroll
-            for (int j = 1; j < NSM; ++j) rs.w[r][j - 1] = cx.w[w][r][j - 1];
+                for (int q = 0; q < NSM; ++q)
+                    if (q < U && j < ns && cx.slot[q] == rs.sl[j]) q0 = q;
+                idx[j] = q0;
+            }
+#pragma unroll
+            for (int j = 1; j < NSM; ++j) {
+                const float wj = (a == rs.sl[j] ? 1.f - al : 0.f) + (b == rs.sl[j] ? al : 0.f);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float wr = __shfl_sync(0xffffffffu, wj, r);
+                    rs.w[r][j - 1] = make_float2(wr, wr);
+                }
+            }
+        }
         int m_end = 0;
         if (active) {
             m_end = (tf + 2 * (R - 1)) / 2 + 1;
