@@ -57,6 +57,7 @@ struct LsuArgs {
     unsigned *err;
     float2 *ring;              // this thread's ring base
     int ring_stride;
+    int lane;
 };
 
 template <int R, int D, int NS>
@@ -116,7 +117,7 @@ template <int R, int D>
 __device__ __forceinline__ void lsu_process_run(const LsuArgs &g, int tf)
 {
     RunSlots<R> rs;
-    run_slots<R>(g.ao, g.bo, g.alo, tf, g.n_blocks, g.n_slots_total, g.null_slot, g.err, rs);
+    run_slots<R>(g.ao, g.bo, g.alo, tf, g.n_blocks, g.n_slots_total, g.null_slot, g.err, g.lane, rs);
     if constexpr (R > 1) {
         if (rs.overflow) {
             lsu_process_run<R / 2, D>(g, tf);
@@ -180,6 +181,7 @@ k_mac_signal_lsu(const float2 *__restrict__ X, int n_blocks, int M, int P,
     g.err = err;
     g.ring = ring_all + threadIdx.x;
     g.ring_stride = 32 * LSU_WARPS;
+    g.lane = lane;
     lsu_process_run<R, D>(g, tf);
 }
 

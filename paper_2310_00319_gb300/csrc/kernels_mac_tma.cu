@@ -211,7 +211,7 @@ template <int R>
 __device__ __forceinline__ void tma_process_run(const TmaArgs &g, Pipe &pp, int tf)
 {
     RunSlots<R> rs;
-    run_slots<R>(g.ao, g.bo, g.alo, tf, g.n_blocks, g.n_slots_total, g.null_slot, g.err, rs);
+    run_slots<R>(g.ao, g.bo, g.alo, tf, g.n_blocks, g.n_slots_total, g.null_slot, g.err, g.lane, rs);
     if constexpr (R > 1) {
         if (rs.overflow) {
             tma_process_run<R / 2>(g, pp, tf);
@@ -565,7 +565,7 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
     if (w >= n_active) return;                        // ---- consumers (no CTA barriers below)
     const int tf = T0 + 2 * R * w;
     RunSlots<R, NSM> rs;
-    run_slots<R, NSM>(ao, bo, alo, tf, n_blocks, n_slots_total, null_slot, err, rs);
+    run_slots<R, NSM>(ao, bo, alo, tf, n_blocks, n_slots_total, null_slot, err, lane, rs);
     int idx[NSM];
 #pragma unroll
     for (int j = 0; j < NSM; ++j) {
@@ -838,7 +838,8 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
                 }
                 if (!ovf && U > RNS) {
                     // only a group staging more than RNS filters can hold a run that
-                    // mixes more: run w = lanes 8w .. 8w + 7, its distinct slots
+                    // mixes more: run w = lanes 8w .. 8w + 7, its distinct slots as
+                    // run_slots_lanes counts them
                     const int sh = lane & ~(R - 1);
                     bool ra = (al != 1.f) || (a == b), rb = (al != 0.f) && (b != a);
                     rns = 0;
@@ -960,51 +961,19 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
         const int T0 = cx.T0, nb_o = cx.n_blocks, nchunks = cx.nchunks, U = cx.U;
         const int tf = T0 + 2 * R * w;
         const bool active = w < cx.n_active;
-        // the run's slots in order of first use (blocks in order, a before b; a
-        // slot only where its weight is nonzero), as run_slots_core finds them,
-        // with lane r < 8 holding block r, then every block's weights to all lanes
+        // the run's slots and weights from the blocks' entries (lane r < 8: block r)
         RunSlots<R, NSM> rs;
         int idx[NSM];
         {
-            int a = 0, b = 0;
-            float al = 0.f;
-            bool va = false, vb = false;
-            if (lane < R) {
-                a = cx.a[R * w + lane];
-                b = cx.b[R * w + lane];
-                al = cx.al[R * w + lane];
-                va = (al != 1.f) || (a == b);
-                vb = (al != 0.f) && (b != a);
-            }
-            int ns = 0;
-#pragma unroll
-            for (int j = 0; j < NSM; ++j) {
-                const unsigned m = __ballot_sync(0xffffffffu, va || vb);
-                const int v = __shfl_sync(0xffffffffu, va ? a : b, m ? __ffs(m) - 1 : 0);
-                rs.sl[j] = m ? v : 0;
-                if (m) {
-                    ns = j + 1;
-                    va = va && (a != v);
-                    vb = vb && (b != v);
-                }
-            }
-            rs.ns = ns;
+            const int rr = lane < R ? lane : 0;
+            run_slots_lanes<R, NSM>(cx.a[R * w + rr], cx.b[R * w + rr], cx.al[R * w + rr], lane, rs);
 #pragma unroll
             for (int j = 0; j < NSM; ++j) {
                 int q0 = 0;
 #pragma unroll
                 for (int q = 0; q < NSM; ++q)
-                    if (q < U && j < ns && cx.slot[q] == rs.sl[j]) q0 = q;
+                    if (q < U && j < rs.ns && cx.slot[q] == rs.sl[j]) q0 = q;
                 idx[j] = q0;
-            }
-#pragma unroll
-            for (int j = 1; j < NSM; ++j) {
-                const float wj = (a == rs.sl[j] ? 1.f - al : 0.f) + (b == rs.sl[j] ? al : 0.f);
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const float wr = __shfl_sync(0xffffffffu, wj, r);
-                    rs.w[r][j - 1] = make_float2(wr, wr);
-                }
             }
         }
         int m_end = 0;

@@ -64,79 +64,75 @@ struct RunSlots {
     float2 w[R][NSM - 1];        // weights of s_1 .. s_{NSM-1} per block, as (w, w) pairs
 };
 
-// Distinct slots and mix weights of a run from its blocks' schedule entries
-// a[r], b[r], al[r] (already checked): slots in order of first use (block
-// order, a before b), a slot counted only where its weight is nonzero.
+// Distinct slots and mix weights of a run, for a warp whose lanes all take
+// that run: lane r < R holds block r's schedule entries a, b, al (already
+// checked; other lanes' values are ignored). Slots come in order of first use
+// (block order, a before b), a slot counted only where its weight is nonzero,
+// found with ballots over the R lanes; every lane ends with the same RunSlots
+// (the weights of all R blocks). The warp must be converged.
 template <int R, int NSM>
-__device__ __forceinline__ void run_slots_core(const int (&a)[R], const int (&b)[R],
-                                               const float (&al)[R], RunSlots<R, NSM> &rs)
+__device__ __forceinline__ void run_slots_lanes(int a, int b, float al, int lane, RunSlots<R, NSM> &rs)
 {
+    bool va = false, vb = false;
+    if (lane < R) {
+        va = (al != 1.f) || (a == b);                // a's weight 1 - al, or a single slot
+        vb = (al != 0.f) && (b != a);
+    }
     int ns = 0;
-    bool overflow = false;
 #pragma unroll
-    for (int j = 0; j < NSM; ++j) rs.sl[j] = 0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int v = q ? b[r] : a[r];
-            const float wt = q ? al[r] : 1.f - al[r];
-            if (wt == 0.f && !(q == 0 && b[r] == a[r])) continue;   // slot unused by this block
-            bool seen = false;
-#pragma unroll
-            for (int j = 0; j < NSM; ++j) seen |= (j < ns) && (rs.sl[j] == v);
-            if (!seen) {
-                if (ns < NSM) {
-#pragma unroll
-                    for (int j = 0; j < NSM; ++j)
-                        if (j == ns) rs.sl[j] = v;
-                    ++ns;
-                } else {
-                    overflow = true;
-                }
-            }
+    for (int j = 0; j < NSM; ++j) {
+        const unsigned m = __ballot_sync(0xffffffffu, va || vb);
+        const int v = __shfl_sync(0xffffffffu, va ? a : b, m ? __ffs(m) - 1 : 0);
+        rs.sl[j] = m ? v : 0;
+        if (m) {
+            ns = j + 1;
+            va = va && (a != v);
+            vb = vb && (b != v);
         }
     }
+    rs.overflow = __any_sync(0xffffffffu, va || vb);   // more than NSM distinct slots
+    const int a0 = __shfl_sync(0xffffffffu, a, 0);
     if (ns == 0) {
-        rs.sl[0] = a[0];
+        rs.sl[0] = a0;
         ns = 1;
     }
     rs.ns = ns;
-    rs.overflow = overflow;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+    for (int j = 1; j < NSM; ++j) {
+        const float wj = (a == rs.sl[j] ? 1.f - al : 0.f) + (b == rs.sl[j] ? al : 0.f);
 #pragma unroll
-        for (int j = 1; j < NSM; ++j) {
-            const float wj = (a[r] == rs.sl[j] ? 1.f - al[r] : 0.f) + (b[r] == rs.sl[j] ? al[r] : 0.f);
-            rs.w[r][j - 1] = make_float2(wj, wj);
+        for (int r = 0; r < R; ++r) {
+            const float wr = __shfl_sync(0xffffffffu, wj, r);
+            rs.w[r][j - 1] = make_float2(wr, wr);
         }
     }
 }
 
-// Schedule of blocks tf, tf+2, .., tf+2(R-1) (rows past n_blocks repeat the
-// last valid row; their results are dropped).
+// run_slots_lanes for blocks tf, tf+2, .., tf+2(R-1) read from the schedule:
+// lane r < R loads and checks block r's entries; rows past n_blocks repeat
+// the last valid row (their results are dropped).
 template <int R, int NSM = MAX_NS>
 __device__ __forceinline__ void run_slots(const int32_t *__restrict__ ao, const int32_t *__restrict__ bo,
                                           const float *__restrict__ alo, int tf, int n_blocks,
-                                          int n_slots_total, int null_slot, unsigned *err,
+                                          int n_slots_total, int null_slot, unsigned *err, int lane,
                                           RunSlots<R, NSM> &rs)
 {
-    int a[R], b[R];
-    float al[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int t = tf + 2 * r;
-        if (t < n_blocks) {
-            a[r] = checked_slot(__ldg(ao + t), n_slots_total, null_slot, err);
-            b[r] = bo ? checked_slot(__ldg(bo + t), n_slots_total, null_slot, err) : a[r];
-            al[r] = alo ? __ldg(alo + t) : 0.f;
-        } else {
-            a[r] = r ? a[r - 1] : 0;
-            b[r] = r ? b[r - 1] : 0;
-            al[r] = r ? al[r - 1] : 0.f;
-        }
+    int a = 0, b = 0;
+    float al = 0.f;
+    const int t = tf + 2 * lane;
+    if (lane < R && t < n_blocks) {
+        a = checked_slot(__ldg(ao + t), n_slots_total, null_slot, err);
+        b = bo ? checked_slot(__ldg(bo + t), n_slots_total, null_slot, err) : a;
+        al = alo ? __ldg(alo + t) : 0.f;
     }
-    run_slots_core<R, NSM>(a, b, al, rs);
+    // the last valid row of the run (none: every row reads as zeros)
+    int last = tf < n_blocks ? (n_blocks - 1 - tf) / 2 : 0;
+    if (last > R - 1) last = R - 1;
+    const int src = lane < last ? lane : last;
+    a = __shfl_sync(0xffffffffu, a, src);
+    b = __shfl_sync(0xffffffffu, b, src);
+    al = __shfl_sync(0xffffffffu, al, src);
+    run_slots_lanes<R, NSM>(a, b, al, lane, rs);
 }
 
 // One step of Eq. 7 for the R blocks of a run: partition values h0 = H_{s_0}(m),
