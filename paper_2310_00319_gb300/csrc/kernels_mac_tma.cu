@@ -966,7 +966,7 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
         int idx[NSM];
         {
             const int rr = lane < R ? lane : 0;
-            run_slots_lanes<R, NSM>(cx.a[R * w + rr], cx.b[R * w + rr], cx.al[R * w + rr], lane, rs);
+            run_slots_lanes<R, NSM, RNS - 1>(cx.a[R * w + rr], cx.b[R * w + rr], cx.al[R * w + rr], lane, rs);
 #pragma unroll
             for (int j = 0; j < NSM; ++j) {
                 int q0 = 0;

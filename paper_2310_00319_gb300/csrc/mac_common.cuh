@@ -69,8 +69,9 @@ struct RunSlots {
 // checked; other lanes' values are ignored). Slots come in order of first use
 // (block order, a before b), a slot counted only where its weight is nonzero,
 // found with ballots over the R lanes; every lane ends with the same RunSlots
-// (the weights of all R blocks). The warp must be converged.
-template <int R, int NSM>
+// (the weights of all R blocks for slots 1 .. NW; a kernel whose runs mix at
+// most NW + 1 slots needs no more). The warp must be converged.
+template <int R, int NSM, int NW = NSM - 1>
 __device__ __forceinline__ void run_slots_lanes(int a, int b, float al, int lane, RunSlots<R, NSM> &rs)
 {
     bool va = false, vb = false;
@@ -80,15 +81,16 @@ __device__ __forceinline__ void run_slots_lanes(int a, int b, float al, int lane
     }
     int ns = 0;
 #pragma unroll
+    for (int j = 0; j < NSM; ++j) rs.sl[j] = 0;
+#pragma unroll
     for (int j = 0; j < NSM; ++j) {
         const unsigned m = __ballot_sync(0xffffffffu, va || vb);
-        const int v = __shfl_sync(0xffffffffu, va ? a : b, m ? __ffs(m) - 1 : 0);
-        rs.sl[j] = m ? v : 0;
-        if (m) {
-            ns = j + 1;
-            va = va && (a != v);
-            vb = vb && (b != v);
-        }
+        if (!m) break;                               // every slot found (uniform)
+        const int v = __shfl_sync(0xffffffffu, va ? a : b, __ffs(m) - 1);
+        rs.sl[j] = v;
+        ns = j + 1;
+        va = va && (a != v);
+        vb = vb && (b != v);
     }
     rs.overflow = __any_sync(0xffffffffu, va || vb);   // more than NSM distinct slots
     const int a0 = __shfl_sync(0xffffffffu, a, 0);
@@ -98,7 +100,7 @@ __device__ __forceinline__ void run_slots_lanes(int a, int b, float al, int lane
     }
     rs.ns = ns;
 #pragma unroll
-    for (int j = 1; j < NSM; ++j) {
+    for (int j = 1; j <= NW; ++j) {
         const float wj = (a == rs.sl[j] ? 1.f - al : 0.f) + (b == rs.sl[j] ? al : 0.f);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
