@@ -815,18 +815,15 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
                     va = (al != 1.f) || (a == b);
                     vb = (al != 0.f) && (b != a);
                 }
-                // rows past the output's last block repeat its last valid entry
-                const int last = (I.nb - 1 - I.T0) / 2 < 31 ? (I.nb - 1 - I.T0) / 2 : 31;
-                a = __shfl_sync(0xffffffffu, a, lane < last ? lane : last);
-                b = __shfl_sync(0xffffffffu, b, lane < last ? lane : last);
-                al = __shfl_sync(0xffffffffu, al, lane < last ? lane : last);
+                // census: the group's distinct slots with a nonzero weight (in block
+                // order, a before b; rows past the output's last block take no part)
                 U = 0;
                 int ovf = 0;
+                const bool va0 = va, vb0 = vb;
                 for (int i = 0; i <= NSM; ++i) {
-                    const unsigned ma = __ballot_sync(0xffffffffu, va), mb = __ballot_sync(0xffffffffu, vb);
-                    if (!ma && !mb) break;
-                    const int v = ma ? __shfl_sync(0xffffffffu, a, __ffs(ma) - 1)
-                                     : __shfl_sync(0xffffffffu, b, __ffs(mb) - 1);
+                    const unsigned m = __ballot_sync(0xffffffffu, va || vb);
+                    if (!m) break;
+                    const int v = __shfl_sync(0xffffffffu, va ? a : b, __ffs(m) - 1);
                     if (U == NSM) {
                         ovf = 1;
                         break;
@@ -841,7 +838,7 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
                     // mixes more: run w = lanes 8w .. 8w + 7, its distinct slots as
                     // run_slots_lanes counts them
                     const int sh = lane & ~(R - 1);
-                    bool ra = (al != 1.f) || (a == b), rb = (al != 0.f) && (b != a);
+                    bool ra = va0, rb = vb0;
                     rns = 0;
 #pragma unroll
                     for (int j = 0; j < NSM; ++j) {
@@ -965,7 +962,10 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
         RunSlots<R, NSM> rs;
         int idx[NSM];
         {
-            const int rr = lane < R ? lane : 0;
+            // rows past the output's last block repeat the run's last valid row
+            int lastr = tf < nb_o ? (nb_o - 1 - tf) / 2 : 0;
+            if (lastr > R - 1) lastr = R - 1;
+            const int rr = lane < lastr ? lane : lastr;
             run_slots_lanes<R, NSM, RNS - 1>(cx.a[R * w + rr], cx.b[R * w + rr], cx.al[R * w + rr], lane, rs);
 #pragma unroll
             for (int j = 0; j < NSM; ++j) {
