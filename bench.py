@@ -57,7 +57,7 @@ SMS, FP32_LANES = 152, 128
 # DRAM bytes (read + write) of one launch of the persistent multiply-accumulate kernel at
 # the default 64-channel workload: an ncu capture of the same kernel at 32 channels, scaled
 # by the channel count (the traffic grows in proportion to it).
-MAC_TRAFFIC_BYTES = 2 * (309.473280e6 + 215.099136e6)
+MAC_TRAFFIC_BYTES = 2 * (309.411072e6 + 215.104000e6)
 
 # DRAM bytes (read + write) of one launch of the fused adjoint kernel at the
 # 16-channel differentiable workload: an ncu capture of the same kernel at 2
