@@ -541,15 +541,19 @@ k_mac_signal_group(const __grid_constant__ CUtensorMap xmap, const __grid_consta
             }
             filled |= 1u << q;
             ppar = (ppar & ~(1u << q)) | ((uint32_t)(c / NSTAGE & 1) << q);
-            if (lane == 0) {
+            {
                 uint64_t *bar = gs->bar + 1 + q;
-                mbar_expect_tx(bar, (uint32_t)((1 + U) * D * RB));
-                // new X rows i = -8c - 7 .. -8c (blocks T0 - 16c - 14 .. T0 - 16c)
-                tma_load_3d(xring + ring_slot(-D * c) * ROWB, &xmap, k0, T0 - 2 * D * c - 2 * (D - 1),
-                            cin, bar);
-                for (int j = 0; j < U; ++j)
-                    tma_load_3d(hst + (q * GroupGeo<NSM, BPL>::HSTAGE_ROWS + j * D) * ROWB, &hmap, k0,
-                                c * D, gs->slot[j], bar);
+                if (lane == 0) mbar_expect_tx(bar, (uint32_t)((1 + U) * D * RB));
+                __syncwarp();
+                // the chunk's copies from U + 1 lanes at once: lane 0 the new X rows
+                // i = -8c - 7 .. -8c (blocks T0 - 16c - 14 .. T0 - 16c), lane 1 + j
+                // the rows of slot j
+                if (lane == 0)
+                    tma_load_3d(xring + ring_slot(-D * c) * ROWB, &xmap, k0, T0 - 2 * D * c - 2 * (D - 1),
+                                cin, bar);
+                else if (lane <= U)
+                    tma_load_3d(hst + (q * GroupGeo<NSM, BPL>::HSTAGE_ROWS + (lane - 1) * D) * ROWB, &hmap,
+                                k0, c * D, gs->slot[lane - 1], bar);
             }
         }
         if (!ok) {
