@@ -801,7 +801,6 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
             // the next item with work that fits the staging (others: skipped or listed)
             bool found = false;
             int U = 0, a = 0, b = 0, rns = 0;
-            int rsl[NSM];                              // this lane's run's slots, order of first use
             float al = 0.f;
             while (I.id < n_items) {
                 if (I.T0 >= I.nb) {
@@ -848,7 +847,6 @@ k_mac_signal_persist(const __grid_constant__ CUtensorMap xmap, const __grid_cons
                     for (int j = 0; j < NSM; ++j) {
                         const unsigned m = (__ballot_sync(0xffffffffu, ra || rb) >> sh) & 0xffu;
                         const int v = __shfl_sync(0xffffffffu, ra ? a : b, sh + (m ? __ffs(m) - 1 : 0));
-                        rsl[j] = m ? v : 0;
                         if (m) {
                             rns = j + 1;
                             ra = ra && (a != v);
