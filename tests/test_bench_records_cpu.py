@@ -2,8 +2,9 @@
 batched, differentiable and serving workloads keep the figures the line must
 carry (value, per-step time, roofline with kernel and traffic, clocks,
 accuracy against the oracle, the workload's own comparison) and drop the rest;
-the three workloads run with bounded settings and their own autotuning. No
-GPU is needed."""
+the three workloads run with bounded settings and their own autotuning; the
+DRAM traffic the line declares stays within its kernels' algorithmic bytes.
+No GPU is needed."""
 import argparse
 
 import bench
@@ -75,3 +76,22 @@ def test_subrecords_are_bounded(monkeypatch):
     assert seen["serve"][2] == 2000
     assert all(v[3] is None for v in seen.values())      # the autotuner, not a fixed staging
     assert args.steps == 20 and args.staging == 1         # the caller's settings are untouched
+
+
+def test_declared_dram_traffic_is_within_the_algorithmic_bytes():
+    """The DRAM bytes the default line declares for the multiply-accumulate
+    (scaled from an ncu capture at 32 channels) stay within the bytes its
+    launch must move at least once: X read, the bank read and Y written,
+    each once. Traffic above them would mean re-reads; far below, a capture of
+    the wrong kernel or size. The same for the fused adjoint (P read, dP
+    written)."""
+    from synth import workloads as W
+    ch, L, M, n_ir = 64, 256, 94, 8
+    P = 2 * L
+    nb = W.blocks_for(480000, L)
+    algo = 2 * ch * nb * P * 8 + ch * n_ir * M * P * 8
+    assert 0.8 * algo < bench.MAC_TRAFFIC_BYTES <= algo
+    # differentiable workload: 16 channels, 240000 samples, M = 47
+    nb16 = W.blocks_for(240000, L)
+    params = 16 * nb16 * 47 * P * 8
+    assert 0.8 * 2 * params < bench.ADJ_TRAFFIC_BYTES <= 2 * params
